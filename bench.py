@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark: StaticGreedyDU k-seed selection on one GB300.
+
+One step = one full pass of the hot path on one query: initial gains over
+R hash-defined snapshots, then k rounds of argmax + forward DU + reverse
+DU (Algorithm 2 of Cheng et al., CIKM'13), with the graph resident in HBM.
+
+Workload (default): directed R-MAT scale 20 (1,048,576 nodes, 8,388,608
+arcs, (0.57, 0.19, 0.19, 0.05)), weighted cascade, R = 256 (4 x 64-snapshot
+words), k = 50, hash seed 11; seeded synthetic graph.
+
+Metric: snapshot-edges per second (GTEPS), with snapshot-edges the
+implementation-independent count init + forward DU + reverse DU reported
+by the library; ms_per_step is the k-seed select time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the CPU oracle (the plain StaticGreedyDU of oracle/)
+is timed on the host cores on a bounded sample of the same workload.
+Under torchrun each rank runs an independent replica (the path has no
+cross-GPU exchange); value is the sum over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1212_4779_gb300 import inputs  # noqa: E402
+
+METRIC = "GTEPS (snapshot-edges/s) of StaticGreedyDU k-seed selection"
+UNIT = "GTEPS"
+
+# Issued integer operations per hash evaluation, counted from the coin's
+# arithmetic (see the roofline section of the design notes): the 64-bit
+# XOR of the snapshot index, the 64-bit golden-gamma add, two 64-bit
+# xor-shift-multiply rounds (each 64x64 -> 64 multiply is 3 32-bit
+# multiply-adds), the final xor-shift of the high word, the threshold
+# compare, and the bit set / bit-iteration bookkeeping.
+INT_OPS_PER_HASH = 25
+LANES_PER_SM = 128  # INT32 lanes per SM per clock (4 SMSP x 32)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        self.proc = subprocess.Popen([exe, f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits", "-lms", "100"],
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_and_max(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(wl, n, s, d, target_s=15.0):
+    """The oracle's initial-gain phase (snapshot materialisation plus one BFS
+    per (snapshot, node)) on a bounded slice of the snapshots of the same
+    workload, all host cores.  Returns (GTEPS, sample, seconds, cores)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    g = oracle.Graph(n, s, d, wl.model, wl.p)
+    t0 = time.perf_counter()
+    _, e1 = g.init_gains(wl.R, wl.seed, r0=0, r1=1, nthreads=cores)
+    t1 = time.perf_counter() - t0
+    nsnap = int(max(1, min(wl.R - 1, round(target_s / max(t1, 1e-3)))))
+    t0 = time.perf_counter()
+    _, e2 = g.init_gains(wl.R, wl.seed, r0=1, r1=1 + nsnap, nthreads=cores)
+    t2 = time.perf_counter() - t0
+    sample = (f"oracle initial gains of all {n} sources over snapshots 1..{nsnap} of {wl.R} "
+              f"(materialised snapshots, one BFS per (snapshot, node)), {cores} threads")
+    return e2 / t2 / 1e9, sample, t2, cores
+
+
+def run_reference(args, wl):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    n, s, d = wl.graph()
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated
+    sample = cores = None
+    for _ in range(args.steps):
+        v, sample, _t, cores = cpu_baseline(wl, n, s, d, target_s=args.ref_seconds)
+        vals.append(v)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl_desc(wl), "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def wl_desc(wl):
+    return (f"R-MAT scale 20, 8388608 arcs, (0.57,0.19,0.19,0.05), weighted cascade, R={wl.R}, "
+            f"k={wl.k}, hash seed {wl.seed}" if wl.name == "rmat20"
+            else f"{wl.name} {wl.model} p={wl.p} R={wl.R} k={wl.k} seed={wl.seed}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat20_wic")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    wl = inputs.workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1212_4779_gb300 import sg
+
+    n, s, d = wl.graph()
+    g = sg.Graph.from_coo(n, s, d)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    seeds = torch.zeros(wl.k, dtype=torch.int32, device=dev)
+    gains = torch.zeros(wl.k, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # 512 MB > 129 MB L2
+
+    def step():
+        return sg.sg_select(g.handle, wl.R, wl.k, wl.model, wl.p, wl.seed, seeds, gains, stream=stream, stats=True)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_steps, t_warp, edges, launches, st_last = [], [], [], 0, None
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict the graph from L2 between timed steps
+        ev0.record(stream)
+        st = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        t_steps.append(ev0.elapsed_time(ev1))
+        t_warp.append(st["ms_init_warp"])
+        edges.append(st["init_edges"] + st["fwd_edges"] + st["rev_edges"])
+        launches += st["kernel_launches"]
+        st_last = st
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = _barrier_and_max(float(np.sum(t_steps)), ws)
+    ms_step = total_ms / args.steps
+    edges_step = float(np.mean(edges))
+    value = edges_step * ws / (ms_step / 1e3) / 1e9
+
+    peaks, src = _peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    warp_ms = float(np.mean(t_warp))
+    achieved = st_last["init_edges"] * INT_OPS_PER_HASH / (warp_ms / 1e3) / 1e12
+    peak = n_sm * LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "warp_engine_kernel (initial gains)", "achieved": achieved,
+                "peak": peak, "unit": "Tops/s (int32)", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{n_sm} SMs x {LANES_PER_SM} INT32 lanes x median SM clock {sm_mhz:.0f} MHz",
+                "kernel_ms": warp_ms, "hashes_per_launch": st_last["init_edges"],
+                "hash_rate_G_per_s": st_last["init_edges"] / (warp_ms / 1e3) / 1e9}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(sg, wl, n, s, d, args, stream)
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1 and rank == 0:
+        v, sample, _t, cores = cpu_baseline(wl, n, s, d)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl_desc(wl), "n": n, "m": int(g.m), "R": wl.R, "k": wl.k,
+                   "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
+        "snapshot_edges_per_step": edges_step,
+        "phase_ms": {"init": st_last["ms_init"], "init_warp_engine": st_last["ms_init_warp"],
+                     "rounds": st_last["ms_rounds"]},
+        "big_tasks": {"init": st_last["init_big_tasks"], "reverse": st_last["rev_big_tasks"]},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "peaks_source": src,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def measure_e2e(sg, wl, n, s, d, args, stream):
+    """End to end through the C ABI with host buffers: every step uploads
+    the graph from pinned host memory (sg_load_graph, CSR), selects, and
+    reads the seeds and gains back into pinned host memory."""
+    import torch
+
+    order = np.lexsort((d, s))
+    ss, dd = s[order], d[order]
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, ss.astype(np.int64) + 1, 1)
+    rp = np.cumsum(rp)
+    rp_h = torch.from_numpy(rp).pin_memory()
+    col_h = torch.from_numpy(np.ascontiguousarray(dd, dtype=np.int32)).pin_memory()
+    seeds_h = torch.zeros(wl.k, dtype=torch.int32).pin_memory()
+    gains_h = torch.zeros(wl.k, dtype=torch.int64).pin_memory()
+    edges = None
+
+    def one():
+        nonlocal edges
+        h = sg.sg_load_graph(n, col_h.numel(), rp_h, col_h, stream=stream)
+        st = sg.sg_select(h, wl.R, wl.k, wl.model, wl.p, wl.seed, seeds_h, gains_h, stream=stream, stats=True)
+        stream.synchronize()
+        sg.sg_free_graph(h)
+        edges = st["init_edges"] + st["fwd_edges"] + st["rev_edges"]
+
+    for _ in range(max(1, min(2, args.warmup))):
+        one()
+    steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": edges / dt / 1e9, "unit": UNIT, "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": int(rp_h.numel() * 8 + col_h.numel() * 4),
+            "d2h_bytes_per_step": int(wl.k * (4 + 8))}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * sg.h -- C ABI of the GB300 StaticGreedy-DU library (libsg.so).
+ *
+ * StaticGreedy (Cheng, Shen, Huang, Zhang, Cheng, CIKM 2013) picks k seed
+ * nodes of an independent-cascade graph (Section 3.1) greedily on R static
+ * live-edge snapshots (Section 3.3, Algorithm 1); StaticGreedyDU keeps
+ * every candidate's marginal gain current with the dynamic update of
+ * Section 4 (Algorithm 2).  This library runs that path on one GPU:
+ *   - snapshot sampling: arc e is live in snapshot r iff
+ *       hi32(splitmix64(seed ^ (r << 40) ^ e)) < thr(e),
+ *     thr = floor(p * 2^32) (uniform cascade, UIC) or
+ *     thr(u->v) = floor(2^32 / indeg(v)) (weighted cascade, WIC,
+ *     p(u,v) = 1/d_v of Section 3.4.1); snapshots are never stored;
+ *   - initial gains s_v = sum_r |R(G'_r, v)| (Algorithm 2, first loop),
+ *     where R(G'_r, v) includes v itself;
+ *   - k rounds of: v* = argmax over non-seeds of s_v, lowest id on ties;
+ *     forward BFS from v* marking the nodes it newly covers in each
+ *     snapshot; reverse BFS from each newly covered node subtracting one
+ *     from the gain of every node that reaches it (Algorithm 2, inner loops).
+ * All arithmetic is exact integer, so results are bit-identical to any
+ * correct implementation of the same definition.
+ *
+ * Conventions for every entry point:
+ *   - return an sg_status; never abort, trap or print.  On failure
+ *     sg_last_error() returns a thread-local message.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it in stream order.
+ *   - node ids are int32 in [0, n); arcs are directed u -> v.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SG_OK = 0,
+    SG_EINVAL = 1,    /* an argument is out of range or malformed */
+    SG_ENOMEM = 2,    /* a device or host allocation failed */
+    SG_ECUDA = 3,     /* a CUDA runtime call failed */
+    SG_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    SG_EBUSY = 5,     /* the object is in use (e.g. server slots full) */
+    SG_EINTERNAL = 6  /* a device-side consistency check failed */
+} sg_status;
+
+typedef enum { SG_UIC = 0, SG_WIC = 1 } sg_model;
+
+/* Cascade model: UIC uses p in [0, 1] for every arc; WIC ignores p and uses
+ * 1/indeg(v) for every arc u -> v (Section 3.4.1 and Section 5.1). */
+typedef struct {
+    int32_t model; /* sg_model */
+    double p;      /* UIC only */
+} sg_cascade;
+
+/* Counters and timings of one sg_select call.  The three snapshot-edge
+ * counts are implementation independent:
+ *   init_edges = sum over (v, r) and u in R(G'_r, v) of outdeg(u)
+ *   fwd_edges  = sum over newly covered (u, r) of outdeg(u)
+ *   rev_edges  = sum over newly covered (w, r) and u in U(G'_r, w) of indeg(u)
+ * (outdeg / indeg of the canonical graph, live or not). */
+typedef struct {
+    uint64_t init_edges;
+    uint64_t fwd_edges;
+    uint64_t rev_edges;
+    uint64_t init_big_tasks;  /* initial-gain BFS tasks that took the CTA path */
+    uint64_t rev_big_tasks;   /* reverse-BFS tasks that took the CTA path */
+    uint64_t du_entries;      /* (node, 64-snapshot word) pairs newly covered, all rounds */
+    float ms_init;            /* device time of the initial gains */
+    float ms_rounds;          /* device time of the k selection rounds */
+    float ms_total;           /* device time of the whole call */
+    float ms_init_warp;       /* device time of the initial-gain warp-engine launch */
+    int32_t status_flags;     /* nonzero: device-side check failed */
+    int32_t kernel_launches;  /* kernels this call launched */
+} sg_stats;
+
+/* Opaque graph handle; owns its device memory until sg_free_graph. */
+typedef struct sg_graph sg_graph;
+
+/* Device memory hooks.  alloc returns device memory of at least `bytes`
+ * bytes usable on `stream` (NULL on failure); release returns it.  Without
+ * hooks the library uses cudaMallocAsync / cudaFreeAsync.  Passing NULL
+ * functions restores the default.  Not thread-safe with concurrent calls. */
+typedef void *(*sg_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*sg_release_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+sg_status sg_set_allocator(sg_alloc_fn alloc, sg_release_fn release, void *ctx);
+
+/* Load a graph given in CSR form (Section 3.1 graph G).
+ *   n        number of nodes, 1 <= n < 2^31
+ *   m        number of arcs in col, 0 <= m < 2^31
+ *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
+ *   col      int32[m], destinations in [0, n)
+ *   is_device_ptr  0: row_ptr/col are host memory; 1: device memory
+ * The graph is canonicalised: self-loops are dropped and repeated arcs
+ * merged (the paper merges parallel edges, Section 5.1), rows sorted by
+ * destination; canonical arc ids are CSR positions of that graph.  The
+ * caller keeps ownership of its arrays; the library copies them.
+ * Errors: SG_EINVAL for any violated bound above.  The handle is written
+ * to *out only on SG_OK. */
+sg_status sg_load_graph(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                        int is_device_ptr, void *stream, sg_graph **out);
+
+/* Same as sg_load_graph from an arc list src[i] -> dst[i], i < m.
+ * src/dst are host memory when is_device_ptr is 0, device memory when 1. */
+sg_status sg_load_graph_coo(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                            int is_device_ptr, void *stream, sg_graph **out);
+
+/* Node count and canonical arc count. */
+sg_status sg_graph_info(const sg_graph *g, int64_t *n, int64_t *m_canonical);
+
+/* Select k seeds with StaticGreedyDU (Algorithm 2) on R hash-defined
+ * snapshots of g under cascade c.
+ *   R      1 <= R < 2^24 snapshots (64 per bit-sliced word; the last word
+ *          is masked to R mod 64 snapshots)
+ *   k      1 <= k <= n
+ *   seed   64-bit hash seed of the snapshots
+ *   out_seeds int32[k]: seed i (0-based round order)
+ *   out_gains int64[k]: gain_i = f(S_i) - f(S_{i-1}) with
+ *             f(S) = sum_r |R(G'_r, S)|; the spread estimate of S_k is
+ *             sum(gains) / R.
+ *   stats  optional (NULL allowed); filling it synchronises the stream.
+ * Outputs may be device memory, pinned host memory or pageable host
+ * memory; with pageable host memory or stats the call returns after the
+ * stream has finished, otherwise it returns once the work is enqueued.
+ * Ties in the argmax go to the lowest node id among non-seeds, also when
+ * every remaining gain is 0; seeds are never re-picked.
+ * Errors: SG_EINVAL (bounds above, p outside [0,1] or NaN, unknown model),
+ * SG_ENOMEM, SG_ECUDA. */
+sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                    int32_t *out_seeds, int64_t *out_gains, sg_stats *stats);
+
+/* Initial gains only (Algorithm 2, first loop): s[v] = sum_r |R(G'_r, v)|
+ * for every v, written to out_s (int64[n], device or host memory), and the
+ * init snapshot-edge count to *init_edges (NULL allowed; non-NULL
+ * synchronises the stream).  Same argument rules as sg_select. */
+sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, void *stream,
+                        int64_t *out_s, uint64_t *init_edges);
+
+/* Live-edge masks of snapshots 0..R-1 as 64-snapshot words:
+ * out_masks[e * W + w] bit b = live(e, 64w + b), W = ceil(R/64), bits at
+ * or beyond R are 0; e is the canonical arc id.  out_masks: uint64[m*W],
+ * device or host memory.  Exposes the snapshot definition for checking. */
+sg_status sg_live_masks(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, void *stream,
+                        uint64_t *out_masks);
+
+/* Canonical CSR of g into caller buffers (host or device):
+ * row_ptr int64[n+1], col int32[m_canonical]. */
+sg_status sg_graph_csr(const sg_graph *g, void *stream, int64_t *row_ptr, int32_t *col);
+
+/* Free a graph handle (NULL is a no-op).  Waits for the device. */
+void sg_free_graph(sg_graph *g);
+
+/* Message describing the last failure on this thread ("" if none). */
+const char *sg_last_error(void);
+
+/* Library version string. */
+const char *sg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_H */

@@ -1,0 +1,662 @@
+// sg_host.cu -- host side of the C ABI: errors, device memory hooks, graph
+// loading (canonicalisation, CSC, WIC thresholds) and the selection driver.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "sg_internal.cuh"
+
+namespace sgi {
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local char g_err[512] = "";
+}
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+// ------------------------------------------------------------------ memory
+namespace {
+sg_alloc_fn g_alloc = nullptr;
+sg_release_fn g_release = nullptr;
+void *g_alloc_ctx = nullptr;
+}  // namespace
+
+void *dalloc(size_t bytes, cudaStream_t st)
+{
+    if (g_alloc) return g_alloc(bytes, st, g_alloc_ctx);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dfree(void *p, size_t bytes, cudaStream_t st)
+{
+    if (!p) return;
+    if (g_release) {
+        g_release(p, bytes, st, g_alloc_ctx);
+        return;
+    }
+    cudaFreeAsync(p, st);
+}
+
+namespace {
+
+// Workers for host-side passes over rows.
+int host_threads()
+{
+    unsigned h = std::thread::hardware_concurrency();
+    if (h == 0) h = 4;
+    return (int)std::min(h, 64u);
+}
+
+template <class F>
+void parallel_rows(int64_t n, F &&f)
+{
+    const int T = host_threads();
+    if (n < 4096 || T <= 1) {
+        f(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + T - 1) / T;
+    for (int t = 0; t < T; ++t) {
+        const int64_t a = t * chunk, b = std::min(n, a + chunk);
+        if (a >= b) break;
+        th.emplace_back([&f, a, b] { f(a, b); });
+    }
+    for (auto &x : th) x.join();
+}
+
+// Canonical CSR: per row, destinations sorted ascending, repeats merged,
+// self-loops dropped (the paper treats parallel edges as one edge).  The
+// input rows are permuted in place in `col` (a private copy).
+sg_status canonicalise(int64_t n, std::vector<int64_t> &rp_in, std::vector<int32_t> &col,
+                       std::vector<int32_t> &rp_out, std::vector<int32_t> &col_out)
+{
+    std::vector<int32_t> len((size_t)n);
+    parallel_rows(n, [&](int64_t a, int64_t b) {
+        for (int64_t u = a; u < b; ++u) {
+            int32_t *r = col.data() + rp_in[u];
+            const int64_t d = rp_in[u + 1] - rp_in[u];
+            bool canon = true;
+            for (int64_t i = 0; i < d && canon; ++i)
+                if (r[i] == u || (i > 0 && r[i] <= r[i - 1])) canon = false;
+            if (!canon) std::sort(r, r + d);
+            int64_t c = 0;
+            for (int64_t i = 0; i < d; ++i)
+                if (r[i] != u && (i == 0 || r[i] != r[i - 1])) ++c;
+            len[(size_t)u] = (int32_t)c;
+        }
+    });
+    rp_out.assign((size_t)n + 1, 0);
+    for (int64_t u = 0; u < n; ++u) rp_out[(size_t)u + 1] = rp_out[(size_t)u] + len[(size_t)u];
+    col_out.resize((size_t)std::max<int64_t>(1, rp_out[(size_t)n]));
+    parallel_rows(n, [&](int64_t a, int64_t b) {
+        for (int64_t u = a; u < b; ++u) {
+            const int32_t *r = col.data() + rp_in[u];
+            const int64_t d = rp_in[u + 1] - rp_in[u];
+            int32_t *o = col_out.data() + rp_out[(size_t)u];
+            for (int64_t i = 0; i < d; ++i)
+                if (r[i] != u && (i == 0 || r[i] != r[i - 1])) *o++ = r[i];
+        }
+    });
+    return SG_OK;
+}
+
+__global__ void build_fw_kernel(long long m, const int32_t *col, const uint32_t *tmi, uint2 *fw)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int32_t y = col[e];
+        fw[e] = make_uint2((uint32_t)y, tmi[y]);
+    }
+}
+
+template <class T>
+sg_status upload(sgi::DBuf<T> &b, const T *host, size_t count, cudaStream_t st)
+{
+    SG_TRY(dbuf_alloc(b, count, st));
+    if (count) SG_CUDA_TRY(cudaMemcpyAsync(b.p, host, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    return SG_OK;
+}
+
+void free_workspace(sg_workspace &ws, cudaStream_t st)
+{
+    dbuf_free(ws.s, st);
+    dbuf_free(ws.cov, st);
+    dbuf_free(ws.nbits, st);
+    dbuf_free(ws.pendf, st);
+    dbuf_free(ws.du_m, st);
+    dbuf_free(ws.fq_a, st);
+    dbuf_free(ws.fq_b, st);
+    dbuf_free(ws.du_x, st);
+    dbuf_free(ws.big_list, st);
+    dbuf_free(ws.du_off, st);
+    dbuf_free(ws.du_cnt, st);
+    dbuf_free(ws.slot_vis, st);
+    dbuf_free(ws.slot_pend, st);
+    dbuf_free(ws.slot_qa, st);
+    dbuf_free(ws.slot_qb, st);
+    dbuf_free(ws.slot_touched, st);
+    dbuf_free(ws.ctl, st);
+    dbuf_free(ws.am_gain, st);
+    dbuf_free(ws.am_id, st);
+    dbuf_free(ws.out_seeds, st);
+    dbuf_free(ws.out_gains, st);
+    ws.wcap = 0;
+    ws.kcap = 0;
+    ws.nslots = 0;
+}
+
+void free_graph_buffers(sg_graph *g, cudaStream_t st)
+{
+    free_workspace(g->ws, st);
+    dbuf_free(g->rp, st);
+    dbuf_free(g->col, st);
+    dbuf_free(g->crp, st);
+    dbuf_free(g->cin, st);
+    dbuf_free(g->tmi, st);
+    dbuf_free(g->fw, st);
+}
+
+// Build a graph handle from a canonical CSR held on the host.
+sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> &col, cudaStream_t st,
+                      sg_graph **out)
+{
+    const int64_t m = rp[(size_t)n];
+    // CSC by a stable counting sort on destination: in-arcs of each node in
+    // increasing (source, arc id) order.
+    std::vector<int32_t> crp((size_t)n + 1, 0);
+    for (int64_t e = 0; e < m; ++e) crp[(size_t)col[(size_t)e] + 1]++;
+    for (int64_t v = 0; v < n; ++v) crp[(size_t)v + 1] += crp[(size_t)v];
+    std::vector<int2> cin((size_t)std::max<int64_t>(1, m));
+    {
+        std::vector<int32_t> fill(crp.begin(), crp.end() - 1);
+        for (int64_t u = 0; u < n; ++u)
+            for (int32_t e = rp[(size_t)u]; e < rp[(size_t)u + 1]; ++e)
+                cin[(size_t)fill[(size_t)col[(size_t)e]]++] = make_int2((int)u, e);
+    }
+    std::vector<uint32_t> tmi((size_t)n);
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t d = crp[(size_t)v + 1] - crp[(size_t)v];
+        tmi[(size_t)v] = d > 0 ? (uint32_t)((1ull << 32) / (uint64_t)d - 1ull) : 0xffffffffu;
+    }
+    sg_graph *g = new (std::nothrow) sg_graph();
+    if (!g) {
+        set_error("host allocation failed");
+        return SG_ENOMEM;
+    }
+    g->n = n;
+    g->m = m;
+    sg_status rc = SG_OK;
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("no usable CUDA device");
+        delete g;
+        return SG_ECUDA;
+    }
+    if ((rc = upload(g->rp, rp.data(), (size_t)n + 1, st)) != SG_OK ||
+        (rc = upload(g->col, col.data(), (size_t)m, st)) != SG_OK ||
+        (rc = upload(g->crp, crp.data(), (size_t)n + 1, st)) != SG_OK ||
+        (rc = upload(g->cin, cin.data(), (size_t)m, st)) != SG_OK ||
+        (rc = upload(g->tmi, tmi.data(), (size_t)n, st)) != SG_OK) {
+        free_graph_buffers(g, st);
+        delete g;
+        return rc;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        free_graph_buffers(g, st);
+        delete g;
+        return SG_ECUDA;
+    }
+    *out = g;
+    return SG_OK;
+}
+
+bool is_pageable(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeUnregistered;
+}
+
+}  // namespace
+
+GraphView view_of(const sg_graph *g)
+{
+    GraphView v;
+    v.n = (int32_t)g->n;
+    v.m = g->m;
+    v.rp = g->rp.p;
+    v.col = g->col.p;
+    v.fw = g->fw.p;
+    v.crp = g->crp.p;
+    v.cin = g->cin.p;
+    v.tmi = g->tmi.p;
+    return v;
+}
+
+sg_status ensure_wic(sg_graph *g, cudaStream_t st)
+{
+    if (g->fw.p || g->m == 0) return SG_OK;
+    SG_TRY(dbuf_alloc(g->fw, (size_t)g->m, st));
+    const int blocks = (int)std::min<long long>((g->m + 255) / 256, (long long)g->num_sms * 8);
+    build_fw_kernel<<<blocks, 256, 0, st>>>(g->m, g->col.p, g->tmi.p, g->fw.p);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
+    return SG_OK;
+}
+
+sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
+{
+    sg_workspace &ws = g->ws;
+    const int64_t n = g->n;
+    if (ws.wcap < W) {
+        free_workspace(ws, st);
+        const size_t nw = (size_t)n * (size_t)W;
+        SG_TRY(dbuf_alloc(ws.s, (size_t)n, st));
+        SG_TRY(dbuf_alloc(ws.cov, nw, st));
+        SG_TRY(dbuf_alloc(ws.nbits, nw, st));
+        SG_TRY(dbuf_alloc(ws.pendf, nw, st));
+        SG_TRY(dbuf_alloc(ws.du_m, nw, st));
+        SG_TRY(dbuf_alloc(ws.fq_a, nw, st));
+        SG_TRY(dbuf_alloc(ws.fq_b, nw, st));
+        SG_TRY(dbuf_alloc(ws.du_x, nw, st));
+        SG_TRY(dbuf_alloc(ws.big_list, nw, st));
+        SG_TRY(dbuf_alloc(ws.du_off, (size_t)W + 1, st));
+        SG_TRY(dbuf_alloc(ws.du_cnt, (size_t)W, st));
+        SG_TRY(dbuf_alloc(ws.ctl, 1, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.nbits.p, 0, ws.nbits.bytes, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.pendf.p, 0, ws.pendf.bytes, st));
+        // CTA-engine slots: dense per-slot arrays, at most ~2 GiB in total
+        const size_t per_slot = (size_t)n * (2 * sizeof(unsigned long long) + 3 * sizeof(int32_t));
+        const size_t budget = (size_t)2 << 30;
+        int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms, budget / per_slot));
+        const size_t ns = (size_t)slots * (size_t)n;
+        SG_TRY(dbuf_alloc(ws.slot_vis, ns, st));
+        SG_TRY(dbuf_alloc(ws.slot_pend, ns, st));
+        SG_TRY(dbuf_alloc(ws.slot_qa, ns, st));
+        SG_TRY(dbuf_alloc(ws.slot_qb, ns, st));
+        SG_TRY(dbuf_alloc(ws.slot_touched, ns, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.slot_vis.p, 0, ws.slot_vis.bytes, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.slot_pend.p, 0, ws.slot_pend.bytes, st));
+        ws.am_blocks = g->num_sms * 2;
+        SG_TRY(dbuf_alloc(ws.am_gain, (size_t)ws.am_blocks, st));
+        SG_TRY(dbuf_alloc(ws.am_id, (size_t)ws.am_blocks, st));
+        ws.nslots = slots;
+        ws.wcap = W;
+        ws.n = n;
+    }
+    if (ws.kcap < k) {
+        dbuf_free(ws.out_seeds, st);
+        dbuf_free(ws.out_gains, st);
+        SG_TRY(dbuf_alloc(ws.out_seeds, (size_t)k, st));
+        SG_TRY(dbuf_alloc(ws.out_gains, (size_t)k, st));
+        ws.kcap = k;
+    }
+    return SG_OK;
+}
+
+sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out)
+{
+    if (R < 1 || R >= (1 << 24)) {
+        set_error("R must satisfy 1 <= R < 2^24 (got %d)", R);
+        return SG_EINVAL;
+    }
+    Coins co;
+    co.seed = seed;
+    co.R = R;
+    co.W = (R + 63) / 64;
+    co.none_live = 0;
+    co.uic_tm1 = 0xffffffffu;
+    if (c.model == SG_UIC) {
+        if (!(c.p >= 0.0 && c.p <= 1.0)) {
+            set_error("UIC probability must lie in [0, 1]");
+            return SG_EINVAL;
+        }
+        // thr = floor(p * 2^32) in [0, 2^32]; multiplying by 2^32 is exact
+        const uint64_t thr = (uint64_t)std::floor(c.p * 4294967296.0);
+        if (thr == 0) co.none_live = 1;
+        else co.uic_tm1 = (uint32_t)(thr - 1);
+    } else if (c.model != SG_WIC) {
+        set_error("unknown cascade model %d", c.model);
+        return SG_EINVAL;
+    }
+    *out = co;
+    return SG_OK;
+}
+
+}  // namespace sgi
+
+using namespace sgi;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+sg_status check_query(const sg_graph *g, int32_t R, int32_t k)
+{
+    if (!g) {
+        set_error("graph handle is NULL");
+        return SG_EINVAL;
+    }
+    if (k < 1 || k > g->n) {
+        set_error("k must satisfy 1 <= k <= n (k=%d, n=%lld)", k, (long long)g->n);
+        return SG_EINVAL;
+    }
+    const int64_t W = ((int64_t)R + 63) / 64;
+    if (R >= 1 && g->n * W > (int64_t)INT32_MAX) {
+        set_error("n * ceil(R/64) must stay below 2^31");
+        return SG_EINVAL;
+    }
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sg_last_error(void) { return g_err; }
+
+const char *sg_version(void) { return "sg 0.1 (sm_103a)"; }
+
+sg_status sg_set_allocator(sg_alloc_fn alloc, sg_release_fn release, void *ctx)
+{
+    if ((alloc == nullptr) != (release == nullptr)) {
+        set_error("alloc and release must both be set or both be NULL");
+        return SG_EINVAL;
+    }
+    g_alloc = alloc;
+    g_release = release;
+    g_alloc_ctx = ctx;
+    return SG_OK;
+}
+
+sg_status sg_load_graph(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, int is_device_ptr,
+                        void *stream, sg_graph **out)
+{
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!out || n < 1 || n >= (int64_t)INT32_MAX || m < 0 || m >= (int64_t)INT32_MAX || !row_ptr ||
+        (m > 0 && !col)) {
+        set_error("sg_load_graph: need 1 <= n < 2^31, 0 <= m < 2^31 and non-NULL arrays");
+        return SG_EINVAL;
+    }
+    std::vector<int64_t> rp((size_t)n + 1);
+    std::vector<int32_t> c((size_t)std::max<int64_t>(1, m));
+    if (is_device_ptr) {
+        SG_CUDA_TRY(cudaMemcpyAsync(rp.data(), row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        if (m) SG_CUDA_TRY(cudaMemcpyAsync(c.data(), col, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        memcpy(rp.data(), row_ptr, rp.size() * sizeof(int64_t));
+        if (m) memcpy(c.data(), col, (size_t)m * sizeof(int32_t));
+    }
+    if (rp[0] != 0 || rp[(size_t)n] != m) {
+        set_error("sg_load_graph: row_ptr[0] must be 0 and row_ptr[n] must be m");
+        return SG_EINVAL;
+    }
+    for (int64_t u = 0; u < n; ++u)
+        if (rp[(size_t)u + 1] < rp[(size_t)u]) {
+            set_error("sg_load_graph: row_ptr decreases at row %lld", (long long)u);
+            return SG_EINVAL;
+        }
+    for (int64_t e = 0; e < m; ++e)
+        if (c[(size_t)e] < 0 || c[(size_t)e] >= n) {
+            set_error("sg_load_graph: col[%lld] = %d out of range", (long long)e, c[(size_t)e]);
+            return SG_EINVAL;
+        }
+    std::vector<int32_t> rpc, colc;
+    SG_TRY(canonicalise(n, rp, c, rpc, colc));
+    return finish_load(n, rpc, colc, st, out);
+}
+
+sg_status sg_load_graph_coo(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, int is_device_ptr,
+                            void *stream, sg_graph **out)
+{
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!out || n < 1 || n >= (int64_t)INT32_MAX || m < 0 || m >= (int64_t)INT32_MAX ||
+        (m > 0 && (!src || !dst))) {
+        set_error("sg_load_graph_coo: need 1 <= n < 2^31, 0 <= m < 2^31 and non-NULL arrays");
+        return SG_EINVAL;
+    }
+    std::vector<int32_t> s((size_t)std::max<int64_t>(1, m)), d((size_t)std::max<int64_t>(1, m));
+    if (m) {
+        if (is_device_ptr) {
+            SG_CUDA_TRY(cudaMemcpyAsync(s.data(), src, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+            SG_CUDA_TRY(cudaMemcpyAsync(d.data(), dst, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+            SG_CUDA_TRY(cudaStreamSynchronize(st));
+        } else {
+            memcpy(s.data(), src, (size_t)m * 4);
+            memcpy(d.data(), dst, (size_t)m * 4);
+        }
+    }
+    std::vector<int64_t> rp((size_t)n + 1, 0);
+    for (int64_t i = 0; i < m; ++i) {
+        if (s[(size_t)i] < 0 || s[(size_t)i] >= n || d[(size_t)i] < 0 || d[(size_t)i] >= n) {
+            set_error("sg_load_graph_coo: arc %lld has an endpoint out of range", (long long)i);
+            return SG_EINVAL;
+        }
+        rp[(size_t)s[(size_t)i] + 1]++;
+    }
+    for (int64_t u = 0; u < n; ++u) rp[(size_t)u + 1] += rp[(size_t)u];
+    std::vector<int32_t> c((size_t)std::max<int64_t>(1, m));
+    {
+        std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+        for (int64_t i = 0; i < m; ++i) c[(size_t)fill[(size_t)s[(size_t)i]]++] = d[(size_t)i];
+    }
+    std::vector<int32_t> rpc, colc;
+    SG_TRY(canonicalise(n, rp, c, rpc, colc));
+    return finish_load(n, rpc, colc, st, out);
+}
+
+sg_status sg_graph_info(const sg_graph *g, int64_t *n, int64_t *m_canonical)
+{
+    if (!g) {
+        set_error("graph handle is NULL");
+        return SG_EINVAL;
+    }
+    if (n) *n = g->n;
+    if (m_canonical) *m_canonical = g->m;
+    return SG_OK;
+}
+
+sg_status sg_graph_csr(const sg_graph *g, void *stream, int64_t *row_ptr, int32_t *col)
+{
+    clear_error();
+    if (!g || !row_ptr || (g->m > 0 && !col)) {
+        set_error("sg_graph_csr: NULL argument");
+        return SG_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> rp((size_t)g->n + 1);
+    SG_CUDA_TRY(cudaMemcpyAsync(rp.data(), g->rp.p, rp.size() * 4, cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int64_t> rp64(rp.begin(), rp.end());
+    SG_CUDA_TRY(cudaMemcpyAsync(row_ptr, rp64.data(), rp64.size() * 8, cudaMemcpyDefault, st));
+    if (g->m) SG_CUDA_TRY(cudaMemcpyAsync(col, g->col.p, (size_t)g->m * 4, cudaMemcpyDefault, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    return SG_OK;
+}
+
+void sg_free_graph(sg_graph *g)
+{
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    cudaDeviceSynchronize();
+    free_graph_buffers(g, (cudaStream_t)0);
+    cudaDeviceSynchronize();
+    delete g;
+}
+
+sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                    int32_t *out_seeds, int64_t *out_gains, sg_stats *stats)
+{
+    clear_error();
+    SG_TRY(check_query(g, R, k));
+    if (!out_seeds || !out_gains) {
+        set_error("sg_select: output pointers must be non-NULL");
+        return SG_EINVAL;
+    }
+    Coins co;
+    SG_TRY(make_coins(c, seed, R, &co));
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
+    if (model == MODEL_WIC) SG_TRY(ensure_wic(g, st));
+    SG_TRY(ensure_workspace(g, co.W, k, st));
+    sg_workspace &ws = g->ws;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (stats) {
+        for (auto &e : ev) SG_CUDA_TRY(cudaEventCreate(&e));
+        SG_CUDA_TRY(cudaEventRecord(ev[0], st));
+    }
+    const int launches0 = g_launches;
+    SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
+    SG_CUDA_TRY(cudaMemsetAsync(ws.cov.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
+    SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
+    if (stats) SG_CUDA_TRY(cudaEventRecord(ev[3], st));
+    SG_TRY(run_init_gains(g, co, model, st, stats ? ev[1] : nullptr));
+    cudaEvent_t ev_init_done = nullptr;
+    if (stats) {
+        SG_CUDA_TRY(cudaEventCreate(&ev_init_done));
+        SG_CUDA_TRY(cudaEventRecord(ev_init_done, st));
+    }
+    for (int32_t i = 0; i < k; ++i) SG_TRY(run_round(g, co, model, i, st));
+    if (stats) SG_CUDA_TRY(cudaEventRecord(ev[2], st));
+    SG_CUDA_TRY(cudaMemcpyAsync(out_seeds, ws.out_seeds.p, (size_t)k * 4, cudaMemcpyDefault, st));
+    SG_CUDA_TRY(cudaMemcpyAsync(out_gains, ws.out_gains.p, (size_t)k * 8, cudaMemcpyDefault, st));
+    if (stats) {
+        Ctl h;
+        SG_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+        memset(stats, 0, sizeof(*stats));
+        stats->init_edges = h.init_edges;
+        stats->fwd_edges = h.fwd_edges;
+        stats->rev_edges = h.rev_edges;
+        stats->init_big_tasks = h.init_big;
+        stats->rev_big_tasks = h.rev_big;
+        stats->du_entries = h.du_entries;
+        stats->status_flags = h.flags;
+        stats->kernel_launches = g_launches - launches0;
+        cudaEventElapsedTime(&stats->ms_init, ev[0], ev_init_done);
+        cudaEventElapsedTime(&stats->ms_rounds, ev_init_done, ev[2]);
+        cudaEventElapsedTime(&stats->ms_total, ev[0], ev[2]);
+        cudaEventElapsedTime(&stats->ms_init_warp, ev[3], ev[1]);
+        for (auto &e : ev) cudaEventDestroy(e);
+        cudaEventDestroy(ev_init_done);
+        if (h.flags) {
+            set_error("device-side check failed (flags 0x%x)", h.flags);
+            return SG_EINTERNAL;
+        }
+    } else if (is_pageable(out_seeds) || is_pageable(out_gains)) {
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return SG_OK;
+}
+
+sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, void *stream, int64_t *out_s,
+                        uint64_t *init_edges)
+{
+    clear_error();
+    SG_TRY(check_query(g, R, 1));
+    if (!out_s) {
+        set_error("sg_init_gains: out_s must be non-NULL");
+        return SG_EINVAL;
+    }
+    Coins co;
+    SG_TRY(make_coins(c, seed, R, &co));
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
+    if (model == MODEL_WIC) SG_TRY(ensure_wic(g, st));
+    SG_TRY(ensure_workspace(g, co.W, 1, st));
+    sg_workspace &ws = g->ws;
+    SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
+    SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
+    SG_TRY(run_init_gains(g, co, model, st));
+    SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));
+    if (init_edges) {
+        Ctl h;
+        SG_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+        *init_edges = h.init_edges;
+    } else if (is_pageable(out_s)) {
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return SG_OK;
+}
+
+sg_status sg_live_masks(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, void *stream, uint64_t *out_masks)
+{
+    clear_error();
+    if (!g || !out_masks) {
+        set_error("sg_live_masks: NULL argument");
+        return SG_EINVAL;
+    }
+    Coins co;
+    SG_TRY(make_coins(c, seed, R, &co));
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
+    if (model == MODEL_WIC) SG_TRY(ensure_wic(g, st));
+    const size_t count = (size_t)g->m * (size_t)co.W;
+    if (count == 0) return SG_OK;
+    if (!is_pageable(out_masks)) {
+        cudaPointerAttributes at;
+        SG_CUDA_TRY(cudaPointerGetAttributes(&at, out_masks));
+        if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+            return run_live_masks(g, co, model, out_masks, st);
+    }
+    DBuf<uint64_t> tmp;
+    SG_TRY(dbuf_alloc(tmp, count, st));
+    sg_status rc = run_live_masks(g, co, model, tmp.p, st);
+    if (rc == SG_OK && cudaMemcpyAsync(out_masks, tmp.p, count * 8, cudaMemcpyDefault, st) != cudaSuccess) {
+        set_error("sg_live_masks: copy-out failed");
+        rc = SG_ECUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == SG_OK) rc = SG_ECUDA;
+    dbuf_free(tmp, st);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// sg_internal.cuh -- shared declarations of the GB300 StaticGreedy-DU library.
+//
+// Device data layout (all resident in HBM for the life of a graph handle):
+//   rp   int32[n+1]  canonical CSR row offsets (arcs sorted by (src, dst))
+//   col  int32[m]    CSR destinations; canonical arc id e = CSR position
+//   fw   uint2[m]    WIC only: (dst, thr-1) per arc, interleaved so that one
+//                    8-byte coalesced load gives both (built on first WIC use)
+//   crp  int32[n+1]  CSC row offsets (in-arcs of each node)
+//   cin  int2[m]     CSC entries (src, canonical arc id)
+//   tmi  uint32[n]   WIC threshold-1 of every in-arc of the node
+//                    (floor(2^32 / indeg) - 1; in-arcs of one node share it)
+// Per-query state (workspace, reused across calls; zero between calls):
+//   s     int64[n]        marginal gains (Algorithm 2's s_v)
+//   cov   uint64[W][n]    coverage bitsets: bit b of cov[w][v] = v is
+//                         reached from the seed set in snapshot 64w+b
+//   nbits uint64[W][n]    bits newly covered in the current round
+//   pendf uint64[W][n]    forward-DU frontier bits not yet expanded
+//   du_x / du_m [W][n]    newly covered (node, mask) list of the round
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sg.h"
+
+namespace sgi {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define SG_CUDA_TRY(call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            sgi::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                           __LINE__);                                                      \
+            return SG_ECUDA;                                                               \
+        }                                                                                  \
+    } while (0)
+
+#define SG_TRY(expr)                      \
+    do {                                  \
+        sg_status s_ = (expr);            \
+        if (s_ != SG_OK) return s_;       \
+    } while (0)
+
+// ------------------------------------------------------------------ memory
+void *dalloc(size_t bytes, cudaStream_t st);
+void dfree(void *p, size_t bytes, cudaStream_t st);
+
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t bytes = 0;
+};
+
+template <class T>
+sg_status dbuf_alloc(DBuf<T> &b, size_t count, cudaStream_t st)
+{
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    b.p = static_cast<T *>(dalloc(bytes, st));
+    if (!b.p) {
+        set_error("device allocation of %zu bytes failed", bytes);
+        return SG_ENOMEM;
+    }
+    b.bytes = bytes;
+    return SG_OK;
+}
+
+template <class T>
+void dbuf_free(DBuf<T> &b, cudaStream_t st)
+{
+    if (b.p) dfree(b.p, b.bytes, st);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// ----------------------------------------------------------- device views
+enum Model { MODEL_UIC = 0, MODEL_WIC = 1 };
+
+// Coin parameters of one query (hash-defined snapshots).
+struct Coins {
+    uint64_t seed;
+    uint32_t uic_tm1;  // UIC: thr - 1 (thr = floor(p 2^32) >= 1)
+    int32_t none_live; // UIC with thr = 0: no arc is ever live
+    int32_t R;
+    int32_t W;         // ceil(R / 64)
+};
+
+struct GraphView {
+    int32_t n;
+    int64_t m;
+    const int32_t *rp;
+    const int32_t *col;
+    const uint2 *fw;
+    const int32_t *crp;
+    const int2 *cin;
+    const uint32_t *tmi;
+};
+
+// Counters kept on the device during one call (zeroed at the start).
+struct Ctl {
+    unsigned long long init_edges;
+    unsigned long long fwd_edges;
+    unsigned long long rev_edges;
+    unsigned long long init_big;
+    unsigned long long rev_big;
+    unsigned long long du_entries;
+    unsigned long long task_next;   // dynamic task counter of the warp engine
+    unsigned long long big_next;    // dynamic task counter of the CTA engine
+    unsigned long long big_count;   // tasks queued for the CTA engine
+    unsigned int argmax_arrivals;   // argmax: blocks done
+    unsigned int fwd_arrivals;      // forward DU: blocks done
+    int32_t vstar;                  // seed chosen this round
+    int32_t flags;                  // device-side check failures (bit set)
+    long long du_total;             // entries in this round's list
+};
+
+}  // namespace sgi
+
+// Workspace owned by a graph handle and reused by every call on it.
+struct sg_workspace {
+    int64_t n = 0;
+    int32_t wcap = 0;     // words of capacity of the [W][n] arrays
+    int32_t nslots = 0;   // CTA-engine slots
+    sgi::DBuf<long long> s;
+    sgi::DBuf<unsigned long long> cov, nbits, pendf, du_m;
+    sgi::DBuf<int32_t> fq_a, fq_b, du_x, big_list;
+    sgi::DBuf<long long> du_off;    // [W+1] offsets of the round's list per word
+    sgi::DBuf<int32_t> du_cnt;      // [W] entries per word
+    sgi::DBuf<unsigned long long> slot_vis, slot_pend;
+    sgi::DBuf<int32_t> slot_qa, slot_qb, slot_touched;
+    sgi::DBuf<sgi::Ctl> ctl;
+    sgi::DBuf<long long> am_gain;   // argmax per-block partials
+    sgi::DBuf<int32_t> am_id;
+    sgi::DBuf<int32_t> out_seeds;
+    sgi::DBuf<long long> out_gains;
+    int32_t kcap = 0;
+    int32_t am_blocks = 0;
+};
+
+struct sg_graph {
+    int64_t n = 0;
+    int64_t m = 0;
+    int device = 0;
+    int num_sms = 0;
+    sgi::DBuf<int32_t> rp, col, crp;
+    sgi::DBuf<int2> cin;
+    sgi::DBuf<uint32_t> tmi;
+    sgi::DBuf<uint2> fw;      // built on first WIC query
+    sg_workspace ws;
+};
+
+namespace sgi {
+
+GraphView view_of(const sg_graph *g);
+sg_status ensure_wic(sg_graph *g, cudaStream_t st);
+sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st);
+sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out);
+
+// kernels launched by this thread since the counter was last reset
+extern thread_local int g_launches;
+
+// kernels (sg_kernels.cu); `after_warp` (may be null) is recorded right
+// after the initial-gain warp-engine launch
+sg_status run_init_gains(sg_graph *g, const Coins &co, int model, cudaStream_t st,
+                         cudaEvent_t after_warp = nullptr);
+sg_status run_round(sg_graph *g, const Coins &co, int model, int32_t round, cudaStream_t st);
+sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st);
+
+}  // namespace sgi

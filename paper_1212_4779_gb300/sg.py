@@ -1,0 +1,334 @@
+"""Python binding of the C ABI in ``include/sg.h`` (``_build/libsg.so``).
+
+Argument marshalling only: every step of the selection path runs in the
+library's CUDA kernels.  PyTorch supplies device memory (its caching
+allocator is registered as the library's allocator) and streams.  The
+module-level functions carry the C names; :class:`Graph` wraps a handle.
+
+There is no CPU fallback: if the compiled library is missing or no GPU is
+visible, every call raises :class:`SGError`.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libsg.so")
+
+SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ETIMEOUT, SG_EBUSY, SG_EINTERNAL = range(7)
+SG_UIC, SG_WIC = 0, 1
+_STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ETIMEOUT", 5: "SG_EBUSY",
+           6: "SG_EINTERNAL"}
+
+# exported entry points, as declared in include/sg.h
+EXPORTS = ("sg_set_allocator", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+           "sg_init_gains", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
+
+
+class SGError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+
+
+class sg_cascade(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("p", ctypes.c_double)]
+
+
+class sg_stats(ctypes.Structure):
+    _fields_ = [("init_edges", ctypes.c_uint64), ("fwd_edges", ctypes.c_uint64), ("rev_edges", ctypes.c_uint64),
+                ("init_big_tasks", ctypes.c_uint64), ("rev_big_tasks", ctypes.c_uint64),
+                ("du_entries", ctypes.c_uint64), ("ms_init", ctypes.c_float), ("ms_rounds", ctypes.c_float),
+                ("ms_total", ctypes.c_float), ("ms_init_warp", ctypes.c_float), ("status_flags", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+_hooks = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libsg.so`` (built by ``paper_1212_4779_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise SGError(SG_ECUDA, f"CUDA library not built: {_LIB_PATH} is missing "
+                                    "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        L = ctypes.CDLL(_LIB_PATH)
+        P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        L.sg_set_allocator.argtypes = [_ALLOC_FN, _RELEASE_FN, P]
+        L.sg_load_graph.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
+        L.sg_load_graph_coo.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
+        L.sg_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.sg_select.argtypes = [P, i32, i32, sg_cascade, u64, P, P, P, ctypes.POINTER(sg_stats)]
+        L.sg_init_gains.argtypes = [P, i32, sg_cascade, u64, P, P, ctypes.POINTER(u64)]
+        L.sg_live_masks.argtypes = [P, i32, sg_cascade, u64, P, P]
+        L.sg_graph_csr.argtypes = [P, P, P, P]
+        L.sg_free_graph.argtypes = [P]
+        L.sg_free_graph.restype = None
+        L.sg_last_error.restype = ctypes.c_char_p
+        L.sg_version.restype = ctypes.c_char_p
+        for name in ("sg_set_allocator", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+                     "sg_init_gains", "sg_live_masks", "sg_graph_csr"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(rc):
+    if rc != SG_OK:
+        raise SGError(rc, lib().sg_last_error().decode(errors="replace"))
+
+
+def _require_gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise SGError(SG_ECUDA, "no CUDA device visible; the library has no CPU path")
+    return torch
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through PyTorch's caching
+    allocator (on by default once a GPU call is made)."""
+    global _hooks
+    L = lib()
+    if not enable:
+        _check(L.sg_set_allocator(_ALLOC_FN(), _RELEASE_FN(), None))
+        _hooks = None
+        return
+    torch = _require_gpu()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:  # noqa: BLE001 - reported to C as NULL (SG_ENOMEM)
+            return None
+
+    def _release(ptr, nbytes, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:  # noqa: BLE001
+            pass
+
+    hooks = (_ALLOC_FN(_alloc), _RELEASE_FN(_release))
+    _check(L.sg_set_allocator(hooks[0], hooks[1], None))
+    _hooks = hooks
+
+
+def _ensure_ready():
+    torch = _require_gpu()
+    if _hooks is None and os.environ.get("SG_TORCH_ALLOC", "1") != "0":
+        use_torch_allocator(True)
+    return torch
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _addr(a):
+    """(address, is_device) of a numpy array or torch tensor (contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr(), int(a.is_cuda)
+
+
+def _cascade(model, p):
+    m = {"uic": SG_UIC, "wic": SG_WIC, SG_UIC: SG_UIC, SG_WIC: SG_WIC}[model]
+    return sg_cascade(m, float(p))
+
+
+# ------------------------------------------------------------- C-named calls
+
+
+def sg_version() -> str:
+    return lib().sg_version().decode()
+
+
+def sg_last_error() -> str:
+    return lib().sg_last_error().decode(errors="replace")
+
+
+def sg_set_allocator(alloc=None, release=None):
+    """Install Python callables ``alloc(nbytes, stream) -> int`` and
+    ``release(ptr, nbytes, stream)`` as the device allocator; with no
+    arguments restore the library default (cudaMallocAsync)."""
+    global _hooks
+    if alloc is None and release is None:
+        _check(lib().sg_set_allocator(_ALLOC_FN(), _RELEASE_FN(), None))
+        _hooks = None
+        return
+    hooks = (_ALLOC_FN(lambda nb, st, ctx: alloc(int(nb), int(st or 0))),
+             _RELEASE_FN(lambda ptr, nb, st, ctx: release(int(ptr), int(nb), int(st or 0))))
+    _check(lib().sg_set_allocator(hooks[0], hooks[1], None))
+    _hooks = hooks
+
+
+def sg_load_graph(n, m, row_ptr, col, stream=None):
+    """CSR load; ``row_ptr`` int64[n+1] and ``col`` int32[m] as numpy arrays
+    or torch tensors (host or device).  Returns the opaque handle."""
+    _ensure_ready()
+    rp_a, rp_dev = _addr(row_ptr)
+    col_a, col_dev = _addr(col)
+    if rp_dev != col_dev:
+        raise ValueError("row_ptr and col must both be host or both be device memory")
+    h = ctypes.c_void_p()
+    _check(lib().sg_load_graph(int(n), int(m), ctypes.c_void_p(rp_a), ctypes.c_void_p(col_a), rp_dev,
+                               _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def sg_load_graph_coo(n, m, src, dst, stream=None):
+    _ensure_ready()
+    s_a, s_dev = _addr(src)
+    d_a, d_dev = _addr(dst)
+    if s_dev != d_dev:
+        raise ValueError("src and dst must both be host or both be device memory")
+    h = ctypes.c_void_p()
+    _check(lib().sg_load_graph_coo(int(n), int(m), ctypes.c_void_p(s_a), ctypes.c_void_p(d_a), s_dev,
+                                   _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def sg_graph_info(h):
+    n, m = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sg_graph_info(h, ctypes.byref(n), ctypes.byref(m)))
+    return n.value, m.value
+
+
+def sg_select(h, R, k, model, p, seed, out_seeds, out_gains, stream=None, stats=False):
+    """Run StaticGreedyDU; writes ``out_seeds`` (int32[k]) and ``out_gains``
+    (int64[k]) (numpy or torch, host or device).  Returns stats dict or None."""
+    st = sg_stats() if stats else None
+    _check(lib().sg_select(h, int(R), int(k), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                           _stream_ptr(stream), ctypes.c_void_p(_addr(out_seeds)[0]),
+                           ctypes.c_void_p(_addr(out_gains)[0]), ctypes.byref(st) if stats else None))
+    return st.as_dict() if stats else None
+
+
+def sg_init_gains(h, R, model, p, seed, out_s, stream=None, want_edges=False):
+    ed = ctypes.c_uint64(0)
+    _check(lib().sg_init_gains(h, int(R), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                               _stream_ptr(stream), ctypes.c_void_p(_addr(out_s)[0]),
+                               ctypes.byref(ed) if want_edges else None))
+    return ed.value if want_edges else None
+
+
+def sg_live_masks(h, R, model, p, seed, out_masks, stream=None):
+    _check(lib().sg_live_masks(h, int(R), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                               _stream_ptr(stream), ctypes.c_void_p(_addr(out_masks)[0])))
+
+
+def sg_graph_csr(h, row_ptr, col, stream=None):
+    _check(lib().sg_graph_csr(h, _stream_ptr(stream), ctypes.c_void_p(_addr(row_ptr)[0]),
+                              ctypes.c_void_p(_addr(col)[0])))
+
+
+def sg_free_graph(h):
+    if h:
+        lib().sg_free_graph(h)
+
+
+# --------------------------------------------------------------- convenience
+
+
+@dataclass
+class Selection:
+    seeds: np.ndarray
+    gains: np.ndarray
+    stats: dict | None
+
+
+class Graph:
+    """A graph resident on the GPU (wraps an ``sg_graph`` handle)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self.n, self.m = sg_graph_info(handle)
+
+    @classmethod
+    def from_coo(cls, n, src, dst, stream=None):
+        src = np.ascontiguousarray(src, dtype=np.int32) if isinstance(src, np.ndarray) else src
+        dst = np.ascontiguousarray(dst, dtype=np.int32) if isinstance(dst, np.ndarray) else dst
+        return cls(sg_load_graph_coo(n, len(src), src, dst, stream))
+
+    @classmethod
+    def from_csr(cls, n, row_ptr, col, stream=None):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64) if isinstance(row_ptr, np.ndarray) else row_ptr
+        col = np.ascontiguousarray(col, dtype=np.int32) if isinstance(col, np.ndarray) else col
+        return cls(sg_load_graph(n, len(col), row_ptr, col, stream))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def select(self, R, k, model="uic", p=0.0, seed=0, stream=None, stats=False):
+        """Seeds and integer gains (numpy, host) of StaticGreedyDU."""
+        seeds = np.zeros(k, dtype=np.int32)
+        gains = np.zeros(k, dtype=np.int64)
+        st = sg_select(self._h, R, k, model, p, seed, seeds, gains, stream, stats)
+        return Selection(seeds, gains, st)
+
+    def init_gains(self, R, model="uic", p=0.0, seed=0, stream=None):
+        s = np.zeros(self.n, dtype=np.int64)
+        edges = sg_init_gains(self._h, R, model, p, seed, s, stream, want_edges=True)
+        return s, edges
+
+    def live_masks(self, R, model="uic", p=0.0, seed=0, stream=None):
+        W = (R + 63) // 64
+        out = np.zeros((max(1, self.m), W), dtype=np.uint64)
+        sg_live_masks(self._h, R, model, p, seed, out, stream)
+        return out[: self.m]
+
+    def csr(self):
+        rp = np.zeros(self.n + 1, dtype=np.int64)
+        col = np.zeros(max(1, self.m), dtype=np.int32)
+        sg_graph_csr(self._h, rp, col)
+        return rp, col[: self.m]
+
+    def close(self):
+        if self._h:
+            sg_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

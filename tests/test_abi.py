@@ -1,0 +1,76 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry
+point that include/sg.h declares.  No GPU needed (no compute calls)."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sg_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1212_4779_gb300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("sg_load_graph", "sg_load_graph_coo", "sg_select", "sg_graph_info", "sg_free_graph",
+                 "sg_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    for name in _declared():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (sg_\w+)", out))
+    assert set(_declared()) <= exported
+
+
+def test_binding_names_match_header(libpath):
+    from paper_1212_4779_gb300 import sg
+
+    assert set(sg.EXPORTS) == set(_declared())
+    for name in sg.EXPORTS:
+        assert callable(getattr(sg, name))
+
+
+def test_library_is_built_for_sm_103a(libpath):
+    # the fatbinary section carries an sm_103a cubin (reported by the
+    # loader-independent cuobjdump listing of our own build)
+    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
+    assert "sm_103a" in out.stdout
+
+
+def test_error_strings_and_version_without_gpu(libpath):
+    from paper_1212_4779_gb300 import sg
+
+    assert "sm_103a" in sg.sg_version()
+    assert sg.lib().sg_last_error() is not None
+
+
+def test_invalid_arguments_are_rejected_without_gpu(libpath):
+    from paper_1212_4779_gb300 import sg
+
+    L = sg.lib()
+    h = ctypes.c_void_p()
+    # n < 1 and NULL arrays are refused before any device work
+    assert L.sg_load_graph(0, 0, None, None, 0, None, ctypes.byref(h)) == sg.SG_EINVAL
+    assert L.sg_load_graph_coo(5, 3, None, None, 0, None, ctypes.byref(h)) == sg.SG_EINVAL
+    assert b"n" in L.sg_last_error()
+    assert L.sg_graph_info(None, None, None) == sg.SG_EINVAL
+    assert L.sg_select(None, 10, 1, sg.sg_cascade(0, 0.1), 1, None, None, None, None) == sg.SG_EINVAL
+    L.sg_free_graph(None)

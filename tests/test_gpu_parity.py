@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Every comparison is exact: coins, canonical CSR, initial gains, seeds,
+integer gains and the implementation-independent snapshot-edge counters
+are integers, so the tolerance is zero."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1212_4779_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session")
+def sg():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1212_4779_gb300 import sg as _sg
+
+    return _sg
+
+
+def _both(sg, n, s, d, model, p):
+    return sg.Graph.from_coo(n, s, d), oracle.Graph(n, s, d, model, p)
+
+
+# ------------------------------------------------------------------- coins
+
+
+@pytest.mark.parametrize("gen,model,p,R,seed", [
+    (lambda: inputs.er_directed(500, 3000, 1), "uic", 0.1, 100, 1),
+    (lambda: inputs.chung_lu_undirected(800, 3000, 2.5, 7.0, 2), "wic", 0.0, 130, 7),
+    (lambda: inputs.random_small(40, 500, 3, loops_and_dups=True), "uic", 0.5, 64, 2**63 + 5),
+    (lambda: inputs.er_directed(300, 900, 4), "uic", 1.0, 1, 9),
+    (lambda: inputs.er_directed(300, 900, 4), "uic", 0.0, 70, 9),
+])
+def test_live_masks_bit_exact(sg, gen, model, p, R, seed):
+    n, s, d = gen()
+    g, o = _both(sg, n, s, d, model, p)
+    assert g.m == o.m
+    got = g.live_masks(R, model, p, seed)
+    want = o.live_masks(R, seed)
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)
+
+
+def test_canonical_csr_matches_oracle(sg):
+    for seed in range(3):
+        n, s, d = inputs.random_small(50, 900, seed, loops_and_dups=True)
+        g, o = _both(sg, n, s, d, "uic", 0.3)
+        rp, col = g.csr()
+        assert np.array_equal(rp, o.rp)
+        assert np.array_equal(col, o.col[: o.m])
+
+
+def test_csr_input_is_canonicalised(sg):
+    n, s, d = inputs.random_small(60, 700, 11, loops_and_dups=True)
+    order = np.argsort(s, kind="stable")
+    s2, d2 = s[order], d[order]
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, s2.astype(np.int64) + 1, 1)
+    rp = np.cumsum(rp)
+    g = sg.Graph.from_csr(n, rp, d2)
+    o = oracle.Graph(n, s, d, "wic")
+    rpg, colg = g.csr()
+    assert np.array_equal(rpg, o.rp) and np.array_equal(colg, o.col[: o.m])
+    res = g.select(70, 5, "wic", 0.0, 3)
+    ref = o.select(70, 5, 3, mode=oracle.DU)
+    assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+
+
+# ----------------------------------------------------------- initial gains
+
+
+INIT_CASES = [
+    ("er2k_uic0.1", None),
+    ("cl15k_uic0.01", None),
+    ("cl15k_wic", None),
+    ("cl15k_wic", 1),
+    ("cl15k_wic", 65),
+    ("er2k_uic0.1", 200),
+]
+
+
+@pytest.mark.parametrize("name,R", INIT_CASES)
+def test_init_gains_match_oracle(sg, name, R):
+    wl = inputs.workload(name)
+    R = R or wl.R
+    n, s, d = wl.graph()
+    g, o = _both(sg, n, s, d, wl.model, wl.p)
+    got, ed = g.init_gains(R, wl.model, wl.p, wl.seed)
+    want, ed_want = o.init_gains(R, wl.seed)
+    assert np.array_equal(got, want)
+    assert ed == ed_want
+
+
+def test_big_tasks_take_the_cta_engine_and_agree(sg):
+    """High-probability cascade: most sources reach hundreds of nodes per
+    64-snapshot word, so the warp engine hands them to the CTA engine."""
+    n, s, d = inputs.chung_lu_undirected(3000, 12000, 2.5, 8.0, 31)
+    g, o = _both(sg, n, s, d, "uic", 0.3)
+    res = g.select(96, 8, "uic", 0.3, 4, stats=True)
+    ref = o.select(96, 8, 4, mode=oracle.DU)
+    assert res.stats["init_big_tasks"] > 0
+    assert np.array_equal(res.seeds, ref["seeds"])
+    assert np.array_equal(res.gains, ref["gains"])
+    assert [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]] == list(map(int, ref["counters"]))
+
+
+# ---------------------------------------------------------- full selection
+
+
+@pytest.mark.parametrize("name", ["er2k_uic0.1", "cl15k_uic0.01", "cl15k_wic"])
+def test_select_matches_oracle_on_workloads(sg, name):
+    wl = inputs.workload(name)
+    n, s, d = wl.graph()
+    g, o = _both(sg, n, s, d, wl.model, wl.p)
+    res = g.select(wl.R, wl.k, wl.model, wl.p, wl.seed, stats=True)
+    ref = o.select(wl.R, wl.k, wl.seed, mode=oracle.DU)
+    assert np.array_equal(res.seeds, ref["seeds"])
+    assert np.array_equal(res.gains, ref["gains"])
+    got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+    assert got == [int(x) for x in ref["counters"]]
+    assert res.stats["status_flags"] == 0
+
+
+EDGE_CASES = [
+    # (label, graph, model, p, R, k)
+    ("single_node", lambda: (1, np.zeros(0, np.int32), np.zeros(0, np.int32)), "uic", 0.5, 10, 1),
+    ("no_arcs", lambda: (7, np.zeros(0, np.int32), np.zeros(0, np.int32)), "wic", 0.0, 70, 7),
+    ("p0", lambda: inputs.er_directed(100, 500, 5), "uic", 0.0, 33, 6),
+    ("p1_path", lambda: inputs.path_graph(40), "uic", 1.0, 64, 5),
+    ("p1_star", lambda: inputs.out_star(300, centre=17), "uic", 1.0, 65, 4),
+    ("k_equals_n", lambda: inputs.random_small(25, 80, 6), "uic", 0.4, 129, 25),
+    ("R1", lambda: inputs.er_directed(200, 1000, 7), "uic", 0.2, 1, 10),
+    ("R64", lambda: inputs.er_directed(200, 1000, 7), "wic", 0.0, 64, 10),
+    ("loops_dups", lambda: inputs.random_small(80, 1500, 8, loops_and_dups=True), "wic", 0.0, 100, 12),
+    ("two_trees", lambda: (50, np.r_[inputs.out_tree(20, 2)[1], inputs.out_tree(30, 1)[1] + 20],
+                           np.r_[inputs.out_tree(20, 2)[2], inputs.out_tree(30, 1)[2] + 20]), "uic", 1.0, 3, 3),
+]
+
+
+@pytest.mark.parametrize("label,gen,model,p,R,k", EDGE_CASES, ids=[c[0] for c in EDGE_CASES])
+def test_select_edge_cases(sg, label, gen, model, p, R, k):
+    n, s, d = gen()
+    g, o = _both(sg, n, s, d, model, p)
+    res = g.select(R, k, model, p, 12345, stats=True)
+    ref = o.select(R, k, 12345, mode=oracle.DU)
+    assert np.array_equal(res.seeds, ref["seeds"]), label
+    assert np.array_equal(res.gains, ref["gains"]), label
+    got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+    assert got == [int(x) for x in ref["counters"]], label
+
+
+def test_workspace_reuse_across_queries(sg):
+    n, s, d = inputs.chung_lu_undirected(2000, 8000, 2.5, 8.0, 12)
+    g = sg.Graph.from_coo(n, s, d)
+    queries = [("wic", 0.0, 100, 10, 1), ("uic", 0.05, 256, 20, 2), ("uic", 0.02, 64, 5, 3), ("wic", 0.0, 130, 15, 4)]
+    for model, p, R, k, seed in queries + queries[::-1]:
+        res = g.select(R, k, model, p, seed)
+        ref = oracle.Graph(n, s, d, model, p).select(R, k, seed, mode=oracle.DU)
+        assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+
+
+def test_device_outputs_and_stream(sg):
+    import torch
+
+    wl = inputs.workload("er2k_uic0.1")
+    n, s, d = wl.graph()
+    g = sg.Graph.from_coo(n, s, d)
+    st = torch.cuda.Stream()
+    seeds = torch.zeros(wl.k, dtype=torch.int32, device="cuda")
+    gains = torch.zeros(wl.k, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(st):
+        sg.sg_select(g.handle, wl.R, wl.k, wl.model, wl.p, wl.seed, seeds, gains, stream=st)
+    st.synchronize()
+    ref = oracle.Graph(n, s, d, wl.model, wl.p).select(wl.R, wl.k, wl.seed, mode=oracle.DU)
+    assert np.array_equal(seeds.cpu().numpy(), ref["seeds"])
+    assert np.array_equal(gains.cpu().numpy(), ref["gains"])
+
+
+def test_invalid_queries_are_rejected(sg):
+    n, s, d = inputs.er_directed(50, 200, 3)
+    g = sg.Graph.from_coo(n, s, d)
+    for R, k, model, p in [(0, 1, "uic", 0.1), (1 << 24, 1, "uic", 0.1), (10, 0, "uic", 0.1), (10, 51, "uic", 0.1),
+                           (10, 1, "uic", 1.5), (10, 1, "uic", float("nan")), (10, 1, "uic", -0.1)]:
+        with pytest.raises(sg.SGError) as ei:
+            g.select(R, k, model, p, 1)
+        assert ei.value.status == sg.SG_EINVAL
+    with pytest.raises(sg.SGError):
+        sg.Graph.from_coo(5, np.array([0, 7], np.int32), np.array([1, 2], np.int32))
+
+
+# ------------------------------------------------- full size (R-MAT scale 20)
+
+
+@pytest.fixture(scope="module")
+def rmat20(sg):
+    wl = inputs.workload("rmat20_wic")
+    n, s, d = wl.graph()
+    g = sg.Graph.from_coo(n, s, d)
+    o = oracle.Graph(n, s, d, wl.model, wl.p)
+    res = g.select(wl.R, wl.k, wl.model, wl.p, wl.seed, stats=True)
+    return wl, g, o, res
+
+
+def test_rmat20_sampled_initial_gains(sg, rmat20):
+    wl, g, o, res = rmat20
+    s_gpu, _ = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
+    rng = np.random.default_rng(20)
+    outdeg = np.diff(o.rp)
+    hubs = np.argsort(-outdeg)[:16]
+    sample = np.unique(np.r_[rng.choice(g.n, 48, replace=False), hubs, res.seeds[:4]]).astype(np.int32)
+    want, _ = o.reach_sums(wl.R, wl.seed, sample)
+    assert np.array_equal(s_gpu[sample], want)
+    # the first seed is the argmax (lowest id on ties) of the initial gains
+    assert res.seeds[0] == int(np.argmax(s_gpu)) and res.gains[0] == s_gpu.max()
+
+
+def test_rmat20_gains_are_exact_marginals(sg, rmat20):
+    wl, g, o, res = rmat20
+    gains = res.gains
+    assert np.all(np.diff(gains) <= 0)
+    assert len(set(res.seeds.tolist())) == wl.k
+    assert res.stats["status_flags"] == 0
+    prev = 0
+    for i in (1, 2, 5, 10, 25, 50):
+        f = o.spread(wl.R, wl.seed, res.seeds[:i])
+        assert f == int(gains[:i].sum()), i
+        prev = f
+    assert prev == int(gains.sum())
+
+
+def test_rmat20_greedy_choice_beats_sampled_candidates(sg, rmat20):
+    wl, g, o, res = rmat20
+    rng = np.random.default_rng(7)
+    for i in (0, 1, 9, 30):
+        S = res.seeds[:i]
+        fS = o.spread(wl.R, wl.seed, S) if i else 0
+        for u in rng.choice(g.n, 12, replace=False):
+            if u in res.seeds[: i + 1]:
+                continue
+            du = o.spread(wl.R, wl.seed, np.append(S, u)) - fS
+            assert du < res.gains[i] or (du == res.gains[i] and u > res.seeds[i])
