@@ -247,7 +247,7 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
         t_steps.append(ev0.elapsed_time(ev1))
-        t_warp.append(st["ms_init_warp"])
+        t_warp.append(st["ms_init_tier1"])
         edges.append(st["init_edges"] + st["fwd_edges"] + st["rev_edges"])
         launches += st["kernel_launches"]
         st_last = st
@@ -286,9 +286,12 @@ def main():
         "config": {"workload": wl_desc(wl), "n": n, "m": int(g.m), "R": wl.R, "k": wl.k,
                    "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
         "snapshot_edges_per_step": edges_step,
-        "phase_ms": {"init": st_last["ms_init"], "init_warp_engine": st_last["ms_init_warp"],
-                     "rounds": st_last["ms_rounds"]},
-        "big_tasks": {"init": st_last["init_big_tasks"], "reverse": st_last["rev_big_tasks"]},
+        "phase_ms": {"index": st_last["ms_index"], "init": st_last["ms_init"],
+                     "init_tier1": st_last["ms_init_tier1"], "rounds": st_last["ms_rounds"],
+                     "rounds_argmax_fwd": st_last["ms_fwd"], "total": st_last["ms_total"]},
+        "tiers": {k: st_last[k] for k in ("init_tier2_tasks", "init_tier3_tasks", "rev_tier2_tasks",
+                                          "rev_tier3_tasks", "rev_tasks", "du_entries")},
+        "edges": {k: st_last[k] for k in ("init_edges", "fwd_edges", "rev_edges")},
         "gpu_launches": launches,
         "roofline": roofline,
         "cpu_baseline": cpu,

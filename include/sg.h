@@ -61,20 +61,28 @@ typedef struct {
  *   init_edges = sum over (v, r) and u in R(G'_r, v) of outdeg(u)
  *   fwd_edges  = sum over newly covered (u, r) of outdeg(u)
  *   rev_edges  = sum over newly covered (w, r) and u in U(G'_r, w) of indeg(u)
- * (outdeg / indeg of the canonical graph, live or not). */
+ * (outdeg / indeg of the canonical graph, live or not).  The other fields
+ * describe how this implementation ran (tiers, task counts, device times). */
 typedef struct {
     uint64_t init_edges;
     uint64_t fwd_edges;
     uint64_t rev_edges;
-    uint64_t init_big_tasks;  /* initial-gain BFS tasks that took the CTA path */
-    uint64_t rev_big_tasks;   /* reverse-BFS tasks that took the CTA path */
-    uint64_t du_entries;      /* (node, 64-snapshot word) pairs newly covered, all rounds */
-    float ms_init;            /* device time of the initial gains */
-    float ms_rounds;          /* device time of the k selection rounds */
-    float ms_total;           /* device time of the whole call */
-    float ms_init_warp;       /* device time of the initial-gain warp-engine launch */
-    int32_t status_flags;     /* nonzero: device-side check failed */
-    int32_t kernel_launches;  /* kernels this call launched */
+    uint64_t init_tier2_tasks;  /* initial-gain tasks that outgrew the shared-memory table */
+    uint64_t init_tier3_tasks;  /* ... and the global-memory table */
+    uint64_t rev_tier2_tasks;   /* same for reverse (dynamic-update) tasks */
+    uint64_t rev_tier3_tasks;
+    uint64_t rev_tasks;         /* reverse tasks (one snapshot, <= 64 targets), all rounds */
+    uint64_t du_entries;        /* (node, 64-snapshot word) pairs newly covered, all rounds */
+    float ms_index;             /* device time building the heavy-row live index */
+    float ms_init;              /* device time of the initial gains (index included) */
+    float ms_init_tier1;        /* device time of the initial-gain tier-1 launch */
+    float ms_rounds;            /* device time of the k selection rounds */
+    float ms_fwd;               /* ... of which argmax + forward update, summed */
+    float ms_total;             /* device time of the whole call */
+    int32_t status_flags;       /* nonzero: device-side check failed */
+    int32_t kernel_launches;    /* kernels this call launched */
+    int32_t heavy_index;        /* 1 if the heavy-row live index was used */
+    int32_t reserved;
 } sg_stats;
 
 /* Opaque graph handle; owns its device memory until sg_free_graph. */
@@ -102,6 +110,21 @@ sg_status sg_set_allocator(sg_alloc_fn alloc, sg_release_fn release, void *ctx);
  * to *out only on SG_OK. */
 sg_status sg_load_graph(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
                         int is_device_ptr, void *stream, sg_graph **out);
+
+/* Degree at or above which a row gets a per-query live index in graphs
+ * loaded after this call: for each such row and 64-snapshot word the
+ * nonzero live masks of its arcs are computed once per query (from the
+ * same hash) instead of on every expansion.  0 disables the index; the
+ * default is 64.  Results do not depend on it.  Errors: SG_EINVAL if < 0. */
+sg_status sg_set_heavy_threshold(int32_t min_degree);
+
+/* Traversal-engine limits: a task whose visited set grows past tier1_keys
+ * nodes leaves the per-warp shared-memory table for a per-warp global
+ * table, and past tier2_keys nodes for a whole-block engine with dense
+ * arrays.  Values are clamped to 256 and 8192 (the defaults).  A tuning and
+ * testing knob: results do not depend on it.  Applies to later calls.
+ * Errors: SG_EINVAL if either is < 1. */
+sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys);
 
 /* Same as sg_load_graph from an arc list src[i] -> dst[i], i < m.
  * src/dst are host memory when is_device_ptr is 0, device memory when 1. */

@@ -33,6 +33,7 @@ void clear_error() { g_err[0] = 0; }
 
 // ------------------------------------------------------------------ memory
 namespace {
+int g_heavy_min_deg = 64;
 sg_alloc_fn g_alloc = nullptr;
 sg_release_fn g_release = nullptr;
 void *g_alloc_ctx = nullptr;
@@ -150,9 +151,22 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.fq_a, st);
     dbuf_free(ws.fq_b, st);
     dbuf_free(ws.du_x, st);
-    dbuf_free(ws.big_list, st);
-    dbuf_free(ws.du_off, st);
+    dbuf_free(ws.list1, st);
+    dbuf_free(ws.list2, st);
+    dbuf_free(ws.tl, st);
+    dbuf_free(ws.toff, st);
+    dbuf_free(ws.coff, st);
+    dbuf_free(ws.tcnt, st);
     dbuf_free(ws.du_cnt, st);
+    dbuf_free(ws.t2_tab, st);
+    dbuf_free(ws.hcnt_out, st);
+    dbuf_free(ws.hnbr_out, st);
+    dbuf_free(ws.hmask_out, st);
+    dbuf_free(ws.hcnt_in, st);
+    dbuf_free(ws.hnbr_in, st);
+    dbuf_free(ws.hmask_in, st);
+    ws.hw_cap = 0;
+    ws.t2_warps = 0;
     dbuf_free(ws.slot_vis, st);
     dbuf_free(ws.slot_pend, st);
     dbuf_free(ws.slot_qa, st);
@@ -177,6 +191,39 @@ void free_graph_buffers(sg_graph *g, cudaStream_t st)
     dbuf_free(g->cin, st);
     dbuf_free(g->tmi, st);
     dbuf_free(g->fw, st);
+    dbuf_free(g->hid_out, st);
+    dbuf_free(g->hrow_out, st);
+    dbuf_free(g->hpref_out, st);
+    dbuf_free(g->hcpref_out, st);
+    dbuf_free(g->hid_in, st);
+    dbuf_free(g->hrow_in, st);
+    dbuf_free(g->hpref_in, st);
+    dbuf_free(g->hcpref_in, st);
+}
+
+// Heavy rows of one direction (row offsets rp): degree >= min_deg.
+struct HeavyHost {
+    std::vector<int32_t> hid, hrow, hcpref;
+    std::vector<long long> hpref;
+};
+
+HeavyHost heavy_rows(int64_t n, const std::vector<int32_t> &rp, int min_deg)
+{
+    HeavyHost h;
+    h.hid.assign((size_t)n, -1);
+    h.hpref.push_back(0);
+    h.hcpref.push_back(0);
+    if (min_deg <= 0) return h;
+    for (int64_t v = 0; v < n; ++v) {
+        const int d = rp[(size_t)v + 1] - rp[(size_t)v];
+        if (d >= min_deg) {
+            h.hid[(size_t)v] = (int32_t)h.hrow.size();
+            h.hrow.push_back((int32_t)v);
+            h.hpref.push_back(h.hpref.back() + d);
+            h.hcpref.push_back(h.hcpref.back() + (d + 1023) / 1024);
+        }
+    }
+    return h;
 }
 
 // Build a graph handle from a canonical CSR held on the host.
@@ -216,11 +263,26 @@ sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> 
         delete g;
         return SG_ECUDA;
     }
+    const HeavyHost ho = heavy_rows(n, rp, g_heavy_min_deg);
+    const HeavyHost hi = heavy_rows(n, crp, g_heavy_min_deg);
+    g->heavy_min_deg = g_heavy_min_deg;
+    g->nh_out = (int32_t)ho.hrow.size();
+    g->nh_in = (int32_t)hi.hrow.size();
+    g->hsum_out = ho.hpref.back();
+    g->hsum_in = hi.hpref.back();
     if ((rc = upload(g->rp, rp.data(), (size_t)n + 1, st)) != SG_OK ||
         (rc = upload(g->col, col.data(), (size_t)m, st)) != SG_OK ||
         (rc = upload(g->crp, crp.data(), (size_t)n + 1, st)) != SG_OK ||
         (rc = upload(g->cin, cin.data(), (size_t)m, st)) != SG_OK ||
-        (rc = upload(g->tmi, tmi.data(), (size_t)n, st)) != SG_OK) {
+        (rc = upload(g->tmi, tmi.data(), (size_t)n, st)) != SG_OK ||
+        (rc = upload(g->hid_out, ho.hid.data(), ho.hid.size(), st)) != SG_OK ||
+        (rc = upload(g->hrow_out, ho.hrow.data(), ho.hrow.size(), st)) != SG_OK ||
+        (rc = upload(g->hpref_out, ho.hpref.data(), ho.hpref.size(), st)) != SG_OK ||
+        (rc = upload(g->hcpref_out, ho.hcpref.data(), ho.hcpref.size(), st)) != SG_OK ||
+        (rc = upload(g->hid_in, hi.hid.data(), hi.hid.size(), st)) != SG_OK ||
+        (rc = upload(g->hrow_in, hi.hrow.data(), hi.hrow.size(), st)) != SG_OK ||
+        (rc = upload(g->hpref_in, hi.hpref.data(), hi.hpref.size(), st)) != SG_OK ||
+        (rc = upload(g->hcpref_in, hi.hcpref.data(), hi.hcpref.size(), st)) != SG_OK) {
         free_graph_buffers(g, st);
         delete g;
         return rc;
@@ -247,7 +309,7 @@ bool is_pageable(const void *p)
 
 }  // namespace
 
-GraphView view_of(const sg_graph *g)
+GraphView view_of(const sg_graph *g, int heavy_on)
 {
     GraphView v;
     v.n = (int32_t)g->n;
@@ -258,7 +320,41 @@ GraphView view_of(const sg_graph *g)
     v.crp = g->crp.p;
     v.cin = g->cin.p;
     v.tmi = g->tmi.p;
+    const sg_workspace &ws = g->ws;
+    v.hout = HeavyView{g->hid_out.p, g->hpref_out.p, ws.hcnt_out.p, ws.hnbr_out.p, ws.hmask_out.p};
+    v.hin = HeavyView{g->hid_in.p, g->hpref_in.p, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p};
+    v.heavy_on = heavy_on;
     return v;
+}
+
+// The heavy-row index reserves (sum of heavy degrees) x W entries of 12 B
+// per direction; it is used while that stays within 8 GiB.
+bool heavy_index_enabled(const sg_graph *g, int32_t W)
+{
+    if (g->heavy_min_deg <= 0 || (g->nh_out == 0 && g->nh_in == 0)) return false;
+    const double bytes = (double)(g->hsum_out + g->hsum_in) * (double)W * 12.0;
+    return bytes <= 8.0 * (double)(1ull << 30);
+}
+
+sg_status ensure_heavy_index(sg_graph *g, int32_t W, cudaStream_t st)
+{
+    sg_workspace &ws = g->ws;
+    if (ws.hw_cap >= W) return SG_OK;
+    dbuf_free(ws.hcnt_out, st);
+    dbuf_free(ws.hnbr_out, st);
+    dbuf_free(ws.hmask_out, st);
+    dbuf_free(ws.hcnt_in, st);
+    dbuf_free(ws.hnbr_in, st);
+    dbuf_free(ws.hmask_in, st);
+    ws.hw_cap = 0;
+    SG_TRY(dbuf_alloc(ws.hcnt_out, (size_t)g->nh_out * W, st));
+    SG_TRY(dbuf_alloc(ws.hnbr_out, (size_t)g->hsum_out * W, st));
+    SG_TRY(dbuf_alloc(ws.hmask_out, (size_t)g->hsum_out * W, st));
+    SG_TRY(dbuf_alloc(ws.hcnt_in, (size_t)g->nh_in * W, st));
+    SG_TRY(dbuf_alloc(ws.hnbr_in, (size_t)g->hsum_in * W, st));
+    SG_TRY(dbuf_alloc(ws.hmask_in, (size_t)g->hsum_in * W, st));
+    ws.hw_cap = W;
+    return SG_OK;
 }
 
 sg_status ensure_wic(sg_graph *g, cudaStream_t st)
@@ -287,10 +383,19 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
         SG_TRY(dbuf_alloc(ws.fq_a, nw, st));
         SG_TRY(dbuf_alloc(ws.fq_b, nw, st));
         SG_TRY(dbuf_alloc(ws.du_x, nw, st));
-        SG_TRY(dbuf_alloc(ws.big_list, nw, st));
-        SG_TRY(dbuf_alloc(ws.du_off, (size_t)W + 1, st));
+        const size_t ltasks = nw + (size_t)64 * W + 64;
+        SG_TRY(dbuf_alloc(ws.list1, ltasks, st));
+        SG_TRY(dbuf_alloc(ws.list2, ltasks, st));
+        SG_TRY(dbuf_alloc(ws.tl, nw * 64, st));
+        SG_TRY(dbuf_alloc(ws.toff, (size_t)64 * W, st));
+        SG_TRY(dbuf_alloc(ws.coff, (size_t)64 * W + 1, st));
+        SG_TRY(dbuf_alloc(ws.tcnt, (size_t)64 * W, st));
         SG_TRY(dbuf_alloc(ws.du_cnt, (size_t)W, st));
         SG_TRY(dbuf_alloc(ws.ctl, 1, st));
+        // tier-2 warp tables (global memory), cleared once, left clean by every task
+        ws.t2_warps = g->num_sms * 2 * 4;
+        SG_TRY(dbuf_alloc(ws.t2_tab, (size_t)ws.t2_warps * t2_table_bytes(), st));
+        SG_TRY(run_t2_clear(ws.t2_tab.p, ws.t2_warps, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.nbits.p, 0, ws.nbits.bytes, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.pendf.p, 0, ws.pendf.bytes, st));
         // CTA-engine slots: dense per-slot arrays, at most ~2 GiB in total
@@ -382,7 +487,11 @@ sg_status check_query(const sg_graph *g, int32_t R, int32_t k)
         return SG_EINVAL;
     }
     const int64_t W = ((int64_t)R + 63) / 64;
-    if (R >= 1 && g->n * W > (int64_t)INT32_MAX) {
+    if (R >= 1 && (g->n + 1) * W * 64 > (int64_t)INT32_MAX * 16) {
+        set_error("n * ceil(R/64) too large for the per-snapshot target lists");
+        return SG_EINVAL;
+    }
+    if (R >= 1 && g->n * W + 64 * W > (int64_t)INT32_MAX) {
         set_error("n * ceil(R/64) must stay below 2^31");
         return SG_EINVAL;
     }
@@ -396,6 +505,27 @@ extern "C" {
 const char *sg_last_error(void) { return g_err; }
 
 const char *sg_version(void) { return "sg 0.1 (sm_103a)"; }
+
+sg_status sg_set_heavy_threshold(int32_t min_degree)
+{
+    if (min_degree < 0) {
+        set_error("heavy threshold must be >= 0");
+        return SG_EINVAL;
+    }
+    g_heavy_min_deg = min_degree;
+    return SG_OK;
+}
+
+sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys)
+{
+    if (tier1_keys < 1 || tier2_keys < 1) {
+        set_error("engine limits must be >= 1");
+        return SG_EINVAL;
+    }
+    g_tier_limit[0] = tier1_keys;
+    g_tier_limit[1] = tier2_keys;
+    return SG_OK;
+}
 
 sg_status sg_set_allocator(sg_alloc_fn alloc, sg_release_fn release, void *ctx)
 {
@@ -542,27 +672,51 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
+    const int launches0 = g_launches;
     if (model == MODEL_WIC) SG_TRY(ensure_wic(g, st));
     SG_TRY(ensure_workspace(g, co.W, k, st));
+    const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
+    if (heavy_on) SG_TRY(ensure_heavy_index(g, co.W, st));
     sg_workspace &ws = g->ws;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // events: 0 start, 1 after index, 2 after init tier 1, 3 after init,
+    // 4 end; per round: after forward update
+    std::vector<cudaEvent_t> ev;
+    auto mark = [&](void) -> cudaEvent_t {
+        cudaEvent_t e = nullptr;
+        if (!stats) return nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ev.push_back(e);
+        return e;
+    };
+    struct EvGuard {
+        std::vector<cudaEvent_t> &v;
+        ~EvGuard()
+        {
+            for (auto e : v) cudaEventDestroy(e);
+        }
+    } guard{ev};
+    cudaEvent_t e_start = mark(), e_index = mark(), e_t1 = mark(), e_init = mark(), e_end = mark();
+    std::vector<cudaEvent_t> e_round(stats ? (size_t)k + 1 : 0), e_fwd(stats ? (size_t)k : 0);
     if (stats) {
-        for (auto &e : ev) SG_CUDA_TRY(cudaEventCreate(&e));
-        SG_CUDA_TRY(cudaEventRecord(ev[0], st));
+        for (auto &e : e_round) e = mark();
+        for (auto &e : e_fwd) e = mark();
+        SG_CUDA_TRY(cudaEventRecord(e_start, st));
     }
-    const int launches0 = g_launches;
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.cov.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
-    if (stats) SG_CUDA_TRY(cudaEventRecord(ev[3], st));
-    SG_TRY(run_init_gains(g, co, model, st, stats ? ev[1] : nullptr));
-    cudaEvent_t ev_init_done = nullptr;
-    if (stats) {
-        SG_CUDA_TRY(cudaEventCreate(&ev_init_done));
-        SG_CUDA_TRY(cudaEventRecord(ev_init_done, st));
+    if (heavy_on) SG_TRY(run_heavy_index(g, co, model, st));
+    if (stats) SG_CUDA_TRY(cudaEventRecord(e_index, st));
+    SG_TRY(run_init_gains(g, co, model, heavy_on, st, e_t1));
+    if (stats) SG_CUDA_TRY(cudaEventRecord(e_init, st));
+    for (int32_t i = 0; i < k; ++i) {
+        if (stats) SG_CUDA_TRY(cudaEventRecord(e_round[(size_t)i], st));
+        SG_TRY(run_round(g, co, model, heavy_on, i, st, stats ? e_fwd[(size_t)i] : nullptr));
     }
-    for (int32_t i = 0; i < k; ++i) SG_TRY(run_round(g, co, model, i, st));
-    if (stats) SG_CUDA_TRY(cudaEventRecord(ev[2], st));
+    if (stats) {
+        SG_CUDA_TRY(cudaEventRecord(e_round[(size_t)k], st));
+        SG_CUDA_TRY(cudaEventRecord(e_end, st));
+    }
     SG_CUDA_TRY(cudaMemcpyAsync(out_seeds, ws.out_seeds.p, (size_t)k * 4, cudaMemcpyDefault, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_gains, ws.out_gains.p, (size_t)k * 8, cudaMemcpyDefault, st));
     if (stats) {
@@ -573,17 +727,27 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
         stats->init_edges = h.init_edges;
         stats->fwd_edges = h.fwd_edges;
         stats->rev_edges = h.rev_edges;
-        stats->init_big_tasks = h.init_big;
-        stats->rev_big_tasks = h.rev_big;
+        stats->init_tier2_tasks = h.init_t2;
+        stats->init_tier3_tasks = h.init_t3;
+        stats->rev_tier2_tasks = h.rev_t2;
+        stats->rev_tier3_tasks = h.rev_t3;
+        stats->rev_tasks = h.rev_tasks;
         stats->du_entries = h.du_entries;
         stats->status_flags = h.flags;
         stats->kernel_launches = g_launches - launches0;
-        cudaEventElapsedTime(&stats->ms_init, ev[0], ev_init_done);
-        cudaEventElapsedTime(&stats->ms_rounds, ev_init_done, ev[2]);
-        cudaEventElapsedTime(&stats->ms_total, ev[0], ev[2]);
-        cudaEventElapsedTime(&stats->ms_init_warp, ev[3], ev[1]);
-        for (auto &e : ev) cudaEventDestroy(e);
-        cudaEventDestroy(ev_init_done);
+        stats->heavy_index = heavy_on;
+        cudaEventElapsedTime(&stats->ms_index, e_start, e_index);
+        cudaEventElapsedTime(&stats->ms_init, e_start, e_init);
+        cudaEventElapsedTime(&stats->ms_init_tier1, e_index, e_t1);
+        cudaEventElapsedTime(&stats->ms_rounds, e_init, e_end);
+        cudaEventElapsedTime(&stats->ms_total, e_start, e_end);
+        float fsum = 0.f;
+        for (int32_t i = 0; i < k; ++i) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e_round[(size_t)i], e_fwd[(size_t)i]);
+            fsum += t;
+        }
+        stats->ms_fwd = fsum;
         if (h.flags) {
             set_error("device-side check failed (flags 0x%x)", h.flags);
             return SG_EINTERNAL;
@@ -610,10 +774,13 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
     if (model == MODEL_WIC) SG_TRY(ensure_wic(g, st));
     SG_TRY(ensure_workspace(g, co.W, 1, st));
+    const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
+    if (heavy_on) SG_TRY(ensure_heavy_index(g, co.W, st));
     sg_workspace &ws = g->ws;
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
-    SG_TRY(run_init_gains(g, co, model, st));
+    if (heavy_on) SG_TRY(run_heavy_index(g, co, model, st));
+    SG_TRY(run_init_gains(g, co, model, heavy_on, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));
     if (init_edges) {
         Ctl h;

@@ -1,6 +1,6 @@
 // sg_internal.cuh -- shared declarations of the GB300 StaticGreedy-DU library.
 //
-// Device data layout (all resident in HBM for the life of a graph handle):
+// Device data layout (resident in HBM for the life of a graph handle):
 //   rp   int32[n+1]  canonical CSR row offsets (arcs sorted by (src, dst))
 //   col  int32[m]    CSR destinations; canonical arc id e = CSR position
 //   fw   uint2[m]    WIC only: (dst, thr-1) per arc, interleaved so that one
@@ -9,13 +9,21 @@
 //   cin  int2[m]     CSC entries (src, canonical arc id)
 //   tmi  uint32[n]   WIC threshold-1 of every in-arc of the node
 //                    (floor(2^32 / indeg) - 1; in-arcs of one node share it)
+//   heavy rows (degree >= heavy threshold), per direction:
+//     hid   int32[n]     ordinal of the node's heavy row, or -1
+//     hrow  int32[nh]    node of each heavy row
+//     hpref int64[nh+1]  prefix sum of heavy-row degrees
 // Per-query state (workspace, reused across calls; zero between calls):
 //   s     int64[n]        marginal gains (Algorithm 2's s_v)
 //   cov   uint64[W][n]    coverage bitsets: bit b of cov[w][v] = v is
 //                         reached from the seed set in snapshot 64w+b
 //   nbits uint64[W][n]    bits newly covered in the current round
 //   pendf uint64[W][n]    forward-DU frontier bits not yet expanded
-//   du_x / du_m [W][n]    newly covered (node, mask) list of the round
+//   du_x / du_m [W][n]    newly covered (node, mask) list of the round, per word
+//   tl    int32[W][64n]   newly covered nodes of the round, per snapshot
+//   heavy live index, per direction: for heavy row h and word w the
+//     nonzero 64-snapshot live masks of its arcs, compacted in arc order:
+//     hcnt[h*W+w] entries at hnbr/hmask[hpref[h]*W + w*deg(h) ...]
 #pragma once
 
 #include <cuda_runtime.h>
@@ -89,6 +97,15 @@ struct Coins {
     int32_t W;         // ceil(R / 64)
 };
 
+// Heavy rows of one direction and the query's live index over them.
+struct HeavyView {
+    const int32_t *hid;
+    const long long *hpref;
+    const int32_t *hcnt;
+    const int32_t *hnbr;
+    const unsigned long long *hmask;
+};
+
 struct GraphView {
     int32_t n;
     int64_t m;
@@ -98,6 +115,9 @@ struct GraphView {
     const int32_t *crp;
     const int2 *cin;
     const uint32_t *tmi;
+    HeavyView hout;  // heavy CSR rows (forward traversals)
+    HeavyView hin;   // heavy CSC rows (reverse traversals)
+    int32_t heavy_on;
 };
 
 // Counters kept on the device during one call (zeroed at the start).
@@ -105,17 +125,20 @@ struct Ctl {
     unsigned long long init_edges;
     unsigned long long fwd_edges;
     unsigned long long rev_edges;
-    unsigned long long init_big;
-    unsigned long long rev_big;
+    unsigned long long init_t2, init_t3;  // initial-gain tasks run by tier 2 / tier 3
+    unsigned long long rev_t2, rev_t3;    // reverse tasks run by tier 2 / tier 3
     unsigned long long du_entries;
-    unsigned long long task_next;   // dynamic task counter of the warp engine
-    unsigned long long big_next;    // dynamic task counter of the CTA engine
-    unsigned long long big_count;   // tasks queued for the CTA engine
-    unsigned int argmax_arrivals;   // argmax: blocks done
-    unsigned int fwd_arrivals;      // forward DU: blocks done
-    int32_t vstar;                  // seed chosen this round
-    int32_t flags;                  // device-side check failures (bit set)
-    long long du_total;             // entries in this round's list
+    unsigned long long rev_tasks;         // target-sliced reverse tasks, all rounds
+    unsigned long long t1_next;   // dynamic task counter, tier 1
+    unsigned long long l1_count;  // tasks handed from tier 1 to tier 2
+    unsigned long long l1_next;
+    unsigned long long l2_count;  // tasks handed from tier 2 to tier 3
+    unsigned long long l2_next;
+    unsigned int argmax_arrivals;
+    unsigned int fwd_arrivals;
+    int32_t vstar;
+    int32_t flags;
+    long long du_total;   // reverse tasks of the current round
 };
 
 }  // namespace sgi
@@ -124,19 +147,26 @@ struct Ctl {
 struct sg_workspace {
     int64_t n = 0;
     int32_t wcap = 0;     // words of capacity of the [W][n] arrays
-    int32_t nslots = 0;   // CTA-engine slots
+    int32_t nslots = 0;   // tier-3 (CTA engine) slots
+    int32_t t2_warps = 0; // tier-2 warp tables
     sgi::DBuf<long long> s;
     sgi::DBuf<unsigned long long> cov, nbits, pendf, du_m;
-    sgi::DBuf<int32_t> fq_a, fq_b, du_x, big_list;
-    sgi::DBuf<long long> du_off;    // [W+1] offsets of the round's list per word
-    sgi::DBuf<int32_t> du_cnt;      // [W] entries per word
+    sgi::DBuf<int32_t> fq_a, fq_b, du_x, list1, list2, tl;
+    sgi::DBuf<long long> toff, coff;     // per snapshot: target list offset, chunk-task offset [64W+1]
+    sgi::DBuf<int32_t> tcnt;             // per snapshot: newly covered count [64W]
+    sgi::DBuf<int32_t> du_cnt;           // [W] entries per word
     sgi::DBuf<unsigned long long> slot_vis, slot_pend;
     sgi::DBuf<int32_t> slot_qa, slot_qb, slot_touched;
+    sgi::DBuf<unsigned char> t2_tab;     // tier-2 global hash tables
     sgi::DBuf<sgi::Ctl> ctl;
-    sgi::DBuf<long long> am_gain;   // argmax per-block partials
+    sgi::DBuf<long long> am_gain;        // argmax per-block partials
     sgi::DBuf<int32_t> am_id;
     sgi::DBuf<int32_t> out_seeds;
     sgi::DBuf<long long> out_gains;
+    // heavy live index (per direction) for the current W
+    sgi::DBuf<int32_t> hcnt_out, hnbr_out, hcnt_in, hnbr_in;
+    sgi::DBuf<unsigned long long> hmask_out, hmask_in;
+    int32_t hw_cap = 0;   // W the heavy index was sized for
     int32_t kcap = 0;
     int32_t am_blocks = 0;
 };
@@ -150,24 +180,38 @@ struct sg_graph {
     sgi::DBuf<int2> cin;
     sgi::DBuf<uint32_t> tmi;
     sgi::DBuf<uint2> fw;      // built on first WIC query
+    // heavy rows (static)
+    int32_t heavy_min_deg = 0;
+    int32_t nh_out = 0, nh_in = 0;
+    long long hsum_out = 0, hsum_in = 0;   // sum of heavy-row degrees
+    sgi::DBuf<int32_t> hid_out, hrow_out, hid_in, hrow_in;
+    sgi::DBuf<long long> hpref_out, hpref_in;
+    sgi::DBuf<int32_t> hcpref_out, hcpref_in;  // prefix of ceil(deg / index-build block) per heavy row
     sg_workspace ws;
 };
 
 namespace sgi {
 
-GraphView view_of(const sg_graph *g);
+GraphView view_of(const sg_graph *g, int heavy_on);
 sg_status ensure_wic(sg_graph *g, cudaStream_t st);
 sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st);
+sg_status ensure_heavy_index(sg_graph *g, int32_t W, cudaStream_t st);
 sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out);
+bool heavy_index_enabled(const sg_graph *g, int32_t W);
+size_t t2_table_bytes();
 
 // kernels launched by this thread since the counter was last reset
 extern thread_local int g_launches;
+// keys a tier-1 / tier-2 warp table may hold (clamped to half its slots)
+extern int g_tier_limit[2];
 
-// kernels (sg_kernels.cu); `after_warp` (may be null) is recorded right
-// after the initial-gain warp-engine launch
-sg_status run_init_gains(sg_graph *g, const Coins &co, int model, cudaStream_t st,
-                         cudaEvent_t after_warp = nullptr);
-sg_status run_round(sg_graph *g, const Coins &co, int model, int32_t round, cudaStream_t st);
+// kernels (sg_kernels.cu)
+sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t st);
+sg_status run_init_gains(sg_graph *g, const Coins &co, int model, int heavy_on, cudaStream_t st,
+                         cudaEvent_t after_t1 = nullptr);
+sg_status run_round(sg_graph *g, const Coins &co, int model, int heavy_on, int32_t round, cudaStream_t st,
+                    cudaEvent_t after_fwd = nullptr);
 sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st);
+sg_status run_t2_clear(unsigned char *tab, int warps, cudaStream_t st);
 
 }  // namespace sgi

@@ -1,28 +1,32 @@
 // sg_kernels.cu -- device kernels of the StaticGreedy-DU path on sm_103a.
 //
-// Snapshots are bit-sliced: one 64-bit word per (node, task) covers 64
-// snapshots, so a single traversal of the graph serves 64 snapshots at
-// once.  A node x carrying frontier bits F expands each arc e = (x, y) by
-// computing the arc's live bits for exactly the snapshots in F from the
-// splitmix64 hash in registers; the bits new to y are OR-ed into y's
-// visited word and, if y had no pending bits, y is queued.  Every
-// (snapshot, node) pair is therefore expanded exactly once per traversal.
+// Snapshots are bit-sliced: a 64-bit word per (node, task) carries 64
+// independent traversal states at once.  Two slicings are used:
+//   snapshot-sliced  bit b = snapshot 64w+b.  Initial gains (Algorithm 2,
+//                    first loop) run one task per (source v, word w); the
+//                    forward dynamic update runs one per word from v*.
+//   target-sliced    bit j = the j-th of up to 64 newly covered targets of
+//                    ONE snapshot r.  The reverse dynamic update (Algorithm
+//                    2, inner loops) runs one task per (r, 64 targets): each
+//                    node u ends with the set of those targets it reaches,
+//                    and s_u drops by its popcount -- exactly the per-(w, r)
+//                    reverse BFS of the paper, with ancestors shared by the
+//                    64 targets walked once.
+// Expanding a node x with state F over an arc e = (x, y) ORs the arc's live
+// bits into y: snapshot-sliced, live(e, 64w+b) for each b in F;
+// target-sliced, F itself if live(e, r).  Coins come from the splitmix64
+// hash in registers, except on heavy rows (degree >= a threshold) whose
+// per-word live masks are computed once per query into a compact index
+// (nonzero masks only), since hub rows are re-expanded by many tasks.
 //
-// Two traversal engines share that step:
-//   warp engine  one warp per task, visited/pending words in a per-warp
-//                shared-memory open-addressing table; the frontier is
-//                expanded 32 arcs at a time with a load-balanced
-//                (prefix-sum + shuffle search) arc assignment.  A task
-//                whose table passes half full is aborted and queued for
-//   CTA engine   one 512-thread block per task with dense visited/pending
-//                arrays in global memory, level-synchronous, block-wide
-//                load-balanced arc expansion.  The same engine runs the
-//                forward dynamic-update BFS on the coverage bitsets.
-// Tasks:
-//   init (Algorithm 2, first loop): (v, word) -> s_v += sum_x popc(vis_x)
-//   reverse DU (Algorithm 2, inner loops): (w, word, M_w) newly covered ->
-//       s_u -= popc(vis_u) for every u reaching w in the snapshots of M_w
-//   forward DU: from v*, the nodes newly covered in every snapshot.
+// Traversal engines, by task size:
+//   tier 1  one warp per task, visited/pending words in a 512-slot
+//           shared-memory hash table; frontier expanded 32 elements at a
+//           time with a load-balanced (prefix sum + shuffle search) split.
+//   tier 2  the same warp engine over a 16384-slot table in global memory,
+//           for tasks that filled the tier-1 table past half.
+//   tier 3  one 512-thread block per task over dense per-block arrays,
+//           level-synchronous; also runs the forward dynamic update.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,7 +43,13 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr long long SEED_MARK = -(1LL << 62);
 
 enum { DIR_FWD = 0, DIR_REV = 1 };
-enum { TASK_INIT = 0, TASK_REV = 1, TASK_FWD = 2 };
+enum { TASK_INIT = 0, TASK_REVT = 1, TASK_FWD = 2 };
+enum { SLICE_SNAP = 0, SLICE_TGT = 1 };
+
+constexpr int T1_LOGC = 9;   // tier-1 table: 512 slots per warp (shared memory)
+constexpr int T2_LOGC = 14;  // tier-2 table: 16384 slots per warp (global memory)
+constexpr int WE_THREADS = 128;
+constexpr int HB_ARCS = 1024;  // heavy-index build: arcs per work item
 
 // ------------------------------------------------------------------ coins
 // High 32 bits of splitmix64(base ^ (r << 40)) (Steele, Lea, Flood 2014,
@@ -49,7 +59,7 @@ __device__ __forceinline__ uint32_t coin_hi32(uint64_t base, uint32_t r)
     uint64_t z = (base ^ ((uint64_t)r << 40)) + 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    uint32_t hi = (uint32_t)(z >> 32);
+    const uint32_t hi = (uint32_t)(z >> 32);
     return hi ^ (hi >> 31);
 }
 
@@ -76,28 +86,6 @@ __device__ __forceinline__ uint64_t word_mask(int word, int R)
 }
 
 // --------------------------------------------------------------- the graph
-template <int DIR>
-__device__ __forceinline__ void row_of(const GraphView &g, int x, int &beg, int &end)
-{
-    if (DIR == DIR_FWD) {
-        beg = __ldg(g.rp + x);
-        end = __ldg(g.rp + x + 1);
-    } else {
-        beg = __ldg(g.crp + x);
-        end = __ldg(g.crp + x + 1);
-    }
-}
-
-// threshold-1 shared by every arc of x's row (UIC scalar; reverse WIC: the
-// in-arcs of x all point at x, so they share 1/indeg(x)); forward WIC arcs
-// carry their own and ignore this value.
-template <int DIR, int MODEL>
-__device__ __forceinline__ uint32_t row_tm1(const GraphView &g, const Coins &co, int x)
-{
-    if (MODEL == MODEL_WIC && DIR == DIR_REV) return __ldg(g.tmi + x);
-    return co.uic_tm1;
-}
-
 template <int DIR, int MODEL>
 __device__ __forceinline__ void arc_at(const GraphView &g, int j, uint32_t rtm1, int &y, uint32_t &eid,
                                        uint32_t &tm1)
@@ -120,15 +108,64 @@ __device__ __forceinline__ void arc_at(const GraphView &g, int j, uint32_t rtm1,
     }
 }
 
-__device__ __forceinline__ int find_word(const long long *off, int W, long long t)
+// The elements one frontier entry expands: its arcs (light row) or its
+// row's index entries for the word (heavy row).
+struct Row {
+    long long base;
+    int vdeg;   // elements to expand
+    int deg;    // degree in the canonical graph (work counter)
+    int heavy;
+    uint32_t rtm1;
+};
+
+template <int DIR, int MODEL>
+__device__ __forceinline__ Row row_ref(const GraphView &g, const Coins &co, int x, int word)
 {
-    int lo = 0, hi = W - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= t) lo = mid;
-        else hi = mid - 1;
+    Row r;
+    int beg, end;
+    if (DIR == DIR_FWD) {
+        beg = __ldg(g.rp + x);
+        end = __ldg(g.rp + x + 1);
+    } else {
+        beg = __ldg(g.crp + x);
+        end = __ldg(g.crp + x + 1);
     }
-    return lo;
+    r.deg = end - beg;
+    // UIC: one threshold; reverse WIC: all in-arcs of x share 1/indeg(x);
+    // forward WIC arcs carry their own threshold.
+    r.rtm1 = (MODEL == MODEL_WIC && DIR == DIR_REV) ? __ldg(g.tmi + x) : co.uic_tm1;
+    const HeavyView &hv = DIR == DIR_FWD ? g.hout : g.hin;
+    const int h = g.heavy_on ? __ldg(hv.hid + x) : -1;
+    if (h >= 0) {
+        r.heavy = 1;
+        r.base = __ldg(hv.hpref + h) * co.W + (long long)word * r.deg;
+        r.vdeg = __ldg(hv.hcnt + (long long)h * co.W + word);
+    } else {
+        r.heavy = 0;
+        r.base = beg;
+        r.vdeg = r.deg;
+    }
+    return r;
+}
+
+// Live state carried from x to the element's neighbour y.
+template <int DIR, int MODEL, int SLICE>
+__device__ __forceinline__ uint64_t elem(const GraphView &g, const Coins &co, long long base, int heavy,
+                                         uint32_t rtm1, int j, uint64_t F, uint32_t rs, int &y)
+{
+    const HeavyView &hv = DIR == DIR_FWD ? g.hout : g.hin;
+    if (heavy) {
+        const long long q = base + j;
+        y = __ldg(hv.hnbr + q);
+        const uint64_t mk = __ldg(hv.hmask + q);
+        if (SLICE == SLICE_SNAP) return mk & F;
+        return ((mk >> (rs & 63u)) & 1ull) ? F : 0ull;
+    }
+    uint32_t eid, tm1;
+    arc_at<DIR, MODEL>(g, (int)(base + j), rtm1, y, eid, tm1);
+    if (SLICE == SLICE_SNAP) return live_bits(co, eid, rs, F, tm1);
+    if (co.none_live) return 0ull;
+    return coin_hi32(co.seed ^ (uint64_t)eid, rs) <= tm1 ? F : 0ull;
 }
 
 template <class T>
@@ -139,51 +176,16 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// ============================================================ warp engine
-
-template <int LOGC>
-struct __align__(16) WarpTab {
-    static constexpr int C = 1 << LOGC;
-    unsigned long long vis[C];
-    unsigned long long pend[C];
-    int key[C];
-    unsigned short queue[C];
-    unsigned short touched[C];
-    int qtail;
-    int ntouched;
-    int overflow;
-    int pad;
-};
-
-// Find y's slot, inserting it if absent.  Returns -1 (and flags overflow)
-// once the table holds `limit` keys; at most 31 racing lanes can pass the
-// check, so the touched list never exceeds limit + 31 < C entries.
-template <int LOGC>
-__device__ __forceinline__ int table_slot(WarpTab<LOGC> &T, int y, int limit)
+// largest i in [0, count) with off[i] <= t (off non-decreasing, off[0] <= t)
+__device__ __forceinline__ int find_off(const long long *off, int count, long long t)
 {
-    constexpr int C = 1 << LOGC;
-    uint32_t h = ((uint32_t)y * 2654435761u) >> (32 - LOGC);
-    volatile int *keys = T.key;
-    for (int probe = 0; probe < C; ++probe) {
-        const int k = keys[h];
-        if (k == y) return (int)h;
-        if (k == EMPTY_KEY) {
-            if (*(volatile int *)&T.ntouched >= limit) {
-                T.overflow = 1;
-                return -1;
-            }
-            const int old = atomicCAS(&T.key[h], EMPTY_KEY, y);
-            if (old == EMPTY_KEY) {
-                const int t = atomicAdd(&T.ntouched, 1);
-                T.touched[t] = (unsigned short)h;
-                return (int)h;
-            }
-            if (old == y) return (int)h;
-        }
-        h = (h + 1) & (C - 1);
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= t) lo = mid;
+        else hi = mid - 1;
     }
-    T.overflow = 1;
-    return -1;
+    return lo;
 }
 
 struct EngineArgs {
@@ -191,173 +193,281 @@ struct EngineArgs {
     Coins co;
     Ctl *ctl;
     long long *s;
-    const long long *du_off;
-    const int32_t *du_x;
-    const unsigned long long *du_m;
-    int32_t *big_list;
-    long long ntasks;  // TASK_INIT only; TASK_REV reads ctl->du_total
-    int chunk;
+    const int32_t *tl;      // per-snapshot target lists
+    const long long *toff;  // [64W] list offsets
+    const int32_t *tcnt;    // [64W] list lengths
+    const long long *coff;  // [64W+1] chunk-task offsets
+    int32_t *list1, *list2;
+    unsigned char *t2_tab;
+    long long ntasks;       // TASK_INIT: n * W
+    int limit;              // keys a warp table may hold before the task moves up a tier
 };
 
-template <int LOGC, int DIR, int MODEL, int TASK>
-__global__ void __launch_bounds__(128) warp_engine_kernel(EngineArgs a)
+// ============================================================ warp engine
+
+struct WTab {
+    unsigned long long *vis, *pend;
+    int *key;
+    unsigned short *queue, *touched;
+    int *ctr;  // [0] queue tail, [1] keys, [2] overflow
+};
+
+template <int LOGC>
+__host__ __device__ constexpr size_t tab_bytes()
+{
+    return (size_t)(1 << LOGC) * 24 + 16;
+}
+
+template <int LOGC>
+__device__ __forceinline__ WTab tab_at(unsigned char *p)
 {
     constexpr int C = 1 << LOGC;
-    constexpr int LIMIT = C / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    WarpTab<LOGC> &T = reinterpret_cast<WarpTab<LOGC> *>(smem_raw)[threadIdx.x >> 5];
+    WTab t;
+    t.vis = reinterpret_cast<unsigned long long *>(p);
+    t.pend = t.vis + C;
+    t.key = reinterpret_cast<int *>(t.pend + C);
+    t.queue = reinterpret_cast<unsigned short *>(t.key + C);
+    t.touched = t.queue + C;
+    t.ctr = reinterpret_cast<int *>(t.touched + C);
+    return t;
+}
 
-    for (int i = lane; i < C; i += 32) {
-        T.key[i] = EMPTY_KEY;
-        T.vis[i] = 0;
-        T.pend[i] = 0;
-    }
-    if (lane == 0) {
-        T.qtail = 0;
-        T.ntouched = 0;
-        T.overflow = 0;
-    }
-    __syncwarp();
+template <int LOGC>
+__device__ __forceinline__ uint32_t slot_of(int y)
+{
+    return ((uint32_t)y * 2654435761u) >> (32 - LOGC);
+}
 
+// Find y's slot, inserting it if absent.  Returns -1 (and flags overflow)
+// once the table holds `limit` keys; at most 31 racing lanes can pass the
+// check, so the touched list never exceeds limit + 31 < C entries.
+template <int LOGC>
+__device__ __forceinline__ int table_slot(const WTab &T, int y, int limit)
+{
+    constexpr int C = 1 << LOGC;
+    uint32_t h = slot_of<LOGC>(y);
+    volatile int *keys = T.key;
+    for (int probe = 0; probe < C; ++probe) {
+        const int k = keys[h];
+        if (k == y) return (int)h;
+        if (k == EMPTY_KEY) {
+            if (*(volatile int *)&T.ctr[1] >= limit) {
+                T.ctr[2] = 1;
+                return -1;
+            }
+            const int old = atomicCAS(&T.key[h], EMPTY_KEY, y);
+            if (old == EMPTY_KEY) {
+                const int t = atomicAdd(&T.ctr[1], 1);
+                T.touched[t] = (unsigned short)h;
+                return (int)h;
+            }
+            if (old == y) return (int)h;
+        }
+        h = (h + 1) & (C - 1);
+    }
+    T.ctr[2] = 1;
+    return -1;
+}
+
+// One task by one warp.  Returns true if the table overflowed (nothing of
+// the task was applied; the table is clean again either way).
+template <int LOGC, int DIR, int MODEL, int TASK>
+__device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, long long t, int lane,
+                                          unsigned long long &edges_acc)
+{
+    constexpr int C = 1 << LOGC;
+    const int LIMIT = a.limit;  // in [1, C/2]
+    constexpr int SLICE = TASK == TASK_REVT ? SLICE_TGT : SLICE_SNAP;
     const GraphView &g = a.g;
     const Coins &co = a.co;
-    const long long ntasks = (TASK == TASK_INIT) ? a.ntasks : *(volatile long long *)&a.ctl->du_total;
-    const int n = g.n;
-    unsigned long long my_edges = 0;
-
+    int x0 = 0, word;
+    uint32_t rs;
+    if (TASK == TASK_INIT) {
+        x0 = (int)(t / co.W);
+        word = (int)(t - (long long)x0 * co.W);
+        rs = (uint32_t)word * 64u;
+        if (lane == 0) {
+            const uint64_t M0 = word_mask(word, co.R);
+            const uint32_t h = slot_of<LOGC>(x0);
+            T.key[h] = x0;
+            T.vis[h] = M0;
+            T.pend[h] = M0;
+            T.touched[0] = (unsigned short)h;
+            T.queue[0] = (unsigned short)h;
+            T.ctr[0] = 1;
+            T.ctr[1] = 1;
+        }
+    } else {
+        const int r = find_off(a.coff, 64 * co.W, t);
+        const long long c = t - a.coff[r];
+        word = r >> 6;
+        rs = (uint32_t)r;
+        const long long b0 = a.toff[r] + 64 * c;
+        const int cnt = (int)min(64LL, (long long)a.tcnt[r] - 64 * c);
+        for (int j = lane; j < cnt; j += 32) {
+            const int x = a.tl[b0 + j];
+            const int h = table_slot<LOGC>(T, x, LIMIT);
+            if (h < 0) continue;  // table full: the task moves up a tier
+            T.vis[h] = 1ull << j;
+            T.pend[h] = 1ull << j;
+            const int pos = atomicAdd(&T.ctr[0], 1);
+            T.queue[pos & (C - 1)] = (unsigned short)h;
+        }
+    }
+    __syncwarp();
+    unsigned long long tedges = 0;
+    int qhead = 0;
     while (true) {
+        const int qtail = *(volatile int *)&T.ctr[0];
+        const int ovf = *(volatile int *)&T.ctr[2];
+        if (ovf || qhead >= qtail) break;
+        const int nb = min(32, qtail - qhead);
         long long base = 0;
-        if (lane == 0) base = (long long)atomicAdd(&a.ctl->task_next, (unsigned long long)a.chunk);
-        base = __shfl_sync(FULL, base, 0);
-        if (base >= ntasks) break;
-        const long long tend = min(base + (long long)a.chunk, ntasks);
-        for (long long t = base; t < tend; ++t) {
-            int x0, word;
-            uint64_t M0;
-            if (TASK == TASK_INIT) {
-                x0 = (int)(t / co.W);
-                word = (int)(t - (long long)x0 * co.W);
-                M0 = word_mask(word, co.R);
-            } else {
-                word = find_word(a.du_off, co.W, t);
-                const long long i = t - a.du_off[word];
-                x0 = a.du_x[(long long)word * n + i];
-                M0 = a.du_m[(long long)word * n + i];
-            }
-            if (lane == 0) {
-                const uint32_t h = ((uint32_t)x0 * 2654435761u) >> (32 - LOGC);
-                T.key[h] = x0;
-                T.vis[h] = M0;
-                T.pend[h] = M0;
-                T.touched[0] = (unsigned short)h;
-                T.ntouched = 1;
-                T.queue[0] = (unsigned short)h;
-                T.qtail = 1;
-            }
-            __syncwarp();
-            const uint32_t r0 = (uint32_t)word * 64u;
-            unsigned long long tedges = 0;
-            int qhead = 0;
-            while (true) {
-                const int qtail = *(volatile int *)&T.qtail;
-                const int ovf = *(volatile int *)&T.overflow;
-                if (ovf || qhead >= qtail) break;
-                const int nb = min(32, qtail - qhead);
-                int beg = 0, end = 0;
-                uint64_t F = 0;
-                uint32_t rtm1 = co.uic_tm1;
-                if (lane < nb) {
-                    const int h = T.queue[(qhead + lane) & (C - 1)];
-                    const int x = T.key[h];
-                    F = T.pend[h];
-                    T.pend[h] = 0;
-                    row_of<DIR>(g, x, beg, end);
-                    rtm1 = row_tm1<DIR, MODEL>(g, co, x);
-                    tedges += (unsigned long long)__popcll(F) * (unsigned long long)(end - beg);
-                }
-                qhead += nb;
-                __syncwarp();
-                const int deg = end - beg;
-                int incl = deg;
+        int vdeg = 0, heavy = 0;
+        uint32_t rtm1 = 0;
+        uint64_t F = 0;
+        if (lane < nb) {
+            const int h = T.queue[(qhead + lane) & (C - 1)];
+            const int x = T.key[h];
+            F = T.pend[h];
+            T.pend[h] = 0;
+            const Row rr = row_ref<DIR, MODEL>(g, co, x, word);
+            base = rr.base;
+            vdeg = rr.vdeg;
+            heavy = rr.heavy;
+            rtm1 = rr.rtm1;
+            if (TASK == TASK_INIT) tedges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
+        }
+        qhead += nb;
+        __syncwarp();
+        int incl = vdeg;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                const int total = __shfl_sync(FULL, incl, 31);
-                const int excl = incl - deg;
-                for (int abase = 0; abase < total; abase += 32) {
-                    const int j = abase + lane;
-                    int lo = 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - vdeg;
+        for (int abase = 0; abase < total; abase += 32) {
+            const int j = abase + lane;
+            int lo = 0;
 #pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const int cand = lo + step;
-                        const int ex = __shfl_sync(FULL, excl, cand & 31);
-                        if (cand < nb && ex <= j) lo = cand;
-                    }
-                    const int ibeg = __shfl_sync(FULL, beg, lo);
-                    const int iex = __shfl_sync(FULL, excl, lo);
-                    const uint64_t iF = __shfl_sync(FULL, F, lo);
-                    const uint32_t itm1 = __shfl_sync(FULL, rtm1, lo);
-                    if (j < total) {
-                        int y;
-                        uint32_t eid, tm1;
-                        arc_at<DIR, MODEL>(g, ibeg + (j - iex), itm1, y, eid, tm1);
-                        const uint64_t ml = live_bits(co, eid, r0, iF, tm1);
-                        if (ml) {
-                            const int h = table_slot<LOGC>(T, y, LIMIT);
-                            if (h >= 0) {
-                                const uint64_t old = atomicOr(&T.vis[h], (unsigned long long)ml);
-                                const uint64_t nw = ml & ~old;
-                                if (nw) {
-                                    const uint64_t oldp = atomicOr(&T.pend[h], (unsigned long long)nw);
-                                    if (oldp == 0) {
-                                        const int pos = atomicAdd(&T.qtail, 1);
-                                        T.queue[pos & (C - 1)] = (unsigned short)h;
-                                    }
-                                }
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int cand = lo + step;
+                const int ex = __shfl_sync(FULL, excl, cand & 31);
+                if (cand < nb && ex <= j) lo = cand;
+            }
+            const long long ib = __shfl_sync(FULL, base, lo);
+            const int iex = __shfl_sync(FULL, excl, lo);
+            const int ih = __shfl_sync(FULL, heavy, lo);
+            const uint32_t itm1 = __shfl_sync(FULL, rtm1, lo);
+            const uint64_t iF = __shfl_sync(FULL, F, lo);
+            if (j < total) {
+                int y;
+                const uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y);
+                if (ml) {
+                    const int h = table_slot<LOGC>(T, y, LIMIT);
+                    if (h >= 0) {
+                        const uint64_t old = atomicOr(&T.vis[h], (unsigned long long)ml);
+                        const uint64_t nw = ml & ~old;
+                        if (nw) {
+                            const uint64_t oldp = atomicOr(&T.pend[h], (unsigned long long)nw);
+                            if (oldp == 0) {
+                                const int pos = atomicAdd(&T.ctr[0], 1);
+                                T.queue[pos & (C - 1)] = (unsigned short)h;
                             }
                         }
                     }
                 }
-                __syncwarp();
             }
-            __syncwarp();
-            const int ovf = *(volatile int *)&T.overflow;
-            const int nt = *(volatile int *)&T.ntouched;
-            long long cnt = 0;
-            for (int i = lane; i < nt; i += 32) {
-                const int h = T.touched[i];
-                if (!ovf) {
-                    const int c = __popcll(T.vis[h]);
-                    if (TASK == TASK_INIT) cnt += c;
-                    else atomicAdd((unsigned long long *)&a.s[T.key[h]], (unsigned long long)(-(long long)c));
-                }
-                T.key[h] = EMPTY_KEY;
-                T.vis[h] = 0;
-                T.pend[h] = 0;
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    const int ovf = *(volatile int *)&T.ctr[2];
+    const int nt = *(volatile int *)&T.ctr[1];
+    long long cnt = 0;
+    unsigned long long redges = 0;
+    for (int i = lane; i < nt; i += 32) {
+        const int h = T.touched[i];
+        if (!ovf) {
+            const int c = __popcll(T.vis[h]);
+            if (TASK == TASK_INIT) {
+                cnt += c;
+            } else {
+                const int u = T.key[h];
+                atomicAdd((unsigned long long *)&a.s[u], (unsigned long long)(-(long long)c));
+                redges += (unsigned long long)c * (unsigned long long)(__ldg(g.crp + u + 1) - __ldg(g.crp + u));
             }
-            if (TASK == TASK_INIT) cnt = warp_sum(cnt);
-            if (!ovf) my_edges += tedges;
-            __syncwarp();
-            if (lane == 0) {
-                if (ovf) {
-                    const unsigned long long idx = atomicAdd(&a.ctl->big_count, 1ull);
-                    a.big_list[idx] = (int32_t)t;
-                } else if (TASK == TASK_INIT) {
-                    atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)cnt);
-                }
-                T.qtail = 0;
-                T.ntouched = 0;
-                T.overflow = 0;
+        }
+        T.key[h] = EMPTY_KEY;
+        T.vis[h] = 0;
+        T.pend[h] = 0;
+    }
+    if (TASK == TASK_INIT) cnt = warp_sum(cnt);
+    if (!ovf) edges_acc += TASK == TASK_INIT ? tedges : redges;
+    __syncwarp();
+    if (lane == 0) {
+        if (!ovf && TASK == TASK_INIT) atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)cnt);
+        T.ctr[0] = 0;
+        T.ctr[1] = 0;
+        T.ctr[2] = 0;
+    }
+    __syncwarp();
+    return ovf != 0;
+}
+
+// TIER 1: tasks [0, ntasks) by dynamic chunks, shared-memory tables;
+// TIER 2: the tasks tier 1 gave up on, global-memory tables (clean on entry
+// and on exit).  Overflowing tasks are listed for the next tier.
+template <int LOGC, int DIR, int MODEL, int TASK, int TIER>
+__global__ void __launch_bounds__(WE_THREADS) warp_engine_kernel(EngineArgs a, int chunk)
+{
+    constexpr int C = 1 << LOGC;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    WTab T;
+    if (TIER == 1) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        T = tab_at<LOGC>(smem_raw + (size_t)wib * tab_bytes<LOGC>());
+        for (int i = lane; i < C; i += 32) {
+            T.key[i] = EMPTY_KEY;
+            T.vis[i] = 0;
+            T.pend[i] = 0;
+        }
+        if (lane == 0) {
+            T.ctr[0] = 0;
+            T.ctr[1] = 0;
+            T.ctr[2] = 0;
+        }
+        __syncwarp();
+    } else {
+        const size_t gw = (size_t)blockIdx.x * (WE_THREADS / 32) + wib;
+        T = tab_at<LOGC>(a.t2_tab + gw * tab_bytes<LOGC>());
+    }
+    Ctl *ctl = a.ctl;
+    long long ntasks;
+    if (TIER == 1) ntasks = TASK == TASK_INIT ? a.ntasks : *(volatile long long *)&ctl->du_total;
+    else ntasks = (long long)*(volatile unsigned long long *)&ctl->l1_count;
+    unsigned long long edges = 0;
+    while (true) {
+        long long base = 0;
+        if (lane == 0)
+            base = (long long)atomicAdd(TIER == 1 ? &ctl->t1_next : &ctl->l1_next, (unsigned long long)chunk);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= ntasks) break;
+        const long long tend = min(base + (long long)chunk, ntasks);
+        for (long long q = base; q < tend; ++q) {
+            const long long t = TIER == 1 ? q : (long long)a.list1[q];
+            const bool ovf = warp_task<LOGC, DIR, MODEL, TASK>(a, T, t, lane, edges);
+            if (ovf && lane == 0) {
+                if (TIER == 1) a.list1[atomicAdd(&ctl->l1_count, 1ull)] = (int32_t)t;
+                else a.list2[atomicAdd(&ctl->l2_count, 1ull)] = (int32_t)t;
             }
-            __syncwarp();
         }
     }
-    my_edges = warp_sum(my_edges);
-    if (lane == 0 && my_edges)
-        atomicAdd(TASK == TASK_INIT ? &a.ctl->init_edges : &a.ctl->rev_edges, my_edges);
+    edges = warp_sum(edges);
+    if (lane == 0 && edges) atomicAdd(TASK == TASK_INIT ? &ctl->init_edges : &ctl->rev_edges, edges);
 }
 
 // ============================================================= CTA engine
@@ -367,17 +477,18 @@ constexpr int BW = BT / 32;
 
 struct CtaShared {
     unsigned long long F[BT];
-    int x[BT];
-    int beg[BT];
+    long long base[BT];
     int ex[BT];
+    int heavy[BT];
     uint32_t tm1[BT];
     int wsum[BW];
     int qlen, qnext, ntouch, ndu, total;
     long long red_ll[BW];
     unsigned long long red_ull[BW];
+    int bcnt[64], boff[64], bcur[64];
 };
 
-// Block-wide exclusive scan of v; returns the exclusive prefix, *total the sum.
+// Block-wide exclusive scan of v; *total receives the sum.
 __device__ __forceinline__ int block_excl_scan(int v, CtaShared &S, int *total)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -390,7 +501,7 @@ __device__ __forceinline__ int block_excl_scan(int v, CtaShared &S, int *total)
     if (lane == 31) S.wsum[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-        int w = lane < BW ? S.wsum[lane] : 0;
+        const int w = lane < BW ? S.wsum[lane] : 0;
         int wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -420,32 +531,52 @@ __device__ __forceinline__ T block_sum(T v, T *red)
     return r;  // valid in thread 0
 }
 
-struct CtaTask {
+struct CtaState {
     unsigned long long *vis;
     unsigned long long *pend;
     int32_t *qa;
     int32_t *qb;
-    int32_t *touched;        // TASK_INIT / TASK_REV
+    int32_t *touched;           // TASK_INIT / TASK_REVT
     unsigned long long *nbits;  // TASK_FWD
-    int32_t *du_x;           // TASK_FWD (this word's list)
-    unsigned long long *du_m;   // TASK_FWD
+    int32_t *du_x;              // TASK_FWD (this word's list)
 };
 
-// One traversal by the whole block.  TASK_INIT / TASK_REV: vis/pend are a
-// zeroed slot and are zero again on return.  TASK_FWD: vis is the word's
-// coverage bitset, the start bits are M0 minus what is already covered, and
-// every node gaining bits is listed once with its merged new bits.
+// One traversal by the whole block over dense arrays, level-synchronous.
+// TASK_INIT / TASK_REVT: vis/pend are a zeroed slot and are zero again on
+// return.  TASK_FWD: vis is the word's coverage bitset; every node gaining
+// bits is listed once, its merged new bits left in nbits.
+// Seeds: INIT (x0, all bits of the word); REVT the targets tgt[0..ntgt)
+// with one bit each; FWD x0 = v* with the word's bits not yet covered.
 template <int DIR, int MODEL, int TASK>
-__device__ void cta_bfs(const GraphView &g, const Coins &co, Ctl *ctl, long long *s, CtaTask w, int x0,
-                        int word, uint64_t M0, CtaShared &S)
+__device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint32_t rs, const int32_t *tgt,
+                        int ntgt, CtaShared &S)
 {
+    constexpr int SLICE = TASK == TASK_REVT ? SLICE_TGT : SLICE_SNAP;
+    const GraphView &g = a.g;
+    const Coins &co = a.co;
     const int tid = threadIdx.x;
+    long long cnt = 0;
     if (tid == 0) {
         S.qlen = 0;
         S.qnext = 0;
         S.ntouch = 0;
         S.ndu = 0;
-        uint64_t M = M0;
+    }
+    __syncthreads();
+    if (TASK == TASK_REVT) {
+        for (int j = tid; j < ntgt; j += BT) {
+            const int x = tgt[j];
+            w.vis[x] = 1ull << j;
+            w.pend[x] = 1ull << j;
+            w.qa[j] = x;
+            w.touched[j] = x;
+        }
+        if (tid == 0) {
+            S.qlen = ntgt;
+            S.ntouch = ntgt;
+        }
+    } else if (tid == 0) {
+        uint64_t M = word_mask(word, co.R);
         if (TASK == TASK_FWD) M &= ~w.vis[x0];
         if (M) {
             w.vis[x0] |= M;
@@ -459,12 +590,11 @@ __device__ void cta_bfs(const GraphView &g, const Coins &co, Ctl *ctl, long long
             } else {
                 w.touched[0] = x0;
                 S.ntouch = 1;
+                cnt = __popcll(M);
             }
         }
     }
-    long long cnt = (TASK == TASK_INIT && tid == 0) ? (long long)__popcll(M0) : 0;
     unsigned long long edges = 0;
-    const uint32_t r0 = (uint32_t)word * 64u;
     int32_t *cur = w.qa, *nxt = w.qb;
     __syncthreads();
     while (true) {
@@ -472,21 +602,20 @@ __device__ void cta_bfs(const GraphView &g, const Coins &co, Ctl *ctl, long long
         if (L == 0) break;
         for (int cbase = 0; cbase < L; cbase += BT) {
             const int i = cbase + tid;
-            int deg = 0;
+            int vd = 0;
             if (i < L) {
                 const int x = cur[i];
                 const uint64_t F = atomicExch(&w.pend[x], 0ull);
-                int beg, end;
-                row_of<DIR>(g, x, beg, end);
-                deg = F ? end - beg : 0;
-                S.x[tid] = x;
+                const Row rr = row_ref<DIR, MODEL>(g, co, x, word);
+                vd = F ? rr.vdeg : 0;
                 S.F[tid] = F;
-                S.beg[tid] = beg;
-                S.tm1[tid] = row_tm1<DIR, MODEL>(g, co, x);
-                edges += (unsigned long long)__popcll(F) * (unsigned long long)(end - beg);
+                S.base[tid] = rr.base;
+                S.heavy[tid] = rr.heavy;
+                S.tm1[tid] = rr.rtm1;
+                if (TASK != TASK_REVT) edges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
             }
             int total;
-            const int ex = block_excl_scan(deg, S, &total);
+            const int ex = block_excl_scan(vd, S, &total);
             S.ex[tid] = ex;
             __syncthreads();
             const int nb = min(BT, L - cbase);
@@ -500,9 +629,8 @@ __device__ void cta_bfs(const GraphView &g, const Coins &co, Ctl *ctl, long long
                         else hi = mid - 1;
                     }
                     int y;
-                    uint32_t eid, tm1;
-                    arc_at<DIR, MODEL>(g, S.beg[lo] + (j - S.ex[lo]), S.tm1[lo], y, eid, tm1);
-                    const uint64_t ml = live_bits(co, eid, r0, S.F[lo], tm1);
+                    const uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, S.base[lo], S.heavy[lo], S.tm1[lo],
+                                                                j - S.ex[lo], S.F[lo], rs, y);
                     if (ml) {
                         const uint64_t old = atomicOr(&w.vis[y], (unsigned long long)ml);
                         const uint64_t nw = ml & ~old;
@@ -530,158 +658,199 @@ __device__ void cta_bfs(const GraphView &g, const Coins &co, Ctl *ctl, long long
         nxt = tmp;
         __syncthreads();
     }
-    // epilogue
-    if (TASK == TASK_FWD) {
-        const int nd = S.ndu;
-        for (int i = tid; i < nd; i += BT) {
-            const int y = w.du_x[i];
-            w.du_m[i] = w.nbits[y];
-            w.nbits[y] = 0;
-        }
-    } else {
+    if (TASK != TASK_FWD) {
         const int nt = S.ntouch;
         for (int i = tid; i < nt; i += BT) {
             const int y = w.touched[i];
-            if (TASK == TASK_REV)
-                atomicAdd((unsigned long long *)&s[y], (unsigned long long)(-(long long)__popcll(w.vis[y])));
+            if (TASK == TASK_REVT) {
+                const int c = __popcll(w.vis[y]);
+                atomicAdd((unsigned long long *)&a.s[y], (unsigned long long)(-(long long)c));
+                edges += (unsigned long long)c * (unsigned long long)(__ldg(g.crp + y + 1) - __ldg(g.crp + y));
+            }
             w.vis[y] = 0;
         }
     }
     const unsigned long long e_tot = block_sum(edges, S.red_ull);
     if (TASK == TASK_INIT) {
         const long long c_tot = block_sum(cnt, S.red_ll);
-        if (tid == 0) atomicAdd((unsigned long long *)&s[x0], (unsigned long long)c_tot);
+        if (tid == 0) atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)c_tot);
     }
     if (tid == 0 && e_tot) {
-        unsigned long long *dst =
-            TASK == TASK_INIT ? &ctl->init_edges : (TASK == TASK_REV ? &ctl->rev_edges : &ctl->fwd_edges);
+        unsigned long long *dst = TASK == TASK_INIT ? &a.ctl->init_edges
+                                                    : (TASK == TASK_REVT ? &a.ctl->rev_edges : &a.ctl->fwd_edges);
         atomicAdd(dst, e_tot);
     }
     __syncthreads();
 }
 
-struct BigArgs {
-    GraphView g;
-    Coins co;
-    Ctl *ctl;
-    long long *s;
-    const long long *du_off;
-    const int32_t *du_x;
-    const unsigned long long *du_m;
-    const int32_t *big_list;
-    unsigned long long *slot_vis, *slot_pend;
-    int32_t *slot_qa, *slot_qb, *slot_touched;
+struct SlotArgs {
+    unsigned long long *vis, *pend;
+    int32_t *qa, *qb, *touched;
 };
 
-// Tasks the warp engine gave up on, one per block, dense per-block slots.
+// Tier 3: the tasks tier 2 gave up on, one per block, dense per-block slots.
 template <int DIR, int MODEL, int TASK>
-__global__ void __launch_bounds__(BT) cta_engine_kernel(BigArgs a)
+__global__ void __launch_bounds__(BT) cta_engine_kernel(EngineArgs a, SlotArgs sl)
 {
     __shared__ CtaShared S;
     __shared__ long long sh_t;
     const int n = a.g.n;
     const size_t so = (size_t)blockIdx.x * (size_t)n;
-    CtaTask w;
-    w.vis = a.slot_vis + so;
-    w.pend = a.slot_pend + so;
-    w.qa = a.slot_qa + so;
-    w.qb = a.slot_qb + so;
-    w.touched = a.slot_touched + so;
+    CtaState w;
+    w.vis = sl.vis + so;
+    w.pend = sl.pend + so;
+    w.qa = sl.qa + so;
+    w.qb = sl.qb + so;
+    w.touched = sl.touched + so;
     w.nbits = nullptr;
     w.du_x = nullptr;
-    w.du_m = nullptr;
-    const long long count = (long long)*(volatile unsigned long long *)&a.ctl->big_count;
+    Ctl *ctl = a.ctl;
+    const long long count = (long long)*(volatile unsigned long long *)&ctl->l2_count;
     while (true) {
-        if (threadIdx.x == 0) sh_t = (long long)atomicAdd(&a.ctl->big_next, 1ull);
+        if (threadIdx.x == 0) sh_t = (long long)atomicAdd(&ctl->l2_next, 1ull);
         __syncthreads();
         const long long k = sh_t;
         __syncthreads();
         if (k >= count) break;
-        const long long t = a.big_list[k];
-        int x0, word;
-        uint64_t M0;
+        const long long t = a.list2[k];
         if (TASK == TASK_INIT) {
-            x0 = (int)(t / a.co.W);
-            word = (int)(t - (long long)x0 * a.co.W);
-            M0 = word_mask(word, a.co.R);
+            const int x0 = (int)(t / a.co.W);
+            const int word = (int)(t - (long long)x0 * a.co.W);
+            cta_bfs<DIR, MODEL, TASK>(a, w, x0, word, (uint32_t)word * 64u, nullptr, 0, S);
         } else {
-            word = find_word(a.du_off, a.co.W, t);
-            const long long i = t - a.du_off[word];
-            x0 = a.du_x[(long long)word * n + i];
-            M0 = a.du_m[(long long)word * n + i];
+            const int r = find_off(a.coff, 64 * a.co.W, t);
+            const long long c = t - a.coff[r];
+            const int cnt = (int)min(64LL, (long long)a.tcnt[r] - 64 * c);
+            cta_bfs<DIR, MODEL, TASK>(a, w, 0, r >> 6, (uint32_t)r, a.tl + a.toff[r] + 64 * c, cnt, S);
         }
-        cta_bfs<DIR, MODEL, TASK>(a.g, a.co, a.ctl, a.s, w, x0, word, M0, S);
     }
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        if (TASK == TASK_INIT) atomicAdd(&a.ctl->init_big, (unsigned long long)count);
-        else atomicAdd(&a.ctl->rev_big, (unsigned long long)count);
+        const unsigned long long c2 = *(volatile unsigned long long *)&ctl->l1_count;
+        if (TASK == TASK_INIT) {
+            ctl->init_t2 += c2;
+            ctl->init_t3 += (unsigned long long)count;
+        } else {
+            ctl->rev_t2 += c2;
+            ctl->rev_t3 += (unsigned long long)count;
+        }
     }
 }
 
+// ========================================================== forward DU
+
 struct FwdArgs {
-    GraphView g;
-    Coins co;
-    Ctl *ctl;
     unsigned long long *cov, *nbits, *pendf, *du_m;
-    int32_t *fq_a, *fq_b, *du_x;
-    long long *du_off;  // [W+1]
-    int32_t *du_cnt;    // [W]
+    int32_t *fq_a, *fq_b, *du_x, *du_cnt, *tl;
+    long long *toff, *coff;
+    int32_t *tcnt;
+    long long tcap;  // per-word capacity of tl
 };
 
 // Forward DU (Algorithm 2 inner loops, first half): block `word` walks from
-// v* over live arcs of the 64 snapshots of its word, with the word's
-// coverage bitset as the visited set, listing newly covered (w, M_w).  The
-// last block to finish turns the per-word counts into offsets.
+// v* over live arcs of its 64 snapshots with the word's coverage bitset as
+// the visited set, listing the newly covered nodes; it then writes, per
+// snapshot of the word, the list of its newly covered nodes (the targets of
+// the reverse pass).  The last block to finish turns the per-snapshot
+// counts into the offsets of the target-sliced reverse tasks.
 template <int MODEL>
-__global__ void __launch_bounds__(BT) fwd_du_kernel(FwdArgs a)
+__global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
 {
     __shared__ CtaShared S;
     __shared__ int sh_last;
     const int n = a.g.n;
     const int word = blockIdx.x;
-    const int vstar = *(volatile int32_t *)&a.ctl->vstar;
+    const int tid = threadIdx.x;
+    Ctl *ctl = a.ctl;
+    const int vstar = *(volatile int32_t *)&ctl->vstar;
     const size_t so = (size_t)word * (size_t)n;
     if (vstar >= 0) {
-        CtaTask w;
-        w.vis = a.cov + so;
-        w.pend = a.pendf + so;
-        w.qa = a.fq_a + so;
-        w.qb = a.fq_b + so;
+        CtaState w;
+        w.vis = f.cov + so;
+        w.pend = f.pendf + so;
+        w.qa = f.fq_a + so;
+        w.qb = f.fq_b + so;
         w.touched = nullptr;
-        w.nbits = a.nbits + so;
-        w.du_x = a.du_x + so;
-        w.du_m = a.du_m + so;
-        cta_bfs<DIR_FWD, MODEL, TASK_FWD>(a.g, a.co, a.ctl, nullptr, w, vstar, word, word_mask(word, a.co.R), S);
+        w.nbits = f.nbits + so;
+        w.du_x = f.du_x + so;
+        cta_bfs<DIR_FWD, MODEL, TASK_FWD>(a, w, vstar, word, (uint32_t)word * 64u, nullptr, 0, S);
     } else {
-        if (threadIdx.x == 0) S.ndu = 0;
+        if (tid == 0) S.ndu = 0;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        a.du_cnt[word] = S.ndu;
+    // per-snapshot lists of the newly covered nodes of this word
+    const int nd = S.ndu;
+    int32_t *dux = f.du_x + so;
+    unsigned long long *dum = f.du_m + so;
+    unsigned long long *nb = f.nbits + so;
+    if (tid < 64) {
+        S.bcnt[tid] = 0;
+        S.bcur[tid] = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < nd; i += BT) {
+        const int y = dux[i];
+        uint64_t M = nb[y];
+        nb[y] = 0;
+        dum[i] = M;
+        while (M) {
+            const int b = __ffsll((long long)M) - 1;
+            M &= M - 1;
+            atomicAdd(&S.bcnt[b], 1);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int b = 0; b < 64; ++b) {
+            S.boff[b] = acc;
+            acc += S.bcnt[b];
+        }
+    }
+    __syncthreads();
+    if (tid < 64) {
+        f.toff[64 * word + tid] = (long long)word * f.tcap + S.boff[tid];
+        f.tcnt[64 * word + tid] = S.bcnt[tid];
+    }
+    int32_t *tlw = f.tl + (size_t)word * (size_t)f.tcap;
+    for (int i = tid; i < nd; i += BT) {
+        const int y = dux[i];
+        uint64_t M = dum[i];
+        while (M) {
+            const int b = __ffsll((long long)M) - 1;
+            M &= M - 1;
+            tlw[S.boff[b] + atomicAdd(&S.bcur[b], 1)] = y;
+        }
+    }
+    if (tid == 0) {
+        f.du_cnt[word] = nd;
         __threadfence();
-        const unsigned prev = atomicAdd(&a.ctl->fwd_arrivals, 1u);
+        const unsigned prev = atomicAdd(&ctl->fwd_arrivals, 1u);
         sh_last = (prev == gridDim.x - 1);
     }
     __syncthreads();
     if (!sh_last) return;
     __threadfence();
-    // last block: exclusive prefix of the per-word counts, in chunks of BT
+    // last block: chunk-task offsets over every snapshot
+    const int NS = 64 * gridDim.x;
     long long carry = 0;
-    const int W = gridDim.x;
-    for (int base = 0; base < W; base += BT) {
-        const int i = base + threadIdx.x;
-        const int v = i < W ? *(volatile int32_t *)&a.du_cnt[i] : 0;
+    for (int base = 0; base < NS; base += BT) {
+        const int i = base + tid;
+        const int v = i < NS ? (*(volatile int32_t *)&f.tcnt[i] + 63) / 64 : 0;
         int total;
         const int ex = block_excl_scan(v, S, &total);
-        if (i < W) a.du_off[i] = carry + ex;
+        if (i < NS) f.coff[i] = carry + ex;
         carry += total;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        a.du_off[W] = carry;
-        a.ctl->du_total = carry;
-        a.ctl->du_entries += (unsigned long long)carry;
-        a.ctl->fwd_arrivals = 0;
+    long long entries = 0;
+    for (int i = tid; i < (int)gridDim.x; i += BT) entries += *(volatile int32_t *)&f.du_cnt[i];
+    entries = block_sum(entries, S.red_ll);
+    if (tid == 0) {
+        f.coff[NS] = carry;
+        ctl->du_total = carry;
+        ctl->rev_tasks += (unsigned long long)carry;
+        ctl->du_entries += (unsigned long long)entries;
+        ctl->fwd_arrivals = 0;
     }
 }
 
@@ -778,9 +947,89 @@ __global__ void __launch_bounds__(AM_T) argmax_kernel(long long *s, int n, Ctl *
         if (bi >= 0) s[bi] = SEED_MARK;
         else ctl->flags |= 1;
         ctl->argmax_arrivals = 0;
-        ctl->task_next = 0;
-        ctl->big_next = 0;
-        ctl->big_count = 0;
+        ctl->t1_next = 0;
+        ctl->l1_count = 0;
+        ctl->l1_next = 0;
+        ctl->l2_count = 0;
+        ctl->l2_next = 0;
+    }
+}
+
+// ======================================================== heavy live index
+
+// Work item (heavy row h, word w, block of HB_ARCS arcs): the arcs' live
+// masks for the word; nonzero ones are appended (warp-aggregated) to the
+// (h, w) segment.  hcnt must be zero on entry.
+template <int DIR, int MODEL>
+__global__ void __launch_bounds__(256) heavy_index_kernel(GraphView g, Coins co, const int32_t *hrow,
+                                                          const int32_t *hcpref, int nh, int32_t *hcnt,
+                                                          int32_t *hnbr, unsigned long long *hmask,
+                                                          const long long *hpref)
+{
+    const int lane = threadIdx.x & 31;
+    const long long items = (long long)__ldg(hcpref + nh) * co.W;
+    const long long gw0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long it = gw0; it < items; it += nwarps) {
+        const int word = (int)(it % co.W);
+        const long long k = it / co.W;
+        int lo = 0, hi = nh - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(hcpref + mid) <= k) lo = mid;
+            else hi = mid - 1;
+        }
+        const int h = lo;
+        const int blk = (int)(k - __ldg(hcpref + h));
+        const int x = __ldg(hrow + h);
+        int beg, end;
+        if (DIR == DIR_FWD) {
+            beg = __ldg(g.rp + x);
+            end = __ldg(g.rp + x + 1);
+        } else {
+            beg = __ldg(g.crp + x);
+            end = __ldg(g.crp + x + 1);
+        }
+        const int deg = end - beg;
+        const uint32_t rtm1 = (MODEL == MODEL_WIC && DIR == DIR_REV) ? __ldg(g.tmi + x) : co.uic_tm1;
+        const long long seg = __ldg(hpref + h) * co.W + (long long)word * deg;
+        const uint64_t wm = word_mask(word, co.R);
+        const int a0 = blk * HB_ARCS, a1 = min(deg, a0 + HB_ARCS);
+        for (int j0 = a0; j0 < a1; j0 += 32) {
+            const int j = j0 + lane;
+            uint64_t mk = 0;
+            int y = 0;
+            if (j < a1) {
+                uint32_t eid, tm1;
+                arc_at<DIR, MODEL>(g, beg + j, rtm1, y, eid, tm1);
+                mk = live_bits(co, eid, (uint32_t)word * 64u, wm, tm1);
+            }
+            const unsigned bal = __ballot_sync(FULL, mk != 0);
+            if (bal) {
+                int pos0 = 0;
+                if (lane == 0) pos0 = atomicAdd(&hcnt[(long long)h * co.W + word], __popc(bal));
+                pos0 = __shfl_sync(FULL, pos0, 0);
+                if (mk) {
+                    const long long q = seg + pos0 + __popc(bal & ((1u << lane) - 1u));
+                    hnbr[q] = y;
+                    hmask[q] = mk;
+                }
+            }
+        }
+    }
+}
+
+// Tier-2 tables start empty: keys EMPTY, state words and counters zero.
+__global__ void t2_clear_kernel(unsigned char *tab, int warps)
+{
+    for (long long w = blockIdx.x; w < warps; w += gridDim.x) {
+        const WTab T = tab_at<T2_LOGC>(tab + (size_t)w * tab_bytes<T2_LOGC>());
+        for (int i = threadIdx.x; i < (1 << T2_LOGC); i += blockDim.x) {
+            T.key[i] = EMPTY_KEY;
+            T.vis[i] = 0;
+            T.pend[i] = 0;
+        }
+        if (threadIdx.x < 4) T.ctr[threadIdx.x] = 0;
     }
 }
 
@@ -801,93 +1050,103 @@ __global__ void live_masks_kernel(Coins co, long long m, const uint2 *fw, uint32
 
 // ================================================================ launches
 
-constexpr int WE_LOGC = 9;  // 512-entry table per warp
-constexpr int WE_THREADS = 128;
-
-template <int DIR, int MODEL, int TASK>
-sg_status launch_warp_engine(sg_graph *g, const EngineArgs &a, cudaStream_t st)
-{
-    auto kern = warp_engine_kernel<WE_LOGC, DIR, MODEL, TASK>;
-    const size_t smem = (WE_THREADS / 32) * sizeof(WarpTab<WE_LOGC>);
-    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    SG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WE_THREADS, smem));
-    if (per_sm < 1) per_sm = 1;
-    kern<<<g->num_sms * per_sm, WE_THREADS, smem, st>>>(a);
-    SG_CUDA_TRY(cudaGetLastError());
-    ++g_launches;
-    return SG_OK;
-}
-
-template <int DIR, int MODEL, int TASK>
-sg_status launch_cta_engine(sg_graph *g, const BigArgs &a, cudaStream_t st)
-{
-    cta_engine_kernel<DIR, MODEL, TASK><<<g->ws.nslots, BT, 0, st>>>(a);
-    SG_CUDA_TRY(cudaGetLastError());
-    ++g_launches;
-    return SG_OK;
-}
-
-EngineArgs engine_args(sg_graph *g, const Coins &co)
+EngineArgs engine_args(sg_graph *g, const Coins &co, int heavy_on)
 {
     sg_workspace &ws = g->ws;
     EngineArgs a;
-    a.g = view_of(g);
+    a.g = view_of(g, heavy_on);
     a.co = co;
     a.ctl = ws.ctl.p;
     a.s = ws.s.p;
-    a.du_off = ws.du_off.p;
-    a.du_x = ws.du_x.p;
-    a.du_m = ws.du_m.p;
-    a.big_list = ws.big_list.p;
+    a.tl = ws.tl.p;
+    a.toff = ws.toff.p;
+    a.tcnt = ws.tcnt.p;
+    a.coff = ws.coff.p;
+    a.list1 = ws.list1.p;
+    a.list2 = ws.list2.p;
+    a.t2_tab = ws.t2_tab.p;
     a.ntasks = 0;
-    a.chunk = 8;
+    a.limit = 1;
     return a;
 }
 
-BigArgs big_args(sg_graph *g, const Coins &co)
+SlotArgs slot_args(sg_graph *g)
 {
     sg_workspace &ws = g->ws;
-    BigArgs a;
-    a.g = view_of(g);
-    a.co = co;
-    a.ctl = ws.ctl.p;
-    a.s = ws.s.p;
-    a.du_off = ws.du_off.p;
-    a.du_x = ws.du_x.p;
-    a.du_m = ws.du_m.p;
-    a.big_list = ws.big_list.p;
-    a.slot_vis = ws.slot_vis.p;
-    a.slot_pend = ws.slot_pend.p;
-    a.slot_qa = ws.slot_qa.p;
-    a.slot_qb = ws.slot_qb.p;
-    a.slot_touched = ws.slot_touched.p;
-    return a;
+    SlotArgs s;
+    s.vis = ws.slot_vis.p;
+    s.pend = ws.slot_pend.p;
+    s.qa = ws.slot_qa.p;
+    s.qb = ws.slot_qb.p;
+    s.touched = ws.slot_touched.p;
+    return s;
 }
 
-template <int MODEL>
-sg_status init_gains_t(sg_graph *g, const Coins &co, cudaStream_t st, cudaEvent_t after_warp)
+// tier 1 -> tier 2 -> tier 3 for one task family
+template <int DIR, int MODEL, int TASK>
+sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, cudaEvent_t after_t1)
 {
-    EngineArgs a = engine_args(g, co);
-    a.ntasks = (long long)g->n * co.W;
-    SG_TRY((launch_warp_engine<DIR_FWD, MODEL, TASK_INIT>(g, a, st)));
-    if (after_warp) SG_CUDA_TRY(cudaEventRecord(after_warp, st));
-    SG_TRY((launch_cta_engine<DIR_FWD, MODEL, TASK_INIT>(g, big_args(g, co), st)));
+    EngineArgs a = a0;
+    {
+        a.limit = std::max(1, std::min(g_tier_limit[0], (1 << T1_LOGC) / 2));
+        auto kern = warp_engine_kernel<T1_LOGC, DIR, MODEL, TASK, 1>;
+        const size_t smem = (WE_THREADS / 32) * tab_bytes<T1_LOGC>();
+        SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        SG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WE_THREADS, smem));
+        if (per_sm < 1) per_sm = 1;
+        kern<<<g->num_sms * per_sm, WE_THREADS, smem, st>>>(a, 8);
+        SG_CUDA_TRY(cudaGetLastError());
+        ++g_launches;
+    }
+    if (after_t1) SG_CUDA_TRY(cudaEventRecord(after_t1, st));
+    a.limit = std::max(1, std::min(g_tier_limit[1], (1 << T2_LOGC) / 2));
+    warp_engine_kernel<T2_LOGC, DIR, MODEL, TASK, 2>
+        <<<g->ws.t2_warps / (WE_THREADS / 32), WE_THREADS, 0, st>>>(a, 1);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
+    cta_engine_kernel<DIR, MODEL, TASK><<<g->ws.nslots, BT, 0, st>>>(a, slot_args(g));
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
+    return SG_OK;
+}
+
+template <int DIR, int MODEL>
+sg_status launch_index(sg_graph *g, const Coins &co, cudaStream_t st)
+{
+    sg_workspace &ws = g->ws;
+    const bool fwd = DIR == DIR_FWD;
+    const int nh = fwd ? g->nh_out : g->nh_in;
+    if (nh == 0) return SG_OK;
+    int32_t *hcnt = fwd ? ws.hcnt_out.p : ws.hcnt_in.p;
+    SG_CUDA_TRY(cudaMemsetAsync(hcnt, 0, (size_t)nh * co.W * sizeof(int32_t), st));
+    heavy_index_kernel<DIR, MODEL><<<g->num_sms * 8, 256, 0, st>>>(
+        view_of(g, 1), co, fwd ? g->hrow_out.p : g->hrow_in.p, fwd ? g->hcpref_out.p : g->hcpref_in.p, nh, hcnt,
+        fwd ? ws.hnbr_out.p : ws.hnbr_in.p, fwd ? ws.hmask_out.p : ws.hmask_in.p,
+        fwd ? g->hpref_out.p : g->hpref_in.p);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
     return SG_OK;
 }
 
 template <int MODEL>
-sg_status round_t(sg_graph *g, const Coins &co, int32_t round, cudaStream_t st)
+sg_status init_gains_t(sg_graph *g, const Coins &co, int heavy_on, cudaStream_t st, cudaEvent_t after_t1)
+{
+    EngineArgs a = engine_args(g, co, heavy_on);
+    a.ntasks = (long long)g->n * co.W;
+    return launch_tiers<DIR_FWD, MODEL, TASK_INIT>(g, a, st, after_t1);
+}
+
+template <int MODEL>
+sg_status round_t(sg_graph *g, const Coins &co, int heavy_on, int32_t round, cudaStream_t st, cudaEvent_t after_fwd)
 {
     sg_workspace &ws = g->ws;
     argmax_kernel<<<ws.am_blocks, AM_T, 0, st>>>(ws.s.p, (int)g->n, ws.ctl.p, ws.am_gain.p, ws.am_id.p,
                                                  ws.out_seeds.p, ws.out_gains.p, round);
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
+    EngineArgs a = engine_args(g, co, heavy_on);
     FwdArgs f;
-    f.g = view_of(g);
-    f.co = co;
-    f.ctl = ws.ctl.p;
     f.cov = ws.cov.p;
     f.nbits = ws.nbits.p;
     f.pendf = ws.pendf.p;
@@ -895,30 +1154,46 @@ sg_status round_t(sg_graph *g, const Coins &co, int32_t round, cudaStream_t st)
     f.fq_a = ws.fq_a.p;
     f.fq_b = ws.fq_b.p;
     f.du_x = ws.du_x.p;
-    f.du_off = ws.du_off.p;
     f.du_cnt = ws.du_cnt.p;
-    fwd_du_kernel<MODEL><<<co.W, BT, 0, st>>>(f);
+    f.tl = ws.tl.p;
+    f.toff = ws.toff.p;
+    f.coff = ws.coff.p;
+    f.tcnt = ws.tcnt.p;
+    f.tcap = 64 * g->n;
+    fwd_du_kernel<MODEL><<<co.W, BT, 0, st>>>(a, f);
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
-    EngineArgs a = engine_args(g, co);
-    SG_TRY((launch_warp_engine<DIR_REV, MODEL, TASK_REV>(g, a, st)));
-    SG_TRY((launch_cta_engine<DIR_REV, MODEL, TASK_REV>(g, big_args(g, co), st)));
-    return SG_OK;
+    if (after_fwd) SG_CUDA_TRY(cudaEventRecord(after_fwd, st));
+    return launch_tiers<DIR_REV, MODEL, TASK_REVT>(g, a, st, nullptr);
 }
 
 }  // namespace
 
 thread_local int g_launches = 0;
+int g_tier_limit[2] = {(1 << T1_LOGC) / 2, (1 << T2_LOGC) / 2};
 
-sg_status run_init_gains(sg_graph *g, const Coins &co, int model, cudaStream_t st, cudaEvent_t after_warp)
+sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t st)
 {
-    return model == MODEL_WIC ? init_gains_t<MODEL_WIC>(g, co, st, after_warp)
-                              : init_gains_t<MODEL_UIC>(g, co, st, after_warp);
+    if (model == MODEL_WIC) {
+        SG_TRY((launch_index<DIR_FWD, MODEL_WIC>(g, co, st)));
+        return launch_index<DIR_REV, MODEL_WIC>(g, co, st);
+    }
+    SG_TRY((launch_index<DIR_FWD, MODEL_UIC>(g, co, st)));
+    return launch_index<DIR_REV, MODEL_UIC>(g, co, st);
 }
 
-sg_status run_round(sg_graph *g, const Coins &co, int model, int32_t round, cudaStream_t st)
+sg_status run_init_gains(sg_graph *g, const Coins &co, int model, int heavy_on, cudaStream_t st,
+                         cudaEvent_t after_t1)
 {
-    return model == MODEL_WIC ? round_t<MODEL_WIC>(g, co, round, st) : round_t<MODEL_UIC>(g, co, round, st);
+    return model == MODEL_WIC ? init_gains_t<MODEL_WIC>(g, co, heavy_on, st, after_t1)
+                              : init_gains_t<MODEL_UIC>(g, co, heavy_on, st, after_t1);
+}
+
+sg_status run_round(sg_graph *g, const Coins &co, int model, int heavy_on, int32_t round, cudaStream_t st,
+                    cudaEvent_t after_fwd)
+{
+    return model == MODEL_WIC ? round_t<MODEL_WIC>(g, co, heavy_on, round, st, after_fwd)
+                              : round_t<MODEL_UIC>(g, co, heavy_on, round, st, after_fwd);
 }
 
 sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st)
@@ -930,6 +1205,16 @@ sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out,
                                               reinterpret_cast<unsigned long long *>(out));
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
+    return SG_OK;
+}
+
+size_t t2_table_bytes() { return tab_bytes<T2_LOGC>(); }
+
+sg_status run_t2_clear(unsigned char *tab, int warps, cudaStream_t st)
+{
+    if (warps <= 0) return SG_OK;
+    t2_clear_kernel<<<std::min(warps, 4096), 256, 0, st>>>(tab, warps);
+    SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 

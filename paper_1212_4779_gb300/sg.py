@@ -27,7 +27,7 @@ _STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ETI
            6: "SG_EINTERNAL"}
 
 # exported entry points, as declared in include/sg.h
-EXPORTS = ("sg_set_allocator", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+EXPORTS = ("sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
            "sg_init_gains", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
 
 
@@ -43,10 +43,13 @@ class sg_cascade(ctypes.Structure):
 
 class sg_stats(ctypes.Structure):
     _fields_ = [("init_edges", ctypes.c_uint64), ("fwd_edges", ctypes.c_uint64), ("rev_edges", ctypes.c_uint64),
-                ("init_big_tasks", ctypes.c_uint64), ("rev_big_tasks", ctypes.c_uint64),
-                ("du_entries", ctypes.c_uint64), ("ms_init", ctypes.c_float), ("ms_rounds", ctypes.c_float),
-                ("ms_total", ctypes.c_float), ("ms_init_warp", ctypes.c_float), ("status_flags", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int32)]
+                ("init_tier2_tasks", ctypes.c_uint64), ("init_tier3_tasks", ctypes.c_uint64),
+                ("rev_tier2_tasks", ctypes.c_uint64), ("rev_tier3_tasks", ctypes.c_uint64),
+                ("rev_tasks", ctypes.c_uint64), ("du_entries", ctypes.c_uint64),
+                ("ms_index", ctypes.c_float), ("ms_init", ctypes.c_float), ("ms_init_tier1", ctypes.c_float),
+                ("ms_rounds", ctypes.c_float), ("ms_fwd", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("status_flags", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("heavy_index", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +79,8 @@ def lib() -> ctypes.CDLL:
         L = ctypes.CDLL(_LIB_PATH)
         P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
         L.sg_set_allocator.argtypes = [_ALLOC_FN, _RELEASE_FN, P]
+        L.sg_set_heavy_threshold.argtypes = [i32]
+        L.sg_set_engine_limits.argtypes = [i32, i32]
         L.sg_load_graph.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_load_graph_coo.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -87,7 +92,7 @@ def lib() -> ctypes.CDLL:
         L.sg_free_graph.restype = None
         L.sg_last_error.restype = ctypes.c_char_p
         L.sg_version.restype = ctypes.c_char_p
-        for name in ("sg_set_allocator", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+        for name in ("sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
                      "sg_init_gains", "sg_live_masks", "sg_graph_csr"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -192,6 +197,16 @@ def sg_set_allocator(alloc=None, release=None):
              _RELEASE_FN(lambda ptr, nb, st, ctx: release(int(ptr), int(nb), int(st or 0))))
     _check(lib().sg_set_allocator(hooks[0], hooks[1], None))
     _hooks = hooks
+
+
+def sg_set_heavy_threshold(min_degree: int):
+    """Heavy-row live-index threshold for graphs loaded afterwards (0: off)."""
+    _check(lib().sg_set_heavy_threshold(int(min_degree)))
+
+
+def sg_set_engine_limits(tier1_keys: int = 256, tier2_keys: int = 8192):
+    """Visited-set sizes at which tasks move to the next engine tier."""
+    _check(lib().sg_set_engine_limits(int(tier1_keys), int(tier2_keys)))
 
 
 def sg_load_graph(n, m, row_ptr, col, stream=None):

@@ -100,17 +100,87 @@ def test_init_gains_match_oracle(sg, name, R):
     assert ed == ed_want
 
 
-def test_big_tasks_take_the_cta_engine_and_agree(sg):
+def test_big_tasks_take_the_upper_tiers_and_agree(sg):
     """High-probability cascade: most sources reach hundreds of nodes per
-    64-snapshot word, so the warp engine hands them to the CTA engine."""
+    64-snapshot word, so the shared-memory warp tables overflow and tasks
+    move to the global-table tier."""
     n, s, d = inputs.chung_lu_undirected(3000, 12000, 2.5, 8.0, 31)
     g, o = _both(sg, n, s, d, "uic", 0.3)
     res = g.select(96, 8, "uic", 0.3, 4, stats=True)
     ref = o.select(96, 8, 4, mode=oracle.DU)
-    assert res.stats["init_big_tasks"] > 0
+    assert res.stats["init_tier2_tasks"] > 0
     assert np.array_equal(res.seeds, ref["seeds"])
     assert np.array_equal(res.gains, ref["gains"])
     assert [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]] == list(map(int, ref["counters"]))
+
+
+@pytest.fixture
+def limits(sg):
+    yield sg.sg_set_engine_limits
+    sg.sg_set_engine_limits(256, 8192)
+    sg.sg_set_heavy_threshold(64)
+
+
+@pytest.mark.parametrize("t1,t2", [(1, 1), (4, 32), (16, 300), (256, 8192)])
+@pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01"])
+def test_every_tier_gives_identical_results(sg, limits, name, t1, t2):
+    """Tiny table limits push tasks through all three engine tiers; the
+    seeds, gains and counters must not change."""
+    wl = inputs.workload(name)
+    n, s, d = wl.graph()
+    g, o = _both(sg, n, s, d, wl.model, wl.p)
+    limits(t1, t2)
+    k = 12
+    res = g.select(wl.R, k, wl.model, wl.p, wl.seed, stats=True)
+    ref = o.select(wl.R, k, wl.seed, mode=oracle.DU)
+    assert np.array_equal(res.seeds, ref["seeds"])
+    assert np.array_equal(res.gains, ref["gains"])
+    got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+    assert got == [int(x) for x in ref["counters"]]
+    if t2 <= 32:
+        assert res.stats["init_tier3_tasks"] > 0 and res.stats["rev_tier3_tasks"] > 0
+    if t1 <= 4:
+        assert res.stats["init_tier2_tasks"] > 0 and res.stats["rev_tier2_tasks"] > 0
+
+
+@pytest.mark.parametrize("heavy", [0, 2, 8, 64])
+@pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01", "er2k_uic0.1"])
+def test_heavy_index_threshold_gives_identical_results(sg, limits, name, heavy):
+    """The per-query live index of heavy rows is a cache of the same coins:
+    any threshold (0 = none, 2 = nearly every row) gives the same result."""
+    wl = inputs.workload(name)
+    n, s, d = wl.graph()
+    sg.sg_set_heavy_threshold(heavy)
+    g = sg.Graph.from_coo(n, s, d)
+    o = oracle.Graph(n, s, d, wl.model, wl.p)
+    k = 10
+    res = g.select(wl.R, k, wl.model, wl.p, wl.seed, stats=True)
+    ref = o.select(wl.R, k, wl.seed, mode=oracle.DU)
+    assert res.stats["heavy_index"] == (1 if heavy else 0) or heavy > 1000
+    assert np.array_equal(res.seeds, ref["seeds"])
+    assert np.array_equal(res.gains, ref["gains"])
+    got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+    assert got == [int(x) for x in ref["counters"]]
+    s_gpu, ed = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
+    s_ref, ed_ref = o.init_gains(wl.R, wl.seed)
+    assert np.array_equal(s_gpu, s_ref) and ed == ed_ref
+
+
+def test_giant_component_reaches_tier3_and_agrees(sg):
+    """p = 1 on a connected graph: every task reaches all n > 8192 nodes, so
+    initial-gain tasks run in the block-wide dense engine."""
+    n, s, d = inputs.chung_lu_undirected(9000, 30000, 2.5, 6.0, 41)
+    p_ = np.arange(n - 1, dtype=np.int32)
+    s = np.concatenate([s, p_, p_ + 1])
+    d = np.concatenate([d, p_ + 1, p_])
+    g, o = _both(sg, n, s, d, "uic", 1.0)
+    res = g.select(2, 3, "uic", 1.0, 5, stats=True)
+    ref = o.select(2, 3, 5, mode=oracle.DU)
+    assert res.stats["init_tier3_tasks"] > 0
+    assert list(res.gains) == [2 * n, 0, 0] and list(res.seeds) == [0, 1, 2]
+    assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+    got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+    assert got == [int(x) for x in ref["counters"]]
 
 
 # ---------------------------------------------------------- full selection
