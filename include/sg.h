@@ -121,7 +121,7 @@ sg_status sg_set_heavy_threshold(int32_t min_degree);
 /* Traversal-engine limits: a task whose visited set grows past tier1_keys
  * nodes leaves the per-warp shared-memory table for a per-warp global
  * table, and past tier2_keys nodes for a whole-block engine with dense
- * arrays.  Values are clamped to 256 and 8192 (the defaults).  A tuning and
+ * arrays.  Values are clamped to 256 and 4096 (the defaults).  A tuning and
  * testing knob: results do not depend on it.  Applies to later calls.
  * Errors: SG_EINVAL if either is < 1. */
 sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys);

@@ -158,7 +158,9 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.coff, st);
     dbuf_free(ws.tcnt, st);
     dbuf_free(ws.du_cnt, st);
-    dbuf_free(ws.t2_tab, st);
+    dbuf_free(ws.anc, st);
+    dbuf_free(ws.anc_list, st);
+    dbuf_free(ws.anc_cnt, st);
     dbuf_free(ws.hcnt_out, st);
     dbuf_free(ws.hnbr_out, st);
     dbuf_free(ws.hmask_out, st);
@@ -166,11 +168,9 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.hnbr_in, st);
     dbuf_free(ws.hmask_in, st);
     ws.hw_cap = 0;
-    ws.t2_warps = 0;
     dbuf_free(ws.slot_vis, st);
     dbuf_free(ws.slot_pend, st);
     dbuf_free(ws.slot_qa, st);
-    dbuf_free(ws.slot_qb, st);
     dbuf_free(ws.slot_touched, st);
     dbuf_free(ws.ctl, st);
     dbuf_free(ws.am_gain, st);
@@ -391,25 +391,28 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
         SG_TRY(dbuf_alloc(ws.coff, (size_t)64 * W + 1, st));
         SG_TRY(dbuf_alloc(ws.tcnt, (size_t)64 * W, st));
         SG_TRY(dbuf_alloc(ws.du_cnt, (size_t)W, st));
+        SG_TRY(dbuf_alloc(ws.anc, nw, st));
+        SG_TRY(dbuf_alloc(ws.anc_list, nw, st));
+        SG_TRY(dbuf_alloc(ws.anc_cnt, (size_t)W, st));
         SG_TRY(dbuf_alloc(ws.ctl, 1, st));
-        // tier-2 warp tables (global memory), cleared once, left clean by every task
-        ws.t2_warps = g->num_sms * 2 * 4;
-        SG_TRY(dbuf_alloc(ws.t2_tab, (size_t)ws.t2_warps * t2_table_bytes(), st));
-        SG_TRY(run_t2_clear(ws.t2_tab.p, ws.t2_warps, st));
+
         SG_CUDA_TRY(cudaMemsetAsync(ws.nbits.p, 0, ws.nbits.bytes, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.pendf.p, 0, ws.pendf.bytes, st));
-        // CTA-engine slots: dense per-slot arrays, at most ~2 GiB in total
-        const size_t per_slot = (size_t)n * (2 * sizeof(unsigned long long) + 3 * sizeof(int32_t));
-        const size_t budget = (size_t)2 << 30;
-        int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms, budget / per_slot));
+        // tier-3 slots: dense per-slot arrays (vis, pend, ring queue, touched), <= ~4 GiB in total
+        int qcap = 1;
+        while (qcap < n) qcap <<= 1;
+        const size_t per_slot = (size_t)n * (2 * sizeof(unsigned long long) + sizeof(int32_t)) + (size_t)qcap * 4;
+        const size_t budget = (size_t)4 << 30;
+        int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms * 2, budget / per_slot));
         const size_t ns = (size_t)slots * (size_t)n;
         SG_TRY(dbuf_alloc(ws.slot_vis, ns, st));
         SG_TRY(dbuf_alloc(ws.slot_pend, ns, st));
-        SG_TRY(dbuf_alloc(ws.slot_qa, ns, st));
-        SG_TRY(dbuf_alloc(ws.slot_qb, ns, st));
+        SG_TRY(dbuf_alloc(ws.slot_qa, (size_t)slots * (size_t)qcap, st));
         SG_TRY(dbuf_alloc(ws.slot_touched, ns, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.slot_vis.p, 0, ws.slot_vis.bytes, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.slot_pend.p, 0, ws.slot_pend.bytes, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.slot_qa.p, 0xff, ws.slot_qa.bytes, st));
+        ws.slot_qmask = qcap - 1;
         ws.am_blocks = g->num_sms * 2;
         SG_TRY(dbuf_alloc(ws.am_gain, (size_t)ws.am_blocks, st));
         SG_TRY(dbuf_alloc(ws.am_id, (size_t)ws.am_blocks, st));
@@ -704,6 +707,8 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     }
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.cov.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
+    SG_CUDA_TRY(cudaMemsetAsync(ws.anc.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
+    SG_CUDA_TRY(cudaMemsetAsync(ws.anc_cnt.p, 0, (size_t)co.W * 4, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) SG_TRY(run_heavy_index(g, co, model, st));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_index, st));

@@ -20,7 +20,9 @@
 //   nbits uint64[W][n]    bits newly covered in the current round
 //   pendf uint64[W][n]    forward-DU frontier bits not yet expanded
 //   du_x / du_m [W][n]    newly covered (node, mask) list of the round, per word
-//   tl    int32[W][64n]   newly covered nodes of the round, per snapshot
+//   tl    int32[W][64n]   newly covered nodes of the round, per snapshot,
+//                         minus those that reach the round's seed
+//   anc   uint64[W][n]    bit b: the node reaches the round's seed in snapshot 64w+b
 //   heavy live index, per direction: for heavy row h and word w the
 //     nonzero 64-snapshot live masks of its arcs, compacted in arc order:
 //     hcnt[h*W+w] entries at hnbr/hmask[hpref[h]*W + w*deg(h) ...]
@@ -148,16 +150,18 @@ struct sg_workspace {
     int64_t n = 0;
     int32_t wcap = 0;     // words of capacity of the [W][n] arrays
     int32_t nslots = 0;   // tier-3 (CTA engine) slots
-    int32_t t2_warps = 0; // tier-2 warp tables
     sgi::DBuf<long long> s;
     sgi::DBuf<unsigned long long> cov, nbits, pendf, du_m;
     sgi::DBuf<int32_t> fq_a, fq_b, du_x, list1, list2, tl;
     sgi::DBuf<long long> toff, coff;     // per snapshot: target list offset, chunk-task offset [64W+1]
     sgi::DBuf<int32_t> tcnt;             // per snapshot: newly covered count [64W]
     sgi::DBuf<int32_t> du_cnt;           // [W] entries per word
+    sgi::DBuf<unsigned long long> anc;   // [W][n] ancestors of the round's seed, per snapshot bit
+    sgi::DBuf<int32_t> anc_list;         // [W][n] nodes with ancestor bits set
+    sgi::DBuf<int32_t> anc_cnt;          // [W]
     sgi::DBuf<unsigned long long> slot_vis, slot_pend;
-    sgi::DBuf<int32_t> slot_qa, slot_qb, slot_touched;
-    sgi::DBuf<unsigned char> t2_tab;     // tier-2 global hash tables
+    sgi::DBuf<int32_t> slot_qa, slot_touched;
+    int32_t slot_qmask = 0;              // tier-3 per-slot queue: ring of slot_qmask+1 entries (in slot_qa)
     sgi::DBuf<sgi::Ctl> ctl;
     sgi::DBuf<long long> am_gain;        // argmax per-block partials
     sgi::DBuf<int32_t> am_id;
@@ -198,7 +202,7 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st);
 sg_status ensure_heavy_index(sg_graph *g, int32_t W, cudaStream_t st);
 sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out);
 bool heavy_index_enabled(const sg_graph *g, int32_t W);
-size_t t2_table_bytes();
+
 
 // kernels launched by this thread since the counter was last reset
 extern thread_local int g_launches;
@@ -212,6 +216,6 @@ sg_status run_init_gains(sg_graph *g, const Coins &co, int model, int heavy_on, 
 sg_status run_round(sg_graph *g, const Coins &co, int model, int heavy_on, int32_t round, cudaStream_t st,
                     cudaEvent_t after_fwd = nullptr);
 sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st);
-sg_status run_t2_clear(unsigned char *tab, int warps, cudaStream_t st);
+
 
 }  // namespace sgi

@@ -23,10 +23,13 @@
 //   tier 1  one warp per task, visited/pending words in a 512-slot
 //           shared-memory hash table; frontier expanded 32 elements at a
 //           time with a load-balanced (prefix sum + shuffle search) split.
-//   tier 2  the same warp engine over a 16384-slot table in global memory,
-//           for tasks that filled the tier-1 table past half.
-//   tier 3  one 512-thread block per task over dense per-block arrays,
-//           level-synchronous; also runs the forward dynamic update.
+//   tier 2  one 16-warp block per task sharing an 8192-slot shared-memory
+//           table and an asynchronous ring queue, for tasks that filled the
+//           tier-1 table past its limit.
+//   tier 3  the same cooperative engine over dense per-block arrays in
+//           global memory (no limit).
+//   The forward dynamic update and the ancestor walk run a level-
+//   synchronous block traversal over the coverage bitsets.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,11 +46,10 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr long long SEED_MARK = -(1LL << 62);
 
 enum { DIR_FWD = 0, DIR_REV = 1 };
-enum { TASK_INIT = 0, TASK_REVT = 1, TASK_FWD = 2 };
+enum { TASK_INIT = 0, TASK_REVT = 1, TASK_FWD = 2, TASK_ANC = 3 };
 enum { SLICE_SNAP = 0, SLICE_TGT = 1 };
 
 constexpr int T1_LOGC = 9;   // tier-1 table: 512 slots per warp (shared memory)
-constexpr int T2_LOGC = 14;  // tier-2 table: 16384 slots per warp (global memory)
 constexpr int WE_THREADS = 128;
 constexpr int HB_ARCS = 1024;  // heavy-index build: arcs per work item
 
@@ -198,7 +200,7 @@ struct EngineArgs {
     const int32_t *tcnt;    // [64W] list lengths
     const long long *coff;  // [64W+1] chunk-task offsets
     int32_t *list1, *list2;
-    unsigned char *t2_tab;
+    const unsigned long long *anc;  // [W][n] ancestors of v*, per snapshot bit (this round)
     long long ntasks;       // TASK_INIT: n * W
     int limit;              // keys a warp table may hold before the task moves up a tier
 };
@@ -364,7 +366,10 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
             const uint64_t iF = __shfl_sync(FULL, F, lo);
             if (j < total) {
                 int y;
-                const uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y);
+                uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y);
+                // nodes reaching v* in this snapshot were settled by the ancestor pass
+                if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
+                    ml = 0;
                 if (ml) {
                     const int h = table_slot<LOGC>(T, y, LIMIT);
                     if (h >= 0) {
@@ -417,53 +422,39 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
     return ovf != 0;
 }
 
-// TIER 1: tasks [0, ntasks) by dynamic chunks, shared-memory tables;
-// TIER 2: the tasks tier 1 gave up on, global-memory tables (clean on entry
-// and on exit).  Overflowing tasks are listed for the next tier.
-template <int LOGC, int DIR, int MODEL, int TASK, int TIER>
+// Tier 1: tasks [0, ntasks) by dynamic chunks, one warp per task with a
+// shared-memory table; tasks that overflow it are listed for tier 2.
+template <int LOGC, int DIR, int MODEL, int TASK>
 __global__ void __launch_bounds__(WE_THREADS) warp_engine_kernel(EngineArgs a, int chunk)
 {
     constexpr int C = 1 << LOGC;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    WTab T;
-    if (TIER == 1) {
-        extern __shared__ __align__(16) unsigned char smem_raw[];
-        T = tab_at<LOGC>(smem_raw + (size_t)wib * tab_bytes<LOGC>());
-        for (int i = lane; i < C; i += 32) {
-            T.key[i] = EMPTY_KEY;
-            T.vis[i] = 0;
-            T.pend[i] = 0;
-        }
-        if (lane == 0) {
-            T.ctr[0] = 0;
-            T.ctr[1] = 0;
-            T.ctr[2] = 0;
-        }
-        __syncwarp();
-    } else {
-        const size_t gw = (size_t)blockIdx.x * (WE_THREADS / 32) + wib;
-        T = tab_at<LOGC>(a.t2_tab + gw * tab_bytes<LOGC>());
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const WTab T = tab_at<LOGC>(smem_raw + (size_t)wib * tab_bytes<LOGC>());
+    for (int i = lane; i < C; i += 32) {
+        T.key[i] = EMPTY_KEY;
+        T.vis[i] = 0;
+        T.pend[i] = 0;
     }
+    if (lane == 0) {
+        T.ctr[0] = 0;
+        T.ctr[1] = 0;
+        T.ctr[2] = 0;
+    }
+    __syncwarp();
     Ctl *ctl = a.ctl;
-    long long ntasks;
-    if (TIER == 1) ntasks = TASK == TASK_INIT ? a.ntasks : *(volatile long long *)&ctl->du_total;
-    else ntasks = (long long)*(volatile unsigned long long *)&ctl->l1_count;
+    const long long ntasks = TASK == TASK_INIT ? a.ntasks : *(volatile long long *)&ctl->du_total;
     unsigned long long edges = 0;
     while (true) {
         long long base = 0;
-        if (lane == 0)
-            base = (long long)atomicAdd(TIER == 1 ? &ctl->t1_next : &ctl->l1_next, (unsigned long long)chunk);
+        if (lane == 0) base = (long long)atomicAdd(&ctl->t1_next, (unsigned long long)chunk);
         base = __shfl_sync(FULL, base, 0);
         if (base >= ntasks) break;
         const long long tend = min(base + (long long)chunk, ntasks);
-        for (long long q = base; q < tend; ++q) {
-            const long long t = TIER == 1 ? q : (long long)a.list1[q];
+        for (long long t = base; t < tend; ++t) {
             const bool ovf = warp_task<LOGC, DIR, MODEL, TASK>(a, T, t, lane, edges);
-            if (ovf && lane == 0) {
-                if (TIER == 1) a.list1[atomicAdd(&ctl->l1_count, 1ull)] = (int32_t)t;
-                else a.list2[atomicAdd(&ctl->l2_count, 1ull)] = (int32_t)t;
-            }
+            if (ovf && lane == 0) a.list1[atomicAdd(&ctl->l1_count, 1ull)] = (int32_t)t;
         }
     }
     edges = warp_sum(edges);
@@ -544,12 +535,15 @@ struct CtaState {
 // One traversal by the whole block over dense arrays, level-synchronous.
 // TASK_INIT / TASK_REVT: vis/pend are a zeroed slot and are zero again on
 // return.  TASK_FWD: vis is the word's coverage bitset; every node gaining
-// bits is listed once, its merged new bits left in nbits.
-// Seeds: INIT (x0, all bits of the word); REVT the targets tgt[0..ntgt)
-// with one bit each; FWD x0 = v* with the word's bits not yet covered.
+// bits is listed once, its merged new bits left in nbits.  TASK_ANC:
+// reverse walk from v* over the snapshots where v* newly covers nodes; vis
+// (the word's ancestor bits) is kept, and every ancestor u loses
+// sum over its bits r of |N_r| (= ncov[r]) from its gain.
+// Seeds: INIT, FWD, ANC: x0 with bits M0 (FWD: minus what is covered);
+// REVT: the targets tgt[0..ntgt) with one bit each.
 template <int DIR, int MODEL, int TASK>
-__device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint32_t rs, const int32_t *tgt,
-                        int ntgt, CtaShared &S)
+__device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, int word, uint32_t rs,
+                        const int32_t *tgt, int ntgt, const int *ncov, CtaShared &S)
 {
     constexpr int SLICE = TASK == TASK_REVT ? SLICE_TGT : SLICE_SNAP;
     const GraphView &g = a.g;
@@ -576,7 +570,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint3
             S.ntouch = ntgt;
         }
     } else if (tid == 0) {
-        uint64_t M = word_mask(word, co.R);
+        uint64_t M = M0;
         if (TASK == TASK_FWD) M &= ~w.vis[x0];
         if (M) {
             w.vis[x0] |= M;
@@ -590,7 +584,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint3
             } else {
                 w.touched[0] = x0;
                 S.ntouch = 1;
-                cnt = __popcll(M);
+                if (TASK == TASK_INIT) cnt = __popcll(M);
             }
         }
     }
@@ -612,7 +606,8 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint3
                 S.base[tid] = rr.base;
                 S.heavy[tid] = rr.heavy;
                 S.tm1[tid] = rr.rtm1;
-                if (TASK != TASK_REVT) edges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
+                if (TASK == TASK_INIT || TASK == TASK_FWD)
+                    edges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
             }
             int total;
             const int ex = block_excl_scan(vd, S, &total);
@@ -629,8 +624,10 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint3
                         else hi = mid - 1;
                     }
                     int y;
-                    const uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, S.base[lo], S.heavy[lo], S.tm1[lo],
-                                                                j - S.ex[lo], S.F[lo], rs, y);
+                    uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, S.base[lo], S.heavy[lo], S.tm1[lo], j - S.ex[lo],
+                                                          S.F[lo], rs, y);
+                    if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
+                        ml = 0;
                     if (ml) {
                         const uint64_t old = atomicOr(&w.vis[y], (unsigned long long)ml);
                         const uint64_t nw = ml & ~old;
@@ -658,7 +655,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint3
         nxt = tmp;
         __syncthreads();
     }
-    if (TASK != TASK_FWD) {
+    if (TASK == TASK_INIT || TASK == TASK_REVT) {
         const int nt = S.ntouch;
         for (int i = tid; i < nt; i += BT) {
             const int y = w.touched[i];
@@ -669,6 +666,20 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint3
             }
             w.vis[y] = 0;
         }
+    } else if (TASK == TASK_ANC) {
+        const int nt = S.ntouch;
+        for (int i = tid; i < nt; i += BT) {
+            const int y = w.touched[i];
+            uint64_t b = w.vis[y];
+            long long d = 0;
+            while (b) {
+                const int k = __ffsll((long long)b) - 1;
+                b &= b - 1;
+                d += ncov[k];
+            }
+            atomicAdd((unsigned long long *)&a.s[y], (unsigned long long)(-d));
+            edges += (unsigned long long)d * (unsigned long long)(__ldg(g.crp + y + 1) - __ldg(g.crp + y));
+        }
     }
     const unsigned long long e_tot = block_sum(edges, S.red_ull);
     if (TASK == TASK_INIT) {
@@ -677,7 +688,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint3
     }
     if (tid == 0 && e_tot) {
         unsigned long long *dst = TASK == TASK_INIT ? &a.ctl->init_edges
-                                                    : (TASK == TASK_REVT ? &a.ctl->rev_edges : &a.ctl->fwd_edges);
+                                  : (TASK == TASK_FWD ? &a.ctl->fwd_edges : &a.ctl->rev_edges);
         atomicAdd(dst, e_tot);
     }
     __syncthreads();
@@ -685,73 +696,434 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, int word, uint3
 
 struct SlotArgs {
     unsigned long long *vis, *pend;
-    int32_t *qa, *qb, *touched;
+    int32_t *qa, *touched;
+    int qmask;  // tier-3 queue: per-slot ring of qmask+1 entries
 };
 
-// Tier 3: the tasks tier 2 gave up on, one per block, dense per-block slots.
-template <int DIR, int MODEL, int TASK>
-__global__ void __launch_bounds__(BT) cta_engine_kernel(EngineArgs a, SlotArgs sl)
+// ===================================================== cooperative engine
+//
+// One 512-thread block per task: its 16 warps share one visited/pending
+// table and one ring queue of frontier entries.  A warp claims up to 32
+// queued entries at a time (CAS on the queue head), expands them with the
+// same load-balanced arc split as the warp engine and pushes the nodes that
+// gain new bits; there are no level barriers.  The traversal ends when the
+// queue is empty and no warp holds claimed entries.  Every spin (waiting
+// for work, waiting for a pushed entry to land) is bounded; on expiry the
+// block records an error flag instead of waiting on.
+//   TAB_HASH   8192-slot table in shared memory (tier 2; a task that grows
+//              past the key limit moves on to tier 3)
+//   TAB_DENSE  dense per-block arrays in global memory indexed by node
+//              (tier 3; never overflows)
+
+constexpr int CO_T = 512;
+constexpr int CO_W = CO_T / 32;
+constexpr int CO_LOGC = 13;
+constexpr long long CO_SPIN = 1LL << 22;
+constexpr unsigned short QE16 = 0xFFFF;
+enum { TAB_HASH = 0, TAB_DENSE = 1 };
+
+struct CoopCtl {
+    int head, tail, busy, nkeys, overflow, err;
+};
+
+template <int TAB>
+struct CoopTab;
+
+template <>
+struct CoopTab<TAB_HASH> {
+    static constexpr int C = 1 << CO_LOGC;
+    unsigned long long *vis, *pend;
+    int *key;
+    unsigned short *queue, *touched;
+
+    __device__ __forceinline__ static size_t bytes() { return (size_t)C * 24; }
+    __device__ __forceinline__ void bind(unsigned char *p)
+    {
+        vis = reinterpret_cast<unsigned long long *>(p);
+        pend = vis + C;
+        key = reinterpret_cast<int *>(pend + C);
+        queue = reinterpret_cast<unsigned short *>(key + C);
+        touched = queue + C;
+    }
+    // slot of y, inserting it; -1 (and overflow) past `limit` keys
+    __device__ __forceinline__ int slot(int y, int limit, CoopCtl &c)
+    {
+        uint32_t h = ((uint32_t)y * 2654435761u) >> (32 - CO_LOGC);
+        volatile int *keys = key;
+        for (int probe = 0; probe < C; ++probe) {
+            const int k = keys[h];
+            if (k == y) return (int)h;
+            if (k == EMPTY_KEY) {
+                if (*(volatile int *)&c.nkeys >= limit) {
+                    c.overflow = 1;
+                    return -1;
+                }
+                const int old = atomicCAS(&key[h], EMPTY_KEY, y);
+                if (old == EMPTY_KEY) {
+                    touched[atomicAdd(&c.nkeys, 1)] = (unsigned short)h;
+                    return (int)h;
+                }
+                if (old == y) return (int)h;
+            }
+            h = (h + 1) & (C - 1);
+        }
+        c.overflow = 1;
+        return -1;
+    }
+    __device__ __forceinline__ void note_new(int, CoopCtl &) {}
+    __device__ __forceinline__ int node(int idx) const { return key[idx]; }
+    __device__ __forceinline__ void put(int pos, int idx) { *(volatile unsigned short *)&queue[pos & (C - 1)] = (unsigned short)idx; }
+    __device__ __forceinline__ int take(int pos, CoopCtl &c)
+    {
+        volatile unsigned short *q = &queue[pos & (C - 1)];
+        for (long long i = 0; i < CO_SPIN; ++i) {
+            const unsigned short v = *q;
+            if (v != QE16) {
+                *q = QE16;
+                return v;
+            }
+            __nanosleep(32);
+        }
+        c.err = 1;
+        return -1;
+    }
+    __device__ __forceinline__ void clear_slot(int idx)
+    {
+        key[idx] = EMPTY_KEY;
+        vis[idx] = 0;
+        pend[idx] = 0;
+    }
+    __device__ __forceinline__ int touched_at(int i) const { return touched[i]; }
+    __device__ __forceinline__ void clear_queue(int, int)
+    {
+        for (int i = threadIdx.x; i < C; i += blockDim.x) queue[i] = QE16;
+    }
+};
+
+template <>
+struct CoopTab<TAB_DENSE> {
+    unsigned long long *vis, *pend;
+    int *queue, *touched;
+    int qmask;
+
+    __device__ __forceinline__ int slot(int y, int, CoopCtl &) { return y; }
+    __device__ __forceinline__ void note_new(int y, CoopCtl &c) { touched[atomicAdd(&c.nkeys, 1)] = y; }
+    __device__ __forceinline__ int node(int idx) const { return idx; }
+    __device__ __forceinline__ void put(int pos, int idx) { *(volatile int *)&queue[pos & qmask] = idx; }
+    __device__ __forceinline__ int take(int pos, CoopCtl &c)
+    {
+        volatile int *q = &queue[pos & qmask];
+        for (long long i = 0; i < CO_SPIN; ++i) {
+            const int v = *q;
+            if (v != EMPTY_KEY) {
+                *q = EMPTY_KEY;
+                return v;
+            }
+            __nanosleep(32);
+        }
+        c.err = 1;
+        return -1;
+    }
+    __device__ __forceinline__ void clear_slot(int idx)
+    {
+        vis[idx] = 0;
+        pend[idx] = 0;
+    }
+    __device__ __forceinline__ int touched_at(int i) const { return touched[i]; }
+    __device__ __forceinline__ void clear_queue(int head, int tail)
+    {
+        for (int i = head + (int)threadIdx.x; i < tail; i += blockDim.x) queue[i & qmask] = EMPTY_KEY;
+    }
+};
+
+// Seed: entry `idx` carries bits M (vis and pend), queued.
+template <int TAB>
+__device__ __forceinline__ void coop_seed(CoopTab<TAB> &T, CoopCtl &c, int y, uint64_t M, int limit)
 {
-    __shared__ CtaShared S;
-    __shared__ long long sh_t;
-    const int n = a.g.n;
-    const size_t so = (size_t)blockIdx.x * (size_t)n;
-    CtaState w;
-    w.vis = sl.vis + so;
-    w.pend = sl.pend + so;
-    w.qa = sl.qa + so;
-    w.qb = sl.qb + so;
-    w.touched = sl.touched + so;
-    w.nbits = nullptr;
-    w.du_x = nullptr;
-    Ctl *ctl = a.ctl;
-    const long long count = (long long)*(volatile unsigned long long *)&ctl->l2_count;
+    const int idx = T.slot(y, limit, c);
+    if (idx < 0) return;
+    if (TAB == TAB_DENSE) T.note_new(y, c);
+    T.vis[idx] = M;
+    T.pend[idx] = M;
+    T.put(atomicAdd(&c.tail, 1), idx);
+}
+
+// The block's warps expand the task's frontier until nothing is queued or
+// claimed.  Returns this lane's snapshot-edge count for TASK_INIT.
+template <int TAB, int DIR, int MODEL, int TASK>
+__device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, CoopTab<TAB> &T, CoopCtl &c, int word,
+                                                          uint32_t rs, int limit)
+{
+    constexpr int SLICE = TASK == TASK_REVT ? SLICE_TGT : SLICE_SNAP;
+    const GraphView &g = a.g;
+    const Coins &co = a.co;
+    const int lane = threadIdx.x & 31;
+    unsigned long long tedges = 0;
+    long long idle = 0;
     while (true) {
-        if (threadIdx.x == 0) sh_t = (long long)atomicAdd(&ctl->l2_next, 1ull);
-        __syncthreads();
-        const long long k = sh_t;
-        __syncthreads();
-        if (k >= count) break;
-        const long long t = a.list2[k];
-        if (TASK == TASK_INIT) {
-            const int x0 = (int)(t / a.co.W);
-            const int word = (int)(t - (long long)x0 * a.co.W);
-            cta_bfs<DIR, MODEL, TASK>(a, w, x0, word, (uint32_t)word * 64u, nullptr, 0, S);
-        } else {
-            const int r = find_off(a.coff, 64 * a.co.W, t);
-            const long long c = t - a.coff[r];
-            const int cnt = (int)min(64LL, (long long)a.tcnt[r] - 64 * c);
-            cta_bfs<DIR, MODEL, TASK>(a, w, 0, r >> 6, (uint32_t)r, a.tl + a.toff[r] + 64 * c, cnt, S);
+        int nb = 0, qb = 0;
+        if (lane == 0) {
+            atomicAdd(&c.busy, 1);
+            __threadfence_block();
+            int h = *(volatile int *)&c.head;
+            if (!*(volatile int *)&c.overflow) {
+                while (true) {
+                    const int t = *(volatile int *)&c.tail;
+                    if (h >= t) break;
+                    const int want = min(32, t - h);
+                    const int old = atomicCAS(&c.head, h, h + want);
+                    if (old == h) {
+                        nb = want;
+                        qb = h;
+                        break;
+                    }
+                    h = old;
+                }
+            }
+            if (nb == 0) {
+                __threadfence_block();
+                atomicSub(&c.busy, 1);
+            }
+        }
+        nb = __shfl_sync(FULL, nb, 0);
+        qb = __shfl_sync(FULL, qb, 0);
+        if (nb == 0) {
+            int done = 0;
+            if (lane == 0) {
+                const int h = *(volatile int *)&c.head;
+                const int t = *(volatile int *)&c.tail;
+                __threadfence_block();
+                const int b = *(volatile int *)&c.busy;
+                done = *(volatile int *)&c.overflow || *(volatile int *)&c.err || (h >= t && b == 0);
+            }
+            done = __shfl_sync(FULL, done, 0);
+            if (done) break;
+            if (++idle > CO_SPIN) {
+                if (lane == 0) c.err = 1;
+                break;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        idle = 0;
+        long long base = 0;
+        int vdeg = 0, heavy = 0;
+        uint32_t rtm1 = 0;
+        uint64_t F = 0;
+        if (lane < nb) {
+            const int idx = T.take(qb + lane, c);
+            if (idx >= 0) {
+                F = atomicExch(&T.pend[idx], 0ull);
+                const Row rr = row_ref<DIR, MODEL>(g, co, T.node(idx), word);
+                base = rr.base;
+                vdeg = F ? rr.vdeg : 0;
+                heavy = rr.heavy;
+                rtm1 = rr.rtm1;
+                if (TASK == TASK_INIT) tedges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
+            }
+        }
+        int incl = vdeg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - vdeg;
+        for (int abase = 0; abase < total; abase += 32) {
+            const int j = abase + lane;
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int cand = lo + step;
+                const int ex = __shfl_sync(FULL, excl, cand & 31);
+                if (cand < nb && ex <= j) lo = cand;
+            }
+            const long long ib = __shfl_sync(FULL, base, lo);
+            const int iex = __shfl_sync(FULL, excl, lo);
+            const int ih = __shfl_sync(FULL, heavy, lo);
+            const uint32_t itm1 = __shfl_sync(FULL, rtm1, lo);
+            const uint64_t iF = __shfl_sync(FULL, F, lo);
+            if (j < total) {
+                int y;
+                uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y);
+                if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
+                    ml = 0;
+                if (ml) {
+                    const int idx = T.slot(y, limit, c);
+                    if (idx >= 0) {
+                        const uint64_t old = atomicOr(&T.vis[idx], (unsigned long long)ml);
+                        const uint64_t nw = ml & ~old;
+                        if (nw) {
+                            if (TAB == TAB_DENSE && old == 0) T.note_new(y, c);
+                            const uint64_t oldp = atomicOr(&T.pend[idx], (unsigned long long)nw);
+                            if (oldp == 0) T.put(atomicAdd(&c.tail, 1), idx);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            atomicSub(&c.busy, 1);
         }
     }
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        const unsigned long long c2 = *(volatile unsigned long long *)&ctl->l1_count;
+    return tedges;
+}
+
+// Tier 2 (TAB_HASH, tasks of list1) and tier 3 (TAB_DENSE, tasks of list2).
+template <int TAB, int DIR, int MODEL, int TASK>
+__global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, SlotArgs sl)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ CoopCtl c;
+    __shared__ long long sh_t;
+    __shared__ long long red_ll[CO_W];
+    __shared__ unsigned long long red_ull[CO_W];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int wid = tid >> 5;
+    const GraphView &g = a.g;
+    Ctl *ctl = a.ctl;
+    CoopTab<TAB> T;
+    int limit = 0x7fffffff;
+    if constexpr (TAB == TAB_HASH) {
+        T.bind(smem_raw);
+        for (int i = tid; i < CoopTab<TAB_HASH>::C; i += CO_T) {
+            T.key[i] = EMPTY_KEY;
+            T.vis[i] = 0;
+            T.pend[i] = 0;
+            T.queue[i] = QE16;
+        }
+        limit = a.limit;
+    } else {
+        const size_t so = (size_t)blockIdx.x * (size_t)g.n;
+        T.vis = sl.vis + so;
+        T.pend = sl.pend + so;
+        T.touched = sl.touched + so;
+        T.queue = sl.qa + (size_t)blockIdx.x * (size_t)(sl.qmask + 1);
+        T.qmask = sl.qmask;
+    }
+    const long long count = (long long)*(volatile unsigned long long *)(TAB == TAB_HASH ? &ctl->l1_count : &ctl->l2_count);
+    unsigned long long *next = TAB == TAB_HASH ? &ctl->l1_next : &ctl->l2_next;
+    const int32_t *list = TAB == TAB_HASH ? a.list1 : a.list2;
+    unsigned long long edges = 0;
+    __syncthreads();
+    while (true) {
+        if (tid == 0) sh_t = (long long)atomicAdd(next, 1ull);
+        __syncthreads();
+        const long long k = sh_t;
+        if (k >= count) break;
+        const long long t = list[k];
+        int x0 = 0, word;
+        uint32_t rs;
+        if (tid == 0) {
+            c.head = 0;
+            c.tail = 0;
+            c.busy = 0;
+            c.nkeys = 0;
+            c.overflow = 0;
+            c.err = 0;
+        }
+        __syncthreads();
         if (TASK == TASK_INIT) {
-            ctl->init_t2 += c2;
-            ctl->init_t3 += (unsigned long long)count;
+            x0 = (int)(t / a.co.W);
+            word = (int)(t - (long long)x0 * a.co.W);
+            rs = (uint32_t)word * 64u;
+            if (tid == 0) coop_seed<TAB>(T, c, x0, word_mask(word, a.co.R), limit);
         } else {
-            ctl->rev_t2 += c2;
-            ctl->rev_t3 += (unsigned long long)count;
+            const int r = find_off(a.coff, 64 * a.co.W, t);
+            const long long ci = t - a.coff[r];
+            word = r >> 6;
+            rs = (uint32_t)r;
+            const long long b0 = a.toff[r] + 64 * ci;
+            const int cnt = (int)min(64LL, (long long)a.tcnt[r] - 64 * ci);
+            if (tid < cnt) coop_seed<TAB>(T, c, a.tl[b0 + tid], 1ull << tid, limit);
+        }
+        __syncthreads();
+        const unsigned long long tedges = coop_expand<TAB, DIR, MODEL, TASK>(a, T, c, word, rs, limit);
+        __syncthreads();
+        const int ovf = c.overflow | c.err;
+        const int nt = c.nkeys;
+        long long cnt = 0;
+        unsigned long long redges = 0;
+        for (int i = tid; i < nt; i += CO_T) {
+            const int idx = T.touched_at(i);
+            if (!ovf) {
+                const int cc = __popcll(T.vis[idx]);
+                if (TASK == TASK_INIT) {
+                    cnt += cc;
+                } else {
+                    const int u = T.node(idx);
+                    atomicAdd((unsigned long long *)&a.s[u], (unsigned long long)(-(long long)cc));
+                    redges += (unsigned long long)cc * (unsigned long long)(__ldg(g.crp + u + 1) - __ldg(g.crp + u));
+                }
+            }
+            T.clear_slot(idx);
+        }
+        if (ovf) T.clear_queue(c.head, c.tail);
+        if (!ovf) edges += (TASK == TASK_INIT ? tedges : 0) + redges;
+        if (TASK == TASK_INIT) {
+            cnt = warp_sum(cnt);
+            if (lane == 0) red_ll[wid] = cnt;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (c.err) atomicOr(&ctl->flags, 2);
+            if (ovf && !c.err) {
+                if (TAB == TAB_HASH) a.list2[atomicAdd(&ctl->l2_count, 1ull)] = (int32_t)t;
+            } else if (!ovf && TASK == TASK_INIT) {
+                long long tot = 0;
+                for (int w = 0; w < CO_W; ++w) tot += red_ll[w];
+                atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)tot);
+            }
+        }
+        __syncthreads();
+    }
+    edges = warp_sum(edges);
+    if (lane == 0) red_ull[wid] = edges;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long tot = 0;
+        for (int w = 0; w < CO_W; ++w) tot += red_ull[w];
+        if (tot) atomicAdd(TASK == TASK_INIT ? &ctl->init_edges : &ctl->rev_edges, tot);
+        if (blockIdx.x == 0) {
+            if (TAB == TAB_HASH) {
+                if (TASK == TASK_INIT) ctl->init_t2 += (unsigned long long)count;
+                else ctl->rev_t2 += (unsigned long long)count;
+            } else {
+                if (TASK == TASK_INIT) ctl->init_t3 += (unsigned long long)count;
+                else ctl->rev_t3 += (unsigned long long)count;
+            }
         }
     }
 }
 
+size_t coop_hash_smem() { return (size_t)(1 << CO_LOGC) * 24; }
+
 // ========================================================== forward DU
 
 struct FwdArgs {
-    unsigned long long *cov, *nbits, *pendf, *du_m;
-    int32_t *fq_a, *fq_b, *du_x, *du_cnt, *tl;
+    unsigned long long *cov, *nbits, *pendf, *du_m, *anc;
+    int32_t *fq_a, *fq_b, *du_x, *du_cnt, *tl, *anc_list, *anc_cnt;
     long long *toff, *coff;
     int32_t *tcnt;
     long long tcap;  // per-word capacity of tl
 };
 
-// Forward DU (Algorithm 2 inner loops, first half): block `word` walks from
-// v* over live arcs of its 64 snapshots with the word's coverage bitset as
-// the visited set, listing the newly covered nodes; it then writes, per
-// snapshot of the word, the list of its newly covered nodes (the targets of
-// the reverse pass).  The last block to finish turns the per-snapshot
-// counts into the offsets of the target-sliced reverse tasks.
+// Forward DU (Algorithm 2, inner loops) for the 64 snapshots of block
+// `word`:
+//  1. walk from v* over live arcs with the word's coverage bitset as the
+//     visited set: N_r = R(G'_r, v*) minus what earlier seeds cover;
+//  2. walk back from v* over live in-arcs: every u reaching v* in snapshot
+//     r reaches all of N_r (N_r lies inside R(G'_r, v*)), so s_u drops by
+//     |N_r| at once; these ancestors are marked so that
+//  3. the per-snapshot lists of the remaining targets (N_r minus the
+//     ancestors) feed the target-sliced reverse tasks, which never enter a
+//     marked node (a path through one would make its start an ancestor).
+// The last block to finish turns the per-snapshot counts into the offsets
+// of the reverse tasks.
 template <int MODEL>
 __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
 {
@@ -763,6 +1135,14 @@ __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
     Ctl *ctl = a.ctl;
     const int vstar = *(volatile int32_t *)&ctl->vstar;
     const size_t so = (size_t)word * (size_t)n;
+    unsigned long long *ancw = f.anc + so;
+    int32_t *anclw = f.anc_list + so;
+    // the previous round's ancestor marks of this word
+    {
+        const int na = f.anc_cnt[word];
+        for (int i = tid; i < na; i += BT) ancw[anclw[i]] = 0;
+        __syncthreads();
+    }
     if (vstar >= 0) {
         CtaState w;
         w.vis = f.cov + so;
@@ -772,12 +1152,12 @@ __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
         w.touched = nullptr;
         w.nbits = f.nbits + so;
         w.du_x = f.du_x + so;
-        cta_bfs<DIR_FWD, MODEL, TASK_FWD>(a, w, vstar, word, (uint32_t)word * 64u, nullptr, 0, S);
+        cta_bfs<DIR_FWD, MODEL, TASK_FWD>(a, w, vstar, word_mask(word, a.co.R), word, (uint32_t)word * 64u, nullptr,
+                                          0, nullptr, S);
     } else {
         if (tid == 0) S.ndu = 0;
         __syncthreads();
     }
-    // per-snapshot lists of the newly covered nodes of this word
     const int nd = S.ndu;
     int32_t *dux = f.du_x + so;
     unsigned long long *dum = f.du_m + so;
@@ -787,11 +1167,41 @@ __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
         S.bcur[tid] = 0;
     }
     __syncthreads();
+    // |N_r| for the 64 snapshots of the word
     for (int i = tid; i < nd; i += BT) {
         const int y = dux[i];
         uint64_t M = nb[y];
         nb[y] = 0;
         dum[i] = M;
+        while (M) {
+            const int b = __ffsll((long long)M) - 1;
+            M &= M - 1;
+            atomicAdd(&S.bcnt[b], 1);
+        }
+    }
+    __syncthreads();
+    if (tid < 64) S.boff[tid] = S.bcnt[tid];  // keep |N_r| while bcnt is reused
+    __syncthreads();
+    // ancestors of v* (dux[0] is v* whenever this word has new coverage)
+    int nanc = 0;
+    if (nd > 0) {
+        CtaState w;
+        w.vis = ancw;
+        w.pend = f.pendf + so;
+        w.qa = f.fq_a + so;
+        w.qb = f.fq_b + so;
+        w.touched = anclw;
+        w.nbits = nullptr;
+        w.du_x = nullptr;
+        cta_bfs<DIR_REV, MODEL, TASK_ANC>(a, w, dux[0], dum[0], word, (uint32_t)word * 64u, nullptr, 0, S.boff, S);
+        nanc = S.ntouch;
+    }
+    if (tid == 0) f.anc_cnt[word] = nanc;
+    // per-snapshot target lists: newly covered nodes that are not ancestors
+    if (tid < 64) S.bcnt[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < nd; i += BT) {
+        uint64_t M = dum[i] & ~ancw[dux[i]];
         while (M) {
             const int b = __ffsll((long long)M) - 1;
             M &= M - 1;
@@ -814,7 +1224,7 @@ __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
     int32_t *tlw = f.tl + (size_t)word * (size_t)f.tcap;
     for (int i = tid; i < nd; i += BT) {
         const int y = dux[i];
-        uint64_t M = dum[i];
+        uint64_t M = dum[i] & ~ancw[y];
         while (M) {
             const int b = __ffsll((long long)M) - 1;
             M &= M - 1;
@@ -1019,20 +1429,6 @@ __global__ void __launch_bounds__(256) heavy_index_kernel(GraphView g, Coins co,
     }
 }
 
-// Tier-2 tables start empty: keys EMPTY, state words and counters zero.
-__global__ void t2_clear_kernel(unsigned char *tab, int warps)
-{
-    for (long long w = blockIdx.x; w < warps; w += gridDim.x) {
-        const WTab T = tab_at<T2_LOGC>(tab + (size_t)w * tab_bytes<T2_LOGC>());
-        for (int i = threadIdx.x; i < (1 << T2_LOGC); i += blockDim.x) {
-            T.key[i] = EMPTY_KEY;
-            T.vis[i] = 0;
-            T.pend[i] = 0;
-        }
-        if (threadIdx.x < 4) T.ctr[threadIdx.x] = 0;
-    }
-}
-
 // ============================================================== live masks
 
 __global__ void live_masks_kernel(Coins co, long long m, const uint2 *fw, uint32_t uic_tm1, int wic,
@@ -1064,7 +1460,7 @@ EngineArgs engine_args(sg_graph *g, const Coins &co, int heavy_on)
     a.coff = ws.coff.p;
     a.list1 = ws.list1.p;
     a.list2 = ws.list2.p;
-    a.t2_tab = ws.t2_tab.p;
+    a.anc = ws.anc.p;
     a.ntasks = 0;
     a.limit = 1;
     return a;
@@ -1077,8 +1473,8 @@ SlotArgs slot_args(sg_graph *g)
     s.vis = ws.slot_vis.p;
     s.pend = ws.slot_pend.p;
     s.qa = ws.slot_qa.p;
-    s.qb = ws.slot_qb.p;
     s.touched = ws.slot_touched.p;
+    s.qmask = ws.slot_qmask;
     return s;
 }
 
@@ -1089,7 +1485,7 @@ sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, cudaE
     EngineArgs a = a0;
     {
         a.limit = std::max(1, std::min(g_tier_limit[0], (1 << T1_LOGC) / 2));
-        auto kern = warp_engine_kernel<T1_LOGC, DIR, MODEL, TASK, 1>;
+        auto kern = warp_engine_kernel<T1_LOGC, DIR, MODEL, TASK>;
         const size_t smem = (WE_THREADS / 32) * tab_bytes<T1_LOGC>();
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
@@ -1100,12 +1496,16 @@ sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, cudaE
         ++g_launches;
     }
     if (after_t1) SG_CUDA_TRY(cudaEventRecord(after_t1, st));
-    a.limit = std::max(1, std::min(g_tier_limit[1], (1 << T2_LOGC) / 2));
-    warp_engine_kernel<T2_LOGC, DIR, MODEL, TASK, 2>
-        <<<g->ws.t2_warps / (WE_THREADS / 32), WE_THREADS, 0, st>>>(a, 1);
-    SG_CUDA_TRY(cudaGetLastError());
-    ++g_launches;
-    cta_engine_kernel<DIR, MODEL, TASK><<<g->ws.nslots, BT, 0, st>>>(a, slot_args(g));
+    {
+        a.limit = std::max(1, std::min(g_tier_limit[1], (1 << CO_LOGC) / 2));
+        auto kern = coop_engine_kernel<TAB_HASH, DIR, MODEL, TASK>;
+        const size_t smem = coop_hash_smem();
+        SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<g->num_sms, CO_T, smem, st>>>(a, slot_args(g));
+        SG_CUDA_TRY(cudaGetLastError());
+        ++g_launches;
+    }
+    coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK><<<g->ws.nslots, CO_T, 0, st>>>(a, slot_args(g));
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
     return SG_OK;
@@ -1160,6 +1560,9 @@ sg_status round_t(sg_graph *g, const Coins &co, int heavy_on, int32_t round, cud
     f.coff = ws.coff.p;
     f.tcnt = ws.tcnt.p;
     f.tcap = 64 * g->n;
+    f.anc = ws.anc.p;
+    f.anc_list = ws.anc_list.p;
+    f.anc_cnt = ws.anc_cnt.p;
     fwd_du_kernel<MODEL><<<co.W, BT, 0, st>>>(a, f);
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
@@ -1170,7 +1573,7 @@ sg_status round_t(sg_graph *g, const Coins &co, int heavy_on, int32_t round, cud
 }  // namespace
 
 thread_local int g_launches = 0;
-int g_tier_limit[2] = {(1 << T1_LOGC) / 2, (1 << T2_LOGC) / 2};
+int g_tier_limit[2] = {(1 << T1_LOGC) / 2, (1 << CO_LOGC) / 2};
 
 sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t st)
 {
@@ -1205,16 +1608,6 @@ sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out,
                                               reinterpret_cast<unsigned long long *>(out));
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
-    return SG_OK;
-}
-
-size_t t2_table_bytes() { return tab_bytes<T2_LOGC>(); }
-
-sg_status run_t2_clear(unsigned char *tab, int warps, cudaStream_t st)
-{
-    if (warps <= 0) return SG_OK;
-    t2_clear_kernel<<<std::min(warps, 4096), 256, 0, st>>>(tab, warps);
-    SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 
