@@ -792,6 +792,10 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
         SG_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         SG_CUDA_TRY(cudaStreamSynchronize(st));
         *init_edges = h.init_edges;
+        if (h.flags) {
+            set_error("device-side check failed (flags 0x%x)", h.flags);
+            return SG_EINTERNAL;
+        }
     } else if (is_pageable(out_s)) {
         SG_CUDA_TRY(cudaStreamSynchronize(st));
     }

@@ -863,10 +863,12 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
     while (true) {
         int nb = 0, qb = 0;
         if (lane == 0) {
-            atomicAdd(&c.busy, 1);
-            __threadfence_block();
-            int h = *(volatile int *)&c.head;
-            if (!*(volatile int *)&c.overflow) {
+            // announce intent (busy) only when there is something to claim,
+            // so that idle polling never hides quiescence from other warps
+            if (*(volatile int *)&c.head < *(volatile int *)&c.tail && !*(volatile int *)&c.overflow) {
+                atomicAdd(&c.busy, 1);
+                __threadfence_block();
+                int h = *(volatile int *)&c.head;
                 while (true) {
                     const int t = *(volatile int *)&c.tail;
                     if (h >= t) break;
@@ -879,10 +881,10 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                     }
                     h = old;
                 }
-            }
-            if (nb == 0) {
-                __threadfence_block();
-                atomicSub(&c.busy, 1);
+                if (nb == 0) {
+                    __threadfence_block();
+                    atomicSub(&c.busy, 1);
+                }
             }
         }
         nb = __shfl_sync(FULL, nb, 0);
