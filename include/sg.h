@@ -126,6 +126,13 @@ sg_status sg_set_heavy_threshold(int32_t min_degree);
  * Errors: SG_EINVAL if either is < 1. */
 sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys);
 
+/* Landmarks for the initial gains: with 1 (the default), the reach set of
+ * the node of largest out-degree is computed once per snapshot, and a
+ * source that reaches that node in a snapshot is credited with the whole
+ * set instead of traversing it again.  0 disables it.  Results do not
+ * depend on it.  Applies to later calls.  Errors: SG_EINVAL unless 0 or 1. */
+sg_status sg_set_landmarks(int32_t count);
+
 /* Same as sg_load_graph from an arc list src[i] -> dst[i], i < m.
  * src/dst are host memory when is_device_ptr is 0, device memory when 1. */
 sg_status sg_load_graph_coo(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,

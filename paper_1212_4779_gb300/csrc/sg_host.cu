@@ -161,6 +161,9 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.anc, st);
     dbuf_free(ws.anc_list, st);
     dbuf_free(ws.anc_cnt, st);
+    dbuf_free(ws.lmk_rx, st);
+    dbuf_free(ws.lmk_cnt, st);
+    dbuf_free(ws.lmk_edges, st);
     dbuf_free(ws.hcnt_out, st);
     dbuf_free(ws.hnbr_out, st);
     dbuf_free(ws.hmask_out, st);
@@ -266,6 +269,17 @@ sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> 
     const HeavyHost ho = heavy_rows(n, rp, g_heavy_min_deg);
     const HeavyHost hi = heavy_rows(n, crp, g_heavy_min_deg);
     g->heavy_min_deg = g_heavy_min_deg;
+    {
+        int32_t best = -1, bestd = 31;
+        for (int64_t v = 0; v < n; ++v) {
+            const int32_t d = rp[(size_t)v + 1] - rp[(size_t)v];
+            if (d > bestd) {
+                bestd = d;
+                best = (int32_t)v;
+            }
+        }
+        g->lmk_node = best;
+    }
     g->nh_out = (int32_t)ho.hrow.size();
     g->nh_in = (int32_t)hi.hrow.size();
     g->hsum_out = ho.hpref.back();
@@ -394,6 +408,9 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
         SG_TRY(dbuf_alloc(ws.anc, nw, st));
         SG_TRY(dbuf_alloc(ws.anc_list, nw, st));
         SG_TRY(dbuf_alloc(ws.anc_cnt, (size_t)W, st));
+        SG_TRY(dbuf_alloc(ws.lmk_rx, nw, st));
+        SG_TRY(dbuf_alloc(ws.lmk_cnt, (size_t)64 * W, st));
+        SG_TRY(dbuf_alloc(ws.lmk_edges, (size_t)64 * W, st));
         SG_TRY(dbuf_alloc(ws.ctl, 1, st));
 
         SG_CUDA_TRY(cudaMemsetAsync(ws.nbits.p, 0, ws.nbits.bytes, st));
@@ -527,6 +544,16 @@ sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys)
     }
     g_tier_limit[0] = tier1_keys;
     g_tier_limit[1] = tier2_keys;
+    return SG_OK;
+}
+
+sg_status sg_set_landmarks(int32_t count)
+{
+    if (count < 0 || count > 1) {
+        set_error("landmark count must be 0 or 1");
+        return SG_EINVAL;
+    }
+    g_landmarks = count;
     return SG_OK;
 }
 

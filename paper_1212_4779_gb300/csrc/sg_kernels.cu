@@ -46,7 +46,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr long long SEED_MARK = -(1LL << 62);
 
 enum { DIR_FWD = 0, DIR_REV = 1 };
-enum { TASK_INIT = 0, TASK_REVT = 1, TASK_FWD = 2, TASK_ANC = 3 };
+enum { TASK_INIT = 0, TASK_REVT = 1, TASK_FWD = 2, TASK_ANC = 3, TASK_LMK = 4 };
 enum { SLICE_SNAP = 0, SLICE_TGT = 1 };
 
 constexpr int T1_LOGC = 9;   // tier-1 table: 512 slots per warp (shared memory)
@@ -190,6 +190,8 @@ __device__ __forceinline__ int find_off(const long long *off, int count, long lo
     return lo;
 }
 
+struct EngineArgs;
+
 struct EngineArgs {
     GraphView g;
     Coins co;
@@ -201,9 +203,54 @@ struct EngineArgs {
     const long long *coff;  // [64W+1] chunk-task offsets
     int32_t *list1, *list2;
     const unsigned long long *anc;  // [W][n] ancestors of v*, per snapshot bit (this round)
+    // landmark x (initial gains): bit b of lmk_rx[w][y] = y in R(G'_{64w+b}, x);
+    // lmk_cnt / lmk_edges: |R(G'_r, x)| and sum of outdeg over it, per snapshot
+    int lmk_x;
+    const unsigned long long *lmk_rx;
+    const int32_t *lmk_cnt;
+    const unsigned long long *lmk_edges;
     long long ntasks;       // TASK_INIT: n * W
     int limit;              // keys a warp table may hold before the task moves up a tier
 };
+
+
+// Initial gains with a landmark x: a task that reaches x in snapshot r gets
+// all of R(G'_r, x) at once (|R(G'_r, x)| added at the end), so bits of
+// such snapshots need not travel inside R(G'_r, x).  Returns the bits of ml
+// that still have to be recorded at y; bits reaching x itself are recorded
+// in *xbits.  Bits that arrive before x does are masked out at the end.
+__device__ __forceinline__ uint64_t lmk_filter(const EngineArgs &a, int word, int y, uint64_t ml,
+                                               unsigned long long *xbits)
+{
+    if (y == a.lmk_x) {
+        atomicOr(xbits, (unsigned long long)ml);
+        return 0;
+    }
+    const uint64_t rx = __ldg(a.lmk_rx + (size_t)word * a.g.n + y);
+    if (rx & ml) ml &= ~(rx & *(volatile unsigned long long *)xbits);
+    return ml;
+}
+
+// State bits of a finished initial-gain task that count at u: those not
+// accounted for by the landmark.
+__device__ __forceinline__ uint64_t lmk_effective(const EngineArgs &a, int word, int u, uint64_t vis,
+                                                  uint64_t xbits)
+{
+    if (a.lmk_x < 0 || !xbits) return vis;
+    return vis & ~(__ldg(a.lmk_rx + (size_t)word * a.g.n + u) & xbits);
+}
+
+// sum over the snapshots in xbits of |R(G'_r, x)| and of its out-degree sum
+__device__ __forceinline__ void lmk_totals(const EngineArgs &a, int word, uint64_t xbits, long long &cnt,
+                                           unsigned long long &edges)
+{
+    while (xbits) {
+        const int b = __ffsll((long long)xbits) - 1;
+        xbits &= xbits - 1;
+        cnt += a.lmk_cnt[64 * word + b];
+        edges += a.lmk_edges[64 * word + b];
+    }
+}
 
 // ============================================================ warp engine
 
@@ -211,13 +258,14 @@ struct WTab {
     unsigned long long *vis, *pend;
     int *key;
     unsigned short *queue, *touched;
-    int *ctr;  // [0] queue tail, [1] keys, [2] overflow
+    int *ctr;                  // [0] queue tail, [1] keys, [2] overflow
+    unsigned long long *xbits; // snapshots in which the task reached the landmark
 };
 
 template <int LOGC>
 __host__ __device__ constexpr size_t tab_bytes()
 {
-    return (size_t)(1 << LOGC) * 24 + 16;
+    return (size_t)(1 << LOGC) * 24 + 32;
 }
 
 template <int LOGC>
@@ -231,6 +279,7 @@ __device__ __forceinline__ WTab tab_at(unsigned char *p)
     t.queue = reinterpret_cast<unsigned short *>(t.key + C);
     t.touched = t.queue + C;
     t.ctr = reinterpret_cast<int *>(t.touched + C);
+    t.xbits = reinterpret_cast<unsigned long long *>(t.ctr + 4);
     return t;
 }
 
@@ -288,7 +337,18 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         x0 = (int)(t / co.W);
         word = (int)(t - (long long)x0 * co.W);
         rs = (uint32_t)word * 64u;
+        if (x0 == a.lmk_x) {  // the landmark's own task: its reach is known
+            if (lane == 0) {
+                long long c = 0;
+                unsigned long long e = 0;
+                lmk_totals(a, word, word_mask(word, co.R), c, e);
+                atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)c);
+                edges_acc += e;
+            }
+            return false;
+        }
         if (lane == 0) {
+            *T.xbits = 0;
             const uint64_t M0 = word_mask(word, co.R);
             const uint32_t h = slot_of<LOGC>(x0);
             T.key[h] = x0;
@@ -317,7 +377,6 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         }
     }
     __syncwarp();
-    unsigned long long tedges = 0;
     int qhead = 0;
     while (true) {
         const int qtail = *(volatile int *)&T.ctr[0];
@@ -338,7 +397,6 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
             vdeg = rr.vdeg;
             heavy = rr.heavy;
             rtm1 = rr.rtm1;
-            if (TASK == TASK_INIT) tedges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
         }
         qhead += nb;
         __syncwarp();
@@ -370,6 +428,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
                 // nodes reaching v* in this snapshot were settled by the ancestor pass
                 if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                     ml = 0;
+                if (TASK == TASK_INIT && ml && a.lmk_x >= 0) ml = lmk_filter(a, word, y, ml, T.xbits);
                 if (ml) {
                     const int h = table_slot<LOGC>(T, y, LIMIT);
                     if (h >= 0) {
@@ -391,16 +450,20 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
     __syncwarp();
     const int ovf = *(volatile int *)&T.ctr[2];
     const int nt = *(volatile int *)&T.ctr[1];
+    const uint64_t xb = TASK == TASK_INIT ? *(volatile unsigned long long *)T.xbits : 0ull;
     long long cnt = 0;
     unsigned long long redges = 0;
     for (int i = lane; i < nt; i += 32) {
         const int h = T.touched[i];
         if (!ovf) {
-            const int c = __popcll(T.vis[h]);
+            const int u = T.key[h];
             if (TASK == TASK_INIT) {
+                // snapshot-edges of the task: sum over (u, r) reached of outdeg(u)
+                const int c = __popcll(lmk_effective(a, word, u, T.vis[h], xb));
                 cnt += c;
+                redges += (unsigned long long)c * (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
             } else {
-                const int u = T.key[h];
+                const int c = __popcll(T.vis[h]);
                 atomicAdd((unsigned long long *)&a.s[u], (unsigned long long)(-(long long)c));
                 redges += (unsigned long long)c * (unsigned long long)(__ldg(g.crp + u + 1) - __ldg(g.crp + u));
             }
@@ -409,8 +472,15 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         T.vis[h] = 0;
         T.pend[h] = 0;
     }
-    if (TASK == TASK_INIT) cnt = warp_sum(cnt);
-    if (!ovf) edges_acc += TASK == TASK_INIT ? tedges : redges;
+    if (TASK == TASK_INIT) {
+        cnt = warp_sum(cnt);
+        if (lane == 0 && !ovf) {
+            unsigned long long e = 0;
+            lmk_totals(a, word, xb, cnt, e);
+            redges += e;
+        }
+    }
+    if (!ovf) edges_acc += redges;
     __syncwarp();
     if (lane == 0) {
         if (!ovf && TASK == TASK_INIT) atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)cnt);
@@ -571,13 +641,13 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
         }
     } else if (tid == 0) {
         uint64_t M = M0;
-        if (TASK == TASK_FWD) M &= ~w.vis[x0];
+        if (TASK == TASK_FWD || TASK == TASK_LMK) M &= ~w.vis[x0];
         if (M) {
             w.vis[x0] |= M;
             w.pend[x0] = M;
             w.qa[0] = x0;
             S.qlen = 1;
-            if (TASK == TASK_FWD) {
+            if (TASK == TASK_FWD || TASK == TASK_LMK) {
                 w.nbits[x0] |= M;
                 w.du_x[0] = x0;
                 S.ndu = 1;
@@ -633,8 +703,9 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                         const uint64_t nw = ml & ~old;
                         if (nw) {
                             if (TASK == TASK_INIT) cnt += __popcll(nw);
-                            if (TASK != TASK_FWD && old == 0) w.touched[atomicAdd(&S.ntouch, 1)] = y;
-                            if (TASK == TASK_FWD) {
+                            if (TASK != TASK_FWD && TASK != TASK_LMK && old == 0)
+                                w.touched[atomicAdd(&S.ntouch, 1)] = y;
+                            if (TASK == TASK_FWD || TASK == TASK_LMK) {
                                 const uint64_t ob = atomicOr(&w.nbits[y], (unsigned long long)nw);
                                 if (ob == 0) w.du_x[atomicAdd(&S.ndu, 1)] = y;
                             }
@@ -724,6 +795,7 @@ enum { TAB_HASH = 0, TAB_DENSE = 1 };
 
 struct CoopCtl {
     int head, tail, busy, nkeys, overflow, err;
+    unsigned long long xbits;  // initial gains: snapshots in which the task reached the landmark
 };
 
 template <int TAB>
@@ -849,16 +921,15 @@ __device__ __forceinline__ void coop_seed(CoopTab<TAB> &T, CoopCtl &c, int y, ui
 }
 
 // The block's warps expand the task's frontier until nothing is queued or
-// claimed.  Returns this lane's snapshot-edge count for TASK_INIT.
+// claimed.
 template <int TAB, int DIR, int MODEL, int TASK>
-__device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, CoopTab<TAB> &T, CoopCtl &c, int word,
+__device__ __forceinline__ void coop_expand(const EngineArgs &a, CoopTab<TAB> &T, CoopCtl &c, int word,
                                                           uint32_t rs, int limit)
 {
     constexpr int SLICE = TASK == TASK_REVT ? SLICE_TGT : SLICE_SNAP;
     const GraphView &g = a.g;
     const Coins &co = a.co;
     const int lane = threadIdx.x & 31;
-    unsigned long long tedges = 0;
     long long idle = 0;
     while (true) {
         int nb = 0, qb = 0;
@@ -921,7 +992,6 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                 vdeg = F ? rr.vdeg : 0;
                 heavy = rr.heavy;
                 rtm1 = rr.rtm1;
-                if (TASK == TASK_INIT) tedges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
             }
         }
         int incl = vdeg;
@@ -951,6 +1021,7 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                 uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y);
                 if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                     ml = 0;
+                if (TASK == TASK_INIT && ml && a.lmk_x >= 0) ml = lmk_filter(a, word, y, ml, &c.xbits);
                 if (ml) {
                     const int idx = T.slot(y, limit, c);
                     if (idx >= 0) {
@@ -971,7 +1042,6 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
             atomicSub(&c.busy, 1);
         }
     }
-    return tedges;
 }
 
 // Tier 2 (TAB_HASH, tasks of list1) and tier 3 (TAB_DENSE, tasks of list2).
@@ -1027,6 +1097,7 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
             c.nkeys = 0;
             c.overflow = 0;
             c.err = 0;
+            c.xbits = 0;
         }
         __syncthreads();
         if (TASK == TASK_INIT) {
@@ -1044,20 +1115,23 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
             if (tid < cnt) coop_seed<TAB>(T, c, a.tl[b0 + tid], 1ull << tid, limit);
         }
         __syncthreads();
-        const unsigned long long tedges = coop_expand<TAB, DIR, MODEL, TASK>(a, T, c, word, rs, limit);
+        coop_expand<TAB, DIR, MODEL, TASK>(a, T, c, word, rs, limit);
         __syncthreads();
         const int ovf = c.overflow | c.err;
         const int nt = c.nkeys;
+        const uint64_t xb = TASK == TASK_INIT ? c.xbits : 0ull;
         long long cnt = 0;
         unsigned long long redges = 0;
         for (int i = tid; i < nt; i += CO_T) {
             const int idx = T.touched_at(i);
             if (!ovf) {
-                const int cc = __popcll(T.vis[idx]);
+                const int u = T.node(idx);
                 if (TASK == TASK_INIT) {
+                    const int cc = __popcll(lmk_effective(a, word, u, T.vis[idx], xb));
                     cnt += cc;
+                    redges += (unsigned long long)cc * (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
                 } else {
-                    const int u = T.node(idx);
+                    const int cc = __popcll(T.vis[idx]);
                     atomicAdd((unsigned long long *)&a.s[u], (unsigned long long)(-(long long)cc));
                     redges += (unsigned long long)cc * (unsigned long long)(__ldg(g.crp + u + 1) - __ldg(g.crp + u));
                 }
@@ -1065,7 +1139,7 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
             T.clear_slot(idx);
         }
         if (ovf) T.clear_queue(c.head, c.tail);
-        if (!ovf) edges += (TASK == TASK_INIT ? tedges : 0) + redges;
+        if (!ovf) edges += redges;
         if (TASK == TASK_INIT) {
             cnt = warp_sum(cnt);
             if (lane == 0) red_ll[wid] = cnt;
@@ -1078,6 +1152,9 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
             } else if (!ovf && TASK == TASK_INIT) {
                 long long tot = 0;
                 for (int w = 0; w < CO_W; ++w) tot += red_ll[w];
+                unsigned long long e = 0;
+                lmk_totals(a, word, xb, tot, e);
+                edges += e;
                 atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)tot);
             }
         }
@@ -1263,6 +1340,58 @@ __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
         ctl->rev_tasks += (unsigned long long)carry;
         ctl->du_entries += (unsigned long long)entries;
         ctl->fwd_arrivals = 0;
+    }
+}
+
+
+// Landmark reach sets (initial gains): block `word` walks from x over the
+// live arcs of its 64 snapshots into lmk_rx (zero on entry), then records
+// per snapshot |R(G'_r, x)| and the out-degree sum over it.
+struct LmkArgs {
+    unsigned long long *rx, *pendf, *nbits, *edges;
+    int32_t *fq_a, *fq_b, *list, *cnt;
+};
+
+template <int MODEL>
+__global__ void __launch_bounds__(BT) landmark_kernel(EngineArgs a, LmkArgs l)
+{
+    __shared__ CtaShared S;
+    __shared__ unsigned long long esum[64];
+    const int word = blockIdx.x;
+    const int tid = threadIdx.x;
+    const size_t so = (size_t)word * (size_t)a.g.n;
+    CtaState w;
+    w.vis = l.rx + so;
+    w.pend = l.pendf + so;
+    w.qa = l.fq_a + so;
+    w.qb = l.fq_b + so;
+    w.touched = nullptr;
+    w.nbits = l.nbits + so;
+    w.du_x = l.list + so;
+    cta_bfs<DIR_FWD, MODEL, TASK_LMK>(a, w, a.lmk_x, word_mask(word, a.co.R), word, (uint32_t)word * 64u, nullptr, 0,
+                                      nullptr, S);
+    if (tid < 64) {
+        S.bcnt[tid] = 0;
+        esum[tid] = 0;
+    }
+    __syncthreads();
+    const int nd = S.ndu;
+    for (int i = tid; i < nd; i += BT) {
+        const int y = w.du_x[i];
+        w.nbits[y] = 0;
+        uint64_t M = w.vis[y];
+        const unsigned long long d = (unsigned long long)(__ldg(a.g.rp + y + 1) - __ldg(a.g.rp + y));
+        while (M) {
+            const int b = __ffsll((long long)M) - 1;
+            M &= M - 1;
+            atomicAdd(&S.bcnt[b], 1);
+            atomicAdd(&esum[b], d);
+        }
+    }
+    __syncthreads();
+    if (tid < 64) {
+        l.cnt[64 * word + tid] = S.bcnt[tid];
+        l.edges[64 * word + tid] = esum[tid];
     }
 }
 
@@ -1463,6 +1592,10 @@ EngineArgs engine_args(sg_graph *g, const Coins &co, int heavy_on)
     a.list1 = ws.list1.p;
     a.list2 = ws.list2.p;
     a.anc = ws.anc.p;
+    a.lmk_x = -1;
+    a.lmk_rx = ws.lmk_rx.p;
+    a.lmk_cnt = ws.lmk_cnt.p;
+    a.lmk_edges = ws.lmk_edges.p;
     a.ntasks = 0;
     a.limit = 1;
     return a;
@@ -1536,6 +1669,23 @@ sg_status init_gains_t(sg_graph *g, const Coins &co, int heavy_on, cudaStream_t 
 {
     EngineArgs a = engine_args(g, co, heavy_on);
     a.ntasks = (long long)g->n * co.W;
+    if (g->lmk_node >= 0 && g_landmarks > 0) {
+        sg_workspace &ws = g->ws;
+        a.lmk_x = g->lmk_node;
+        SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_rx.p, 0, (size_t)g->n * co.W * 8, st));
+        LmkArgs l;
+        l.rx = ws.lmk_rx.p;
+        l.pendf = ws.pendf.p;
+        l.nbits = ws.nbits.p;
+        l.edges = ws.lmk_edges.p;
+        l.fq_a = ws.fq_a.p;
+        l.fq_b = ws.fq_b.p;
+        l.list = ws.du_x.p;
+        l.cnt = ws.lmk_cnt.p;
+        landmark_kernel<MODEL><<<co.W, BT, 0, st>>>(a, l);
+        SG_CUDA_TRY(cudaGetLastError());
+        ++g_launches;
+    }
     return launch_tiers<DIR_FWD, MODEL, TASK_INIT>(g, a, st, after_t1);
 }
 
@@ -1576,6 +1726,7 @@ sg_status round_t(sg_graph *g, const Coins &co, int heavy_on, int32_t round, cud
 
 thread_local int g_launches = 0;
 int g_tier_limit[2] = {(1 << T1_LOGC) / 2, (1 << CO_LOGC) / 2};
+int g_landmarks = 1;
 
 sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t st)
 {

@@ -119,6 +119,27 @@ def limits(sg):
     yield sg.sg_set_engine_limits
     sg.sg_set_engine_limits(256, 4096)
     sg.sg_set_heavy_threshold(64)
+    sg.sg_set_landmarks(1)
+
+
+@pytest.mark.parametrize("lmk", [0, 1])
+@pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01", "er2k_uic0.1"])
+def test_landmark_gives_identical_results(sg, limits, name, lmk):
+    """Crediting the landmark's reach set is exact: same initial gains, seeds,
+    gains and snapshot-edge counters with and without it, in every tier."""
+    wl = inputs.workload(name)
+    n, s, d = wl.graph()
+    g, o = _both(sg, n, s, d, wl.model, wl.p)
+    sg.sg_set_landmarks(lmk)
+    ref = o.select(wl.R, 8, wl.seed, mode=oracle.DU, want_init=True)
+    for t1, t2 in [(256, 4096), (2, 16)]:
+        limits(t1, t2)
+        s_gpu, ed = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
+        assert np.array_equal(s_gpu, ref["s_init"]) and ed == int(ref["counters"][0])
+        res = g.select(wl.R, 8, wl.model, wl.p, wl.seed, stats=True)
+        assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+        got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+        assert got == [int(x) for x in ref["counters"]]
 
 
 @pytest.mark.parametrize("t1,t2", [(1, 1), (4, 32), (16, 300), (256, 4096)])
