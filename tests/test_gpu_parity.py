@@ -188,21 +188,25 @@ def test_heavy_index_threshold_gives_identical_results(sg, limits, name, heavy):
     assert np.array_equal(s_gpu, s_ref) and ed == ed_ref
 
 
-def test_giant_component_reaches_tier3_and_agrees(sg):
-    """p = 1 on a connected graph: every task reaches all n > 8192 nodes, so
-    initial-gain tasks run in the block-wide dense engine."""
+def test_giant_component_reaches_tier3_and_agrees(sg, limits):
+    """p = 1 on a connected graph: every task reaches all n > 4096 nodes.
+    Without the landmark, initial-gain tasks run in the dense tier-3
+    engine; with it, every source is credited with the landmark's reach."""
     n, s, d = inputs.chung_lu_undirected(9000, 30000, 2.5, 6.0, 41)
     p_ = np.arange(n - 1, dtype=np.int32)
     s = np.concatenate([s, p_, p_ + 1])
     d = np.concatenate([d, p_ + 1, p_])
     g, o = _both(sg, n, s, d, "uic", 1.0)
-    res = g.select(2, 3, "uic", 1.0, 5, stats=True)
     ref = o.select(2, 3, 5, mode=oracle.DU)
-    assert res.stats["init_tier3_tasks"] > 0
-    assert list(res.gains) == [2 * n, 0, 0] and list(res.seeds) == [0, 1, 2]
-    assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
-    got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
-    assert got == [int(x) for x in ref["counters"]]
+    for lmk in (0, 1):
+        sg.sg_set_landmarks(lmk)
+        res = g.select(2, 3, "uic", 1.0, 5, stats=True)
+        if lmk == 0:
+            assert res.stats["init_tier3_tasks"] > 0
+        assert list(res.gains) == [2 * n, 0, 0] and list(res.seeds) == [0, 1, 2]
+        assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+        got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+        assert got == [int(x) for x in ref["counters"]]
 
 
 # ---------------------------------------------------------- full selection
