@@ -292,6 +292,7 @@ def main():
         "tiers": {k: st_last[k] for k in ("init_tier2_tasks", "init_tier3_tasks", "rev_tier2_tasks",
                                           "rev_tier3_tasks", "rev_tasks", "du_entries")},
         "edges": {k: st_last[k] for k in ("init_edges", "fwd_edges", "rev_edges")},
+        "work": {"keys": st_last["work_keys"], "elems": st_last["work_elems"]},
         "gpu_launches": launches,
         "roofline": roofline,
         "cpu_baseline": cpu,

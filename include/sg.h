@@ -83,6 +83,8 @@ typedef struct {
     int32_t kernel_launches;    /* kernels this call launched */
     int32_t heavy_index;        /* 1 if the heavy-row live index was used */
     int32_t reserved;
+    uint64_t work_keys[2][3];   /* [initial, reverse][tier 1..3]: nodes held in task tables */
+    uint64_t work_elems[2][3];  /* [initial, reverse][tier 1..3]: arcs / index entries expanded */
 } sg_stats;
 
 /* Opaque graph handle; owns its device memory until sg_free_graph. */

@@ -768,6 +768,8 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
         stats->status_flags = h.flags;
         stats->kernel_launches = g_launches - launches0;
         stats->heavy_index = heavy_on;
+        memcpy(stats->work_keys, h.work_keys, sizeof(h.work_keys));
+        memcpy(stats->work_elems, h.work_elems, sizeof(h.work_elems));
         cudaEventElapsedTime(&stats->ms_index, e_start, e_index);
         cudaEventElapsedTime(&stats->ms_init, e_start, e_init);
         cudaEventElapsedTime(&stats->ms_init_tier1, e_index, e_t1);

@@ -131,6 +131,8 @@ struct Ctl {
     unsigned long long rev_t2, rev_t3;    // reverse tasks run by tier 2 / tier 3
     unsigned long long du_entries;
     unsigned long long rev_tasks;         // target-sliced reverse tasks, all rounds
+    unsigned long long work_keys[2][3];   // [init, reverse][tier]: nodes held in task tables
+    unsigned long long work_elems[2][3];  // [init, reverse][tier]: arcs / index entries expanded
     unsigned long long t1_next;   // dynamic task counter, tier 1
     unsigned long long l1_count;  // tasks handed from tier 1 to tier 2
     unsigned long long l1_next;

@@ -226,8 +226,8 @@ __device__ __forceinline__ uint64_t lmk_filter(const EngineArgs &a, int word, in
         atomicOr(xbits, (unsigned long long)ml);
         return 0;
     }
-    const uint64_t rx = __ldg(a.lmk_rx + (size_t)word * a.g.n + y);
-    if (rx & ml) ml &= ~(rx & *(volatile unsigned long long *)xbits);
+    const uint64_t xb = *(volatile unsigned long long *)xbits;
+    if (xb & ml) ml &= ~(__ldg(a.lmk_rx + (size_t)word * a.g.n + y) & xb);
     return ml;
 }
 
@@ -324,7 +324,7 @@ __device__ __forceinline__ int table_slot(const WTab &T, int y, int limit)
 // the task was applied; the table is clean again either way).
 template <int LOGC, int DIR, int MODEL, int TASK>
 __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, long long t, int lane,
-                                          unsigned long long &edges_acc)
+                                          unsigned long long &edges_acc, unsigned long long &wk)
 {
     constexpr int C = 1 << LOGC;
     const int LIMIT = a.limit;  // in [1, C/2]
@@ -377,6 +377,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         }
     }
     __syncwarp();
+    unsigned long long tedges = 0;
     int qhead = 0;
     while (true) {
         const int qtail = *(volatile int *)&T.ctr[0];
@@ -397,6 +398,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
             vdeg = rr.vdeg;
             heavy = rr.heavy;
             rtm1 = rr.rtm1;
+            if (TASK == TASK_INIT) tedges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
         }
         qhead += nb;
         __syncwarp();
@@ -408,6 +410,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         }
         const int total = __shfl_sync(FULL, incl, 31);
         const int excl = incl - vdeg;
+        if (lane == 1) wk += (unsigned long long)total;
         for (int abase = 0; abase < total; abase += 32) {
             const int j = abase + lane;
             int lo = 0;
@@ -450,6 +453,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
     __syncwarp();
     const int ovf = *(volatile int *)&T.ctr[2];
     const int nt = *(volatile int *)&T.ctr[1];
+    if (lane == 0) wk += (unsigned long long)nt;  // lane 0: keys, lane 1: elements
     const uint64_t xb = TASK == TASK_INIT ? *(volatile unsigned long long *)T.xbits : 0ull;
     long long cnt = 0;
     unsigned long long redges = 0;
@@ -458,10 +462,14 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         if (!ovf) {
             const int u = T.key[h];
             if (TASK == TASK_INIT) {
-                // snapshot-edges of the task: sum over (u, r) reached of outdeg(u)
-                const int c = __popcll(lmk_effective(a, word, u, T.vis[h], xb));
-                cnt += c;
-                redges += (unsigned long long)c * (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
+                // bits recorded before the task reached the landmark in that
+                // snapshot are credited by the landmark instead
+                const uint64_t v = T.vis[h];
+                const uint64_t ve = lmk_effective(a, word, u, v, xb);
+                cnt += __popcll(ve);
+                if (ve != v)
+                    tedges -= (unsigned long long)__popcll(v & ~ve) *
+                              (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
             } else {
                 const int c = __popcll(T.vis[h]);
                 atomicAdd((unsigned long long *)&a.s[u], (unsigned long long)(-(long long)c));
@@ -477,10 +485,10 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         if (lane == 0 && !ovf) {
             unsigned long long e = 0;
             lmk_totals(a, word, xb, cnt, e);
-            redges += e;
+            tedges += e;
         }
     }
-    if (!ovf) edges_acc += redges;
+    if (!ovf) edges_acc += TASK == TASK_INIT ? tedges : redges;
     __syncwarp();
     if (lane == 0) {
         if (!ovf && TASK == TASK_INIT) atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)cnt);
@@ -515,7 +523,7 @@ __global__ void __launch_bounds__(WE_THREADS) warp_engine_kernel(EngineArgs a, i
     __syncwarp();
     Ctl *ctl = a.ctl;
     const long long ntasks = TASK == TASK_INIT ? a.ntasks : *(volatile long long *)&ctl->du_total;
-    unsigned long long edges = 0;
+    unsigned long long edges = 0, wk = 0;
     while (true) {
         long long base = 0;
         if (lane == 0) base = (long long)atomicAdd(&ctl->t1_next, (unsigned long long)chunk);
@@ -523,12 +531,15 @@ __global__ void __launch_bounds__(WE_THREADS) warp_engine_kernel(EngineArgs a, i
         if (base >= ntasks) break;
         const long long tend = min(base + (long long)chunk, ntasks);
         for (long long t = base; t < tend; ++t) {
-            const bool ovf = warp_task<LOGC, DIR, MODEL, TASK>(a, T, t, lane, edges);
+            const bool ovf = warp_task<LOGC, DIR, MODEL, TASK>(a, T, t, lane, edges, wk);
             if (ovf && lane == 0) a.list1[atomicAdd(&ctl->l1_count, 1ull)] = (int32_t)t;
         }
     }
     edges = warp_sum(edges);
     if (lane == 0 && edges) atomicAdd(TASK == TASK_INIT ? &ctl->init_edges : &ctl->rev_edges, edges);
+    if (lane < 2 && wk)
+        atomicAdd(lane == 0 ? &ctl->work_keys[TASK == TASK_INIT ? 0 : 1][0] : &ctl->work_elems[TASK == TASK_INIT ? 0 : 1][0],
+                  wk);
 }
 
 // ============================================================= CTA engine
@@ -923,13 +934,14 @@ __device__ __forceinline__ void coop_seed(CoopTab<TAB> &T, CoopCtl &c, int y, ui
 // The block's warps expand the task's frontier until nothing is queued or
 // claimed.
 template <int TAB, int DIR, int MODEL, int TASK>
-__device__ __forceinline__ void coop_expand(const EngineArgs &a, CoopTab<TAB> &T, CoopCtl &c, int word,
-                                                          uint32_t rs, int limit)
+__device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, CoopTab<TAB> &T, CoopCtl &c, int word,
+                                                          uint32_t rs, int limit, unsigned long long &elems)
 {
     constexpr int SLICE = TASK == TASK_REVT ? SLICE_TGT : SLICE_SNAP;
     const GraphView &g = a.g;
     const Coins &co = a.co;
     const int lane = threadIdx.x & 31;
+    unsigned long long tedges = 0;
     long long idle = 0;
     while (true) {
         int nb = 0, qb = 0;
@@ -992,6 +1004,7 @@ __device__ __forceinline__ void coop_expand(const EngineArgs &a, CoopTab<TAB> &T
                 vdeg = F ? rr.vdeg : 0;
                 heavy = rr.heavy;
                 rtm1 = rr.rtm1;
+                if (TASK == TASK_INIT) tedges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
             }
         }
         int incl = vdeg;
@@ -1002,6 +1015,7 @@ __device__ __forceinline__ void coop_expand(const EngineArgs &a, CoopTab<TAB> &T
         }
         const int total = __shfl_sync(FULL, incl, 31);
         const int excl = incl - vdeg;
+        if (lane == 0) elems += (unsigned long long)total;
         for (int abase = 0; abase < total; abase += 32) {
             const int j = abase + lane;
             int lo = 0;
@@ -1042,6 +1056,7 @@ __device__ __forceinline__ void coop_expand(const EngineArgs &a, CoopTab<TAB> &T
             atomicSub(&c.busy, 1);
         }
     }
+    return tedges;
 }
 
 // Tier 2 (TAB_HASH, tasks of list1) and tier 3 (TAB_DENSE, tasks of list2).
@@ -1080,7 +1095,7 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
     const long long count = (long long)*(volatile unsigned long long *)(TAB == TAB_HASH ? &ctl->l1_count : &ctl->l2_count);
     unsigned long long *next = TAB == TAB_HASH ? &ctl->l1_next : &ctl->l2_next;
     const int32_t *list = TAB == TAB_HASH ? a.list1 : a.list2;
-    unsigned long long edges = 0;
+    unsigned long long edges = 0, wk_keys = 0, wk_elems = 0;
     __syncthreads();
     while (true) {
         if (tid == 0) sh_t = (long long)atomicAdd(next, 1ull);
@@ -1115,7 +1130,7 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
             if (tid < cnt) coop_seed<TAB>(T, c, a.tl[b0 + tid], 1ull << tid, limit);
         }
         __syncthreads();
-        coop_expand<TAB, DIR, MODEL, TASK>(a, T, c, word, rs, limit);
+        unsigned long long tedges = coop_expand<TAB, DIR, MODEL, TASK>(a, T, c, word, rs, limit, wk_elems);
         __syncthreads();
         const int ovf = c.overflow | c.err;
         const int nt = c.nkeys;
@@ -1127,9 +1142,12 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
             if (!ovf) {
                 const int u = T.node(idx);
                 if (TASK == TASK_INIT) {
-                    const int cc = __popcll(lmk_effective(a, word, u, T.vis[idx], xb));
-                    cnt += cc;
-                    redges += (unsigned long long)cc * (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
+                    const uint64_t v = T.vis[idx];
+                    const uint64_t ve = lmk_effective(a, word, u, v, xb);
+                    cnt += __popcll(ve);
+                    if (ve != v)
+                        tedges -= (unsigned long long)__popcll(v & ~ve) *
+                                  (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
                 } else {
                     const int cc = __popcll(T.vis[idx]);
                     atomicAdd((unsigned long long *)&a.s[u], (unsigned long long)(-(long long)cc));
@@ -1139,7 +1157,8 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
             T.clear_slot(idx);
         }
         if (ovf) T.clear_queue(c.head, c.tail);
-        if (!ovf) edges += redges;
+        if (!ovf) edges += (TASK == TASK_INIT ? tedges : 0) + redges;
+        if (tid == 0) wk_keys += (unsigned long long)nt;
         if (TASK == TASK_INIT) {
             cnt = warp_sum(cnt);
             if (lane == 0) red_ll[wid] = cnt;
@@ -1161,11 +1180,19 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
         __syncthreads();
     }
     edges = warp_sum(edges);
+    wk_elems = warp_sum(wk_elems);
     if (lane == 0) red_ull[wid] = edges;
+    if (lane == 0) red_ll[wid] = (long long)wk_elems;
     __syncthreads();
     if (tid == 0) {
-        unsigned long long tot = 0;
-        for (int w = 0; w < CO_W; ++w) tot += red_ull[w];
+        unsigned long long tot = 0, el = 0;
+        for (int w = 0; w < CO_W; ++w) {
+            tot += red_ull[w];
+            el += (unsigned long long)red_ll[w];
+        }
+        const int tr = TAB == TAB_HASH ? 1 : 2;
+        atomicAdd(&ctl->work_keys[TASK == TASK_INIT ? 0 : 1][tr], wk_keys);
+        atomicAdd(&ctl->work_elems[TASK == TASK_INIT ? 0 : 1][tr], el);
         if (tot) atomicAdd(TASK == TASK_INIT ? &ctl->init_edges : &ctl->rev_edges, tot);
         if (blockIdx.x == 0) {
             if (TAB == TAB_HASH) {

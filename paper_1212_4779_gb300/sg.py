@@ -49,10 +49,15 @@ class sg_stats(ctypes.Structure):
                 ("ms_index", ctypes.c_float), ("ms_init", ctypes.c_float), ("ms_init_tier1", ctypes.c_float),
                 ("ms_rounds", ctypes.c_float), ("ms_fwd", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("status_flags", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("heavy_index", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("heavy_index", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("work_keys", (ctypes.c_uint64 * 3) * 2), ("work_elems", (ctypes.c_uint64 * 3) * 2)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = [list(row) for row in v] if k.startswith("work_") else v
+        return out
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
