@@ -135,6 +135,13 @@ sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys);
  * depend on it.  Applies to later calls.  Errors: SG_EINVAL unless 0 or 1. */
 sg_status sg_set_landmarks(int32_t count);
 
+/* Per-snapshot live in-arc lists of heavy rows for the reverse (dynamic
+ * update) pass: 1 (the default) builds them per query from the heavy-row
+ * index so that a reverse step over one snapshot reads only that
+ * snapshot's live in-arcs of a hub; 0 disables.  Results do not depend on
+ * it.  Applies to later calls.  Errors: SG_EINVAL unless 0 or 1. */
+sg_status sg_set_snapshot_lists(int32_t enable);
+
 /* Same as sg_load_graph from an arc list src[i] -> dst[i], i < m.
  * src/dst are host memory when is_device_ptr is 0, device memory when 1. */
 sg_status sg_load_graph_coo(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,

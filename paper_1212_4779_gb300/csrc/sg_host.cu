@@ -32,6 +32,8 @@ void set_error(const char *fmt, ...)
 void clear_error() { g_err[0] = 0; }
 
 // ------------------------------------------------------------------ memory
+int g_snapshot_lists = 1;
+
 namespace {
 int g_heavy_min_deg = 64;
 sg_alloc_fn g_alloc = nullptr;
@@ -170,6 +172,13 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.hcnt_in, st);
     dbuf_free(ws.hnbr_in, st);
     dbuf_free(ws.hmask_in, st);
+    dbuf_free(ws.soff, st);
+    dbuf_free(ws.snbr, st);
+    dbuf_free(ws.svalid, st);
+    dbuf_free(ws.scan_tmp, st);
+    ws.soff_cap = 0;
+    ws.snbr_cap = 0;
+    ws.slists_on = 0;
     ws.hw_cap = 0;
     dbuf_free(ws.slot_vis, st);
     dbuf_free(ws.slot_pend, st);
@@ -335,8 +344,10 @@ GraphView view_of(const sg_graph *g, int heavy_on)
     v.cin = g->cin.p;
     v.tmi = g->tmi.p;
     const sg_workspace &ws = g->ws;
-    v.hout = HeavyView{g->hid_out.p, g->hpref_out.p, ws.hcnt_out.p, ws.hnbr_out.p, ws.hmask_out.p};
-    v.hin = HeavyView{g->hid_in.p, g->hpref_in.p, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p};
+    v.hout = HeavyView{g->hid_out.p, g->hpref_out.p, ws.hcnt_out.p, ws.hnbr_out.p, ws.hmask_out.p,
+                       nullptr, nullptr, nullptr};
+    v.hin = HeavyView{g->hid_in.p, g->hpref_in.p, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p,
+                      ws.slists_on ? ws.soff.p : nullptr, ws.snbr.p, ws.svalid.p};
     v.heavy_on = heavy_on;
     return v;
 }
@@ -360,6 +371,13 @@ sg_status ensure_heavy_index(sg_graph *g, int32_t W, cudaStream_t st)
     dbuf_free(ws.hcnt_in, st);
     dbuf_free(ws.hnbr_in, st);
     dbuf_free(ws.hmask_in, st);
+    dbuf_free(ws.soff, st);
+    dbuf_free(ws.snbr, st);
+    dbuf_free(ws.svalid, st);
+    dbuf_free(ws.scan_tmp, st);
+    ws.soff_cap = 0;
+    ws.snbr_cap = 0;
+    ws.slists_on = 0;
     ws.hw_cap = 0;
     SG_TRY(dbuf_alloc(ws.hcnt_out, (size_t)g->nh_out * W, st));
     SG_TRY(dbuf_alloc(ws.hnbr_out, (size_t)g->hsum_out * W, st));
@@ -394,8 +412,8 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
         SG_TRY(dbuf_alloc(ws.nbits, nw, st));
         SG_TRY(dbuf_alloc(ws.pendf, nw, st));
         SG_TRY(dbuf_alloc(ws.du_m, nw, st));
-        SG_TRY(dbuf_alloc(ws.fq_a, nw, st));
-        SG_TRY(dbuf_alloc(ws.fq_b, nw, st));
+        SG_TRY(dbuf_alloc(ws.fq_a, nw * 8, st));  // one queue per (word, forward group)
+        SG_TRY(dbuf_alloc(ws.fq_b, nw * 8, st));
         SG_TRY(dbuf_alloc(ws.du_x, nw, st));
         const size_t ltasks = nw + (size_t)64 * W + 64;
         SG_TRY(dbuf_alloc(ws.list1, ltasks, st));
@@ -444,6 +462,38 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
         SG_TRY(dbuf_alloc(ws.out_gains, (size_t)k, st));
         ws.kcap = k;
     }
+    return SG_OK;
+}
+
+// Per-snapshot live in-lists of heavy rows.  Their total size is a random
+// count with mean R * sum over heavy in-arcs of p(arc) (WIC: R per heavy
+// row); the list buffer holds 1.5x that plus slack, and if a query exceeds
+// it the device flag marks the lists invalid and the reverse tasks use the
+// per-word index instead.  Skipped when the buffer would pass 2 GiB.
+sg_status ensure_snapshot_lists(sg_graph *g, const Coins &co, double p_uic, int model, cudaStream_t st)
+{
+    sg_workspace &ws = g->ws;
+    ws.slists_on = 0;
+    if (g->nh_in == 0) return SG_OK;
+    const double R = 64.0 * co.W;
+    const double expect = model == MODEL_WIC ? R * (double)g->nh_in : R * p_uic * (double)g->hsum_in;
+    const size_t want = (size_t)(expect * 1.5) + (1u << 20);
+    const size_t nq = (size_t)g->nh_in * 64 * co.W + 1;
+    if ((double)want * 4.0 + (double)nq * 16.0 > 2.0 * (double)(1ull << 30)) return SG_OK;
+    if (ws.soff_cap < nq) {
+        dbuf_free(ws.soff, st);
+        dbuf_free(ws.scan_tmp, st);
+        SG_TRY(dbuf_alloc(ws.soff, nq, st));
+        SG_TRY(dbuf_alloc(ws.scan_tmp, nq + nq / 1024 + 16, st));
+        ws.soff_cap = nq;
+    }
+    if (ws.snbr_cap < want) {
+        dbuf_free(ws.snbr, st);
+        SG_TRY(dbuf_alloc(ws.snbr, want, st));
+        ws.snbr_cap = want;
+    }
+    if (!ws.svalid.p) SG_TRY(dbuf_alloc(ws.svalid, 1, st));
+    ws.slists_on = 1;
     return SG_OK;
 }
 
@@ -544,6 +594,16 @@ sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys)
     }
     g_tier_limit[0] = tier1_keys;
     g_tier_limit[1] = tier2_keys;
+    return SG_OK;
+}
+
+sg_status sg_set_snapshot_lists(int32_t enable)
+{
+    if (enable < 0 || enable > 1) {
+        set_error("enable must be 0 or 1");
+        return SG_EINVAL;
+    }
+    g_snapshot_lists = enable;
     return SG_OK;
 }
 
@@ -707,6 +767,8 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     SG_TRY(ensure_workspace(g, co.W, k, st));
     const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, co.W, st));
+    g->ws.slists_on = 0;
+    if (heavy_on && g_snapshot_lists) SG_TRY(ensure_snapshot_lists(g, co, c.p, model, st));
     sg_workspace &ws = g->ws;
     // events: 0 start, 1 after index, 2 after init tier 1, 3 after init,
     // 4 end; per round: after forward update
@@ -738,6 +800,7 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     SG_CUDA_TRY(cudaMemsetAsync(ws.anc_cnt.p, 0, (size_t)co.W * 4, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) SG_TRY(run_heavy_index(g, co, model, st));
+    if (ws.slists_on) SG_TRY(run_snapshot_lists(g, co, st));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_index, st));
     SG_TRY(run_init_gains(g, co, model, heavy_on, st, e_t1));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_init, st));
@@ -810,6 +873,7 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     SG_TRY(ensure_workspace(g, co.W, 1, st));
     const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, co.W, st));
+    g->ws.slists_on = 0;
     sg_workspace &ws = g->ws;
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));

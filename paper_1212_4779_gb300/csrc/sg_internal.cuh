@@ -106,6 +106,11 @@ struct HeavyView {
     const int32_t *hcnt;
     const int32_t *hnbr;
     const unsigned long long *hmask;
+    // per-snapshot live lists (reverse direction only): the live in-arcs of
+    // heavy row h in snapshot r are snbr[soff[h*64W + r] .. soff[h*64W + r + 1])
+    const long long *soff;
+    const int32_t *snbr;
+    const int32_t *svalid;  // device flag: 1 if the lists were built completely
 };
 
 struct GraphView {
@@ -176,6 +181,12 @@ struct sg_workspace {
     sgi::DBuf<int32_t> hcnt_out, hnbr_out, hcnt_in, hnbr_in;
     sgi::DBuf<unsigned long long> hmask_out, hmask_in;
     int32_t hw_cap = 0;   // W the heavy index was sized for
+    // per-snapshot live in-lists of heavy rows
+    sgi::DBuf<long long> soff;
+    sgi::DBuf<int32_t> snbr, svalid;
+    sgi::DBuf<long long> scan_tmp;
+    size_t soff_cap = 0, snbr_cap = 0;
+    int32_t slists_on = 0;    // built for the current query
     int32_t kcap = 0;
     int32_t am_blocks = 0;
 };
@@ -216,9 +227,13 @@ extern thread_local int g_launches;
 extern int g_tier_limit[2];
 // landmark nodes used for the initial gains (0 or 1)
 extern int g_landmarks;
+// per-snapshot live in-lists of heavy rows for the reverse update (0 or 1)
+extern int g_snapshot_lists;
 
 // kernels (sg_kernels.cu)
 sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t st);
+sg_status run_snapshot_lists(sg_graph *g, const Coins &co, cudaStream_t st);
+sg_status ensure_snapshot_lists(sg_graph *g, const Coins &co, double p_uic, int model, cudaStream_t st);
 sg_status run_init_gains(sg_graph *g, const Coins &co, int model, int heavy_on, cudaStream_t st,
                          cudaEvent_t after_t1 = nullptr);
 sg_status run_round(sg_graph *g, const Coins &co, int model, int heavy_on, int32_t round, cudaStream_t st,

@@ -120,8 +120,8 @@ struct Row {
     uint32_t rtm1;
 };
 
-template <int DIR, int MODEL>
-__device__ __forceinline__ Row row_ref(const GraphView &g, const Coins &co, int x, int word)
+template <int DIR, int MODEL, int SLICE = SLICE_SNAP>
+__device__ __forceinline__ Row row_ref(const GraphView &g, const Coins &co, int x, int word, uint32_t rs = 0)
 {
     Row r;
     int beg, end;
@@ -138,7 +138,13 @@ __device__ __forceinline__ Row row_ref(const GraphView &g, const Coins &co, int 
     r.rtm1 = (MODEL == MODEL_WIC && DIR == DIR_REV) ? __ldg(g.tmi + x) : co.uic_tm1;
     const HeavyView &hv = DIR == DIR_FWD ? g.hout : g.hin;
     const int h = g.heavy_on ? __ldg(hv.hid + x) : -1;
-    if (h >= 0) {
+    if (DIR == DIR_REV && SLICE == SLICE_TGT && h >= 0 && hv.soff && __ldg(hv.svalid)) {
+        // one snapshot: its live in-arcs directly
+        const long long q = (long long)h * (64 * co.W) + rs;
+        r.heavy = 2;
+        r.base = __ldg(hv.soff + q);
+        r.vdeg = (int)(__ldg(hv.soff + q + 1) - r.base);
+    } else if (h >= 0) {
         r.heavy = 1;
         r.base = __ldg(hv.hpref + h) * co.W + (long long)word * r.deg;
         r.vdeg = __ldg(hv.hcnt + (long long)h * co.W + word);
@@ -156,6 +162,10 @@ __device__ __forceinline__ uint64_t elem(const GraphView &g, const Coins &co, lo
                                          uint32_t rtm1, int j, uint64_t F, uint32_t rs, int &y)
 {
     const HeavyView &hv = DIR == DIR_FWD ? g.hout : g.hin;
+    if (SLICE == SLICE_TGT && DIR == DIR_REV && heavy == 2) {
+        y = __ldg(hv.snbr + base + j);
+        return F;
+    }
     if (heavy) {
         const long long q = base + j;
         y = __ldg(hv.hnbr + q);
@@ -393,7 +403,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
             const int x = T.key[h];
             F = T.pend[h];
             T.pend[h] = 0;
-            const Row rr = row_ref<DIR, MODEL>(g, co, x, word);
+            const Row rr = row_ref<DIR, MODEL, SLICE>(g, co, x, word, rs);
             base = rr.base;
             vdeg = rr.vdeg;
             heavy = rr.heavy;
@@ -608,9 +618,11 @@ struct CtaState {
     unsigned long long *pend;
     int32_t *qa;
     int32_t *qb;
-    int32_t *touched;           // TASK_INIT / TASK_REVT
-    unsigned long long *nbits;  // TASK_FWD
-    int32_t *du_x;              // TASK_FWD (this word's list)
+    int32_t *touched;           // TASK_INIT / TASK_REVT / TASK_ANC
+    unsigned long long *nbits;  // TASK_FWD / TASK_LMK
+    int32_t *du_x;              // TASK_FWD / TASK_LMK: the word's list of nodes gaining bits
+    int32_t *ndu;               // ... and its length (global, shared by the word's blocks)
+    unsigned long long gm;      // snapshot bits this block owns (several blocks may share a word)
 };
 
 // One traversal by the whole block over dense arrays, level-synchronous.
@@ -652,17 +664,21 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
         }
     } else if (tid == 0) {
         uint64_t M = M0;
-        if (TASK == TASK_FWD || TASK == TASK_LMK) M &= ~w.vis[x0];
-        if (M) {
+        if (TASK == TASK_FWD || TASK == TASK_LMK) {
+            M &= w.gm;
+            M &= ~atomicOr(&w.vis[x0], (unsigned long long)M);
+            if (M) {
+                atomicOr(&w.pend[x0], (unsigned long long)M);
+                w.qa[0] = x0;
+                S.qlen = 1;
+                if (atomicOr(&w.nbits[x0], (unsigned long long)M) == 0) w.du_x[atomicAdd(w.ndu, 1)] = x0;
+            }
+        } else if (M) {
             w.vis[x0] |= M;
             w.pend[x0] = M;
             w.qa[0] = x0;
             S.qlen = 1;
-            if (TASK == TASK_FWD || TASK == TASK_LMK) {
-                w.nbits[x0] |= M;
-                w.du_x[0] = x0;
-                S.ndu = 1;
-            } else {
+            {
                 w.touched[0] = x0;
                 S.ntouch = 1;
                 if (TASK == TASK_INIT) cnt = __popcll(M);
@@ -680,8 +696,9 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
             int vd = 0;
             if (i < L) {
                 const int x = cur[i];
-                const uint64_t F = atomicExch(&w.pend[x], 0ull);
-                const Row rr = row_ref<DIR, MODEL>(g, co, x, word);
+                const uint64_t F = w.gm == ~0ull ? atomicExch(&w.pend[x], 0ull)
+                                                 : (atomicAnd(&w.pend[x], ~w.gm) & w.gm);
+                const Row rr = row_ref<DIR, MODEL, SLICE>(g, co, x, word, rs);
                 vd = F ? rr.vdeg : 0;
                 S.F[tid] = F;
                 S.base[tid] = rr.base;
@@ -718,10 +735,10 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                                 w.touched[atomicAdd(&S.ntouch, 1)] = y;
                             if (TASK == TASK_FWD || TASK == TASK_LMK) {
                                 const uint64_t ob = atomicOr(&w.nbits[y], (unsigned long long)nw);
-                                if (ob == 0) w.du_x[atomicAdd(&S.ndu, 1)] = y;
+                                if (ob == 0) w.du_x[atomicAdd(w.ndu, 1)] = y;
                             }
                             const uint64_t op = atomicOr(&w.pend[y], (unsigned long long)nw);
-                            if (op == 0) nxt[atomicAdd(&S.qnext, 1)] = y;
+                            if ((op & w.gm) == 0) nxt[atomicAdd(&S.qnext, 1)] = y;
                         }
                     }
                 }
@@ -999,7 +1016,7 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
             const int idx = T.take(qb + lane, c);
             if (idx >= 0) {
                 F = atomicExch(&T.pend[idx], 0ull);
-                const Row rr = row_ref<DIR, MODEL>(g, co, T.node(idx), word);
+                const Row rr = row_ref<DIR, MODEL, SLICE>(g, co, T.node(idx), word, rs);
                 base = rr.base;
                 vdeg = F ? rr.vdeg : 0;
                 heavy = rr.heavy;
@@ -1218,10 +1235,41 @@ struct FwdArgs {
     long long tcap;  // per-word capacity of tl
 };
 
-// Forward DU (Algorithm 2, inner loops) for the 64 snapshots of block
-// `word`:
-//  1. walk from v* over live arcs with the word's coverage bitset as the
-//     visited set: N_r = R(G'_r, v*) minus what earlier seeds cover;
+constexpr int FWD_GROUPS = 8;  // blocks per 64-snapshot word in the forward walk
+
+// Forward DU, walk (Algorithm 2, inner loops): block (word, group) walks
+// from v* over the live arcs of the 64/FWD_GROUPS snapshots it owns, with
+// the word's coverage bitset as the visited set, so that N_r = R(G'_r, v*)
+// minus what earlier seeds cover is marked in cov and nbits; every node of
+// the word gaining bits is listed once.
+template <int MODEL>
+__global__ void __launch_bounds__(BT) fwd_walk_kernel(EngineArgs a, FwdArgs f)
+{
+    __shared__ CtaShared S;
+    const int n = a.g.n;
+    const int word = blockIdx.x / FWD_GROUPS;
+    const int grp = blockIdx.x - word * FWD_GROUPS;
+    const int vstar = *(volatile int32_t *)&a.ctl->vstar;
+    if (vstar < 0) return;
+    constexpr int GB = 64 / FWD_GROUPS;
+    const size_t so = (size_t)word * (size_t)n;
+    const size_t qo = (size_t)blockIdx.x * (size_t)n;
+    CtaState w;
+    w.vis = f.cov + so;
+    w.pend = f.pendf + so;
+    w.qa = f.fq_a + qo;
+    w.qb = f.fq_b + qo;
+    w.touched = nullptr;
+    w.nbits = f.nbits + so;
+    w.du_x = f.du_x + so;
+    w.ndu = f.du_cnt + word;
+    w.gm = (GB == 64 ? ~0ull : ((1ull << GB) - 1ull)) << (grp * GB);
+    cta_bfs<DIR_FWD, MODEL, TASK_FWD>(a, w, vstar, word_mask(word, a.co.R), word, (uint32_t)word * 64u, nullptr, 0,
+                                      nullptr, S);
+}
+
+// Forward DU, per word after the walk:
+//  1. |N_r| for the word's snapshots;
 //  2. walk back from v* over live in-arcs: every u reaching v* in snapshot
 //     r reaches all of N_r (N_r lies inside R(G'_r, v*)), so s_u drops by
 //     |N_r| at once; these ancestors are marked so that
@@ -1231,10 +1279,11 @@ struct FwdArgs {
 // The last block to finish turns the per-snapshot counts into the offsets
 // of the reverse tasks.
 template <int MODEL>
-__global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
+__global__ void __launch_bounds__(BT) fwd_post_kernel(EngineArgs a, FwdArgs f)
 {
     __shared__ CtaShared S;
     __shared__ int sh_last;
+    __shared__ unsigned long long sh_mv;
     const int n = a.g.n;
     const int word = blockIdx.x;
     const int tid = threadIdx.x;
@@ -1247,24 +1296,10 @@ __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
     {
         const int na = f.anc_cnt[word];
         for (int i = tid; i < na; i += BT) ancw[anclw[i]] = 0;
-        __syncthreads();
     }
-    if (vstar >= 0) {
-        CtaState w;
-        w.vis = f.cov + so;
-        w.pend = f.pendf + so;
-        w.qa = f.fq_a + so;
-        w.qb = f.fq_b + so;
-        w.touched = nullptr;
-        w.nbits = f.nbits + so;
-        w.du_x = f.du_x + so;
-        cta_bfs<DIR_FWD, MODEL, TASK_FWD>(a, w, vstar, word_mask(word, a.co.R), word, (uint32_t)word * 64u, nullptr,
-                                          0, nullptr, S);
-    } else {
-        if (tid == 0) S.ndu = 0;
-        __syncthreads();
-    }
-    const int nd = S.ndu;
+    if (tid == 0) sh_mv = vstar >= 0 ? f.nbits[so + vstar] : 0ull;  // bits v* newly covers
+    __syncthreads();
+    const int nd = vstar >= 0 ? *(volatile int32_t *)&f.du_cnt[word] : 0;
     int32_t *dux = f.du_x + so;
     unsigned long long *dum = f.du_m + so;
     unsigned long long *nb = f.nbits + so;
@@ -1288,18 +1323,20 @@ __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
     __syncthreads();
     if (tid < 64) S.boff[tid] = S.bcnt[tid];  // keep |N_r| while bcnt is reused
     __syncthreads();
-    // ancestors of v* (dux[0] is v* whenever this word has new coverage)
+    // ancestors of v* over the snapshots where v* newly covers nodes
     int nanc = 0;
-    if (nd > 0) {
+    if (sh_mv) {
         CtaState w;
         w.vis = ancw;
         w.pend = f.pendf + so;
-        w.qa = f.fq_a + so;
-        w.qb = f.fq_b + so;
+        w.qa = f.fq_a + (size_t)word * FWD_GROUPS * (size_t)n;
+        w.qb = f.fq_b + (size_t)word * FWD_GROUPS * (size_t)n;
         w.touched = anclw;
         w.nbits = nullptr;
         w.du_x = nullptr;
-        cta_bfs<DIR_REV, MODEL, TASK_ANC>(a, w, dux[0], dum[0], word, (uint32_t)word * 64u, nullptr, 0, S.boff, S);
+        w.ndu = nullptr;
+        w.gm = ~0ull;
+        cta_bfs<DIR_REV, MODEL, TASK_ANC>(a, w, vstar, sh_mv, word, (uint32_t)word * 64u, nullptr, 0, S.boff, S);
         nanc = S.ntouch;
     }
     if (tid == 0) f.anc_cnt[word] = nanc;
@@ -1338,7 +1375,6 @@ __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
         }
     }
     if (tid == 0) {
-        f.du_cnt[word] = nd;
         __threadfence();
         const unsigned prev = atomicAdd(&ctl->fwd_arrivals, 1u);
         sh_last = (prev == gridDim.x - 1);
@@ -1376,7 +1412,7 @@ __global__ void __launch_bounds__(BT) fwd_du_kernel(EngineArgs a, FwdArgs f)
 // per snapshot |R(G'_r, x)| and the out-degree sum over it.
 struct LmkArgs {
     unsigned long long *rx, *pendf, *nbits, *edges;
-    int32_t *fq_a, *fq_b, *list, *cnt;
+    int32_t *fq_a, *fq_b, *list, *cnt, *ndu;
 };
 
 template <int MODEL>
@@ -1395,6 +1431,8 @@ __global__ void __launch_bounds__(BT) landmark_kernel(EngineArgs a, LmkArgs l)
     w.touched = nullptr;
     w.nbits = l.nbits + so;
     w.du_x = l.list + so;
+    w.ndu = l.ndu + word;
+    w.gm = ~0ull;
     cta_bfs<DIR_FWD, MODEL, TASK_LMK>(a, w, a.lmk_x, word_mask(word, a.co.R), word, (uint32_t)word * 64u, nullptr, 0,
                                       nullptr, S);
     if (tid < 64) {
@@ -1402,7 +1440,7 @@ __global__ void __launch_bounds__(BT) landmark_kernel(EngineArgs a, LmkArgs l)
         esum[tid] = 0;
     }
     __syncthreads();
-    const int nd = S.ndu;
+    const int nd = *(volatile int32_t *)w.ndu;
     for (int i = tid; i < nd; i += BT) {
         const int y = w.du_x[i];
         w.nbits[y] = 0;
@@ -1434,7 +1472,8 @@ __device__ __forceinline__ bool better(long long g1, int i1, long long g2, int i
 // v* = argmax over non-seeds (s >= 0) of s, lowest id on ties; the last
 // block publishes it, marks v* as a seed, and resets the round's counters.
 __global__ void __launch_bounds__(AM_T) argmax_kernel(long long *s, int n, Ctl *ctl, long long *pg, int *pi,
-                                                      int32_t *out_seeds, long long *out_gains, int round)
+                                                      int32_t *out_seeds, long long *out_gains, int round,
+                                                      int32_t *du_cnt, int W)
 {
     __shared__ long long sg[AM_T / 32];
     __shared__ int si[AM_T / 32];
@@ -1478,6 +1517,7 @@ __global__ void __launch_bounds__(AM_T) argmax_kernel(long long *s, int n, Ctl *
     __syncthreads();
     if (!sh_last) return;
     __threadfence();
+    for (int w = threadIdx.x; w < W; w += AM_T) du_cnt[w] = 0;
     bg = -1;
     bi = -1;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += AM_T) {
@@ -1585,6 +1625,97 @@ __global__ void __launch_bounds__(256) heavy_index_kernel(GraphView g, Coins co,
             }
         }
     }
+}
+
+
+// ------------------------------------------- per-snapshot heavy in-lists
+// From the per-word index of heavy in-rows: count the live in-arcs of every
+// (heavy row, snapshot), scan, and fill.  mode 0 counts into scnt, mode 1
+// fills snbr using scnt as cursors (reset to zero in between).
+__global__ void __launch_bounds__(256) snapshot_lists_kernel(Coins co, int nh, const int32_t *hcnt,
+                                                             const int32_t *hnbr, const unsigned long long *hmask,
+                                                             const long long *hpref, const int32_t *crp,
+                                                             const int32_t *hrow, long long *scnt,
+                                                             const long long *soff, int32_t *snbr,
+                                                             long long cap, int32_t *svalid, int mode)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nseg = (long long)nh * co.W;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int R64 = 64 * co.W;
+    for (long long sg = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5); sg < nseg; sg += nwarps) {
+        const int h = (int)(sg / co.W);
+        const int w = (int)(sg - (long long)h * co.W);
+        const int x = hrow[h];
+        const int deg = crp[x + 1] - crp[x];
+        const long long seg = hpref[h] * co.W + (long long)w * deg;
+        const int cnt = hcnt[sg];
+        for (int j = lane; j < cnt; j += 32) {
+            uint64_t M = hmask[seg + j];
+            const int y = hnbr[seg + j];
+            while (M) {
+                const int b = __ffsll((long long)M) - 1;
+                M &= M - 1;
+                const long long q = (long long)h * R64 + 64 * w + b;
+                if (mode == 0) {
+                    atomicAdd((unsigned long long *)&scnt[q], 1ull);
+                } else {
+                    const long long pos = soff[q] + (long long)atomicAdd((unsigned long long *)&scnt[q], 1ull);
+                    if (pos < cap) snbr[pos] = y;
+                }
+            }
+        }
+    }
+    if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) *svalid = soff[(long long)nh * R64] <= cap ? 1 : 0;
+}
+
+// Exclusive scan of int64 counts (in place into `out`), three phases.
+constexpr int SC_T = 1024;
+__global__ void __launch_bounds__(SC_T) scan_blocks_kernel(const long long *in, long long *out, long long n,
+                                                           long long *sums)
+{
+    __shared__ long long sh[SC_T];
+    const long long i = blockIdx.x * (long long)SC_T + threadIdx.x;
+    const long long v = i < n ? in[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < SC_T; o <<= 1) {
+        const long long t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = sh[threadIdx.x] - v;
+    if (threadIdx.x == SC_T - 1) sums[blockIdx.x] = sh[SC_T - 1];
+}
+
+__global__ void __launch_bounds__(SC_T) scan_sums_kernel(long long *sums, long long nb, long long *total)
+{
+    __shared__ long long sh[SC_T];
+    long long carry = 0;
+    for (long long base = 0; base < nb; base += SC_T) {
+        const long long i = base + threadIdx.x;
+        const long long v = i < nb ? sums[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < SC_T; o <<= 1) {
+            const long long t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) sums[i] = carry + sh[threadIdx.x] - v;
+        const long long add = sh[SC_T - 1];
+        __syncthreads();
+        carry += add;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void scan_add_kernel(long long *out, long long n, const long long *sums)
+{
+    const long long i = blockIdx.x * (long long)SC_T + threadIdx.x;
+    if (i < n) out[i] += sums[blockIdx.x];
 }
 
 // ============================================================== live masks
@@ -1709,6 +1840,8 @@ sg_status init_gains_t(sg_graph *g, const Coins &co, int heavy_on, cudaStream_t 
         l.fq_b = ws.fq_b.p;
         l.list = ws.du_x.p;
         l.cnt = ws.lmk_cnt.p;
+        l.ndu = ws.du_cnt.p;
+        SG_CUDA_TRY(cudaMemsetAsync(ws.du_cnt.p, 0, (size_t)co.W * 4, st));
         landmark_kernel<MODEL><<<co.W, BT, 0, st>>>(a, l);
         SG_CUDA_TRY(cudaGetLastError());
         ++g_launches;
@@ -1721,7 +1854,7 @@ sg_status round_t(sg_graph *g, const Coins &co, int heavy_on, int32_t round, cud
 {
     sg_workspace &ws = g->ws;
     argmax_kernel<<<ws.am_blocks, AM_T, 0, st>>>(ws.s.p, (int)g->n, ws.ctl.p, ws.am_gain.p, ws.am_id.p,
-                                                 ws.out_seeds.p, ws.out_gains.p, round);
+                                                 ws.out_seeds.p, ws.out_gains.p, round, ws.du_cnt.p, co.W);
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
     EngineArgs a = engine_args(g, co, heavy_on);
@@ -1742,9 +1875,11 @@ sg_status round_t(sg_graph *g, const Coins &co, int heavy_on, int32_t round, cud
     f.anc = ws.anc.p;
     f.anc_list = ws.anc_list.p;
     f.anc_cnt = ws.anc_cnt.p;
-    fwd_du_kernel<MODEL><<<co.W, BT, 0, st>>>(a, f);
+    fwd_walk_kernel<MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, f);
     SG_CUDA_TRY(cudaGetLastError());
-    ++g_launches;
+    fwd_post_kernel<MODEL><<<co.W, BT, 0, st>>>(a, f);
+    SG_CUDA_TRY(cudaGetLastError());
+    g_launches += 2;
     if (after_fwd) SG_CUDA_TRY(cudaEventRecord(after_fwd, st));
     return launch_tiers<DIR_REV, MODEL, TASK_REVT>(g, a, st, nullptr);
 }
@@ -1763,6 +1898,36 @@ sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t 
     }
     SG_TRY((launch_index<DIR_FWD, MODEL_UIC>(g, co, st)));
     return launch_index<DIR_REV, MODEL_UIC>(g, co, st);
+}
+
+sg_status run_snapshot_lists(sg_graph *g, const Coins &co, cudaStream_t st)
+{
+    sg_workspace &ws = g->ws;
+    const int nh = g->nh_in;
+    const long long nq = (long long)nh * 64 * co.W;
+    // counts
+    SG_CUDA_TRY(cudaMemsetAsync(ws.scan_tmp.p, 0, (size_t)(nq + 1) * 8, st));
+    const int grid = g->num_sms * 8;
+    snapshot_lists_kernel<<<grid, 256, 0, st>>>(co, nh, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p, g->hpref_in.p,
+                                                g->crp.p, g->hrow_in.p, ws.scan_tmp.p, nullptr, nullptr, 0, nullptr,
+                                                0);
+    SG_CUDA_TRY(cudaGetLastError());
+    // offsets: soff[0..nq] = exclusive scan of counts (nq+1 entries, last = total)
+    const long long n1 = nq + 1;
+    const long long nb = (n1 + SC_T - 1) / SC_T;
+    long long *sums = ws.scan_tmp.p + n1;
+    scan_blocks_kernel<<<(unsigned)nb, SC_T, 0, st>>>(ws.scan_tmp.p, ws.soff.p, n1, sums);
+    scan_sums_kernel<<<1, SC_T, 0, st>>>(sums, nb, sums + nb);
+    scan_add_kernel<<<(unsigned)nb, SC_T, 0, st>>>(ws.soff.p, n1, sums);
+    SG_CUDA_TRY(cudaGetLastError());
+    // fill, counts reused as cursors
+    SG_CUDA_TRY(cudaMemsetAsync(ws.scan_tmp.p, 0, (size_t)nq * 8, st));
+    snapshot_lists_kernel<<<grid, 256, 0, st>>>(co, nh, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p, g->hpref_in.p,
+                                                g->crp.p, g->hrow_in.p, ws.scan_tmp.p, ws.soff.p, ws.snbr.p,
+                                                (long long)ws.snbr_cap, ws.svalid.p, 1);
+    SG_CUDA_TRY(cudaGetLastError());
+    g_launches += 5;
+    return SG_OK;
 }
 
 sg_status run_init_gains(sg_graph *g, const Coins &co, int model, int heavy_on, cudaStream_t st,

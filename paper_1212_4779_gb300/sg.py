@@ -27,7 +27,8 @@ _STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ETI
            6: "SG_EINTERNAL"}
 
 # exported entry points, as declared in include/sg.h
-EXPORTS = ("sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+EXPORTS = ("sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
+           "sg_set_snapshot_lists", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
            "sg_init_gains", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
 
 
@@ -87,6 +88,7 @@ def lib() -> ctypes.CDLL:
         L.sg_set_heavy_threshold.argtypes = [i32]
         L.sg_set_engine_limits.argtypes = [i32, i32]
         L.sg_set_landmarks.argtypes = [i32]
+        L.sg_set_snapshot_lists.argtypes = [i32]
         L.sg_load_graph.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_load_graph_coo.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -99,7 +101,7 @@ def lib() -> ctypes.CDLL:
         L.sg_last_error.restype = ctypes.c_char_p
         L.sg_version.restype = ctypes.c_char_p
         for name in ("sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-                     "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+                     "sg_set_snapshot_lists", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
                      "sg_init_gains", "sg_live_masks", "sg_graph_csr"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -214,6 +216,11 @@ def sg_set_heavy_threshold(min_degree: int):
 def sg_set_engine_limits(tier1_keys: int = 256, tier2_keys: int = 4096):
     """Visited-set sizes at which tasks move to the next engine tier."""
     _check(lib().sg_set_engine_limits(int(tier1_keys), int(tier2_keys)))
+
+
+def sg_set_snapshot_lists(enable: int = 1):
+    """Per-snapshot live in-lists of heavy rows for the reverse pass (0: off)."""
+    _check(lib().sg_set_snapshot_lists(int(enable)))
 
 
 def sg_set_landmarks(count: int = 1):

@@ -120,6 +120,27 @@ def limits(sg):
     sg.sg_set_engine_limits(256, 4096)
     sg.sg_set_heavy_threshold(64)
     sg.sg_set_landmarks(1)
+    sg.sg_set_snapshot_lists(1)
+
+
+@pytest.mark.parametrize("lists", [0, 1])
+@pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01"])
+def test_snapshot_lists_give_identical_results(sg, limits, name, lists):
+    """Per-snapshot live in-lists of heavy rows are a cache of the same
+    coins: identical seeds, gains and counters with them on or off, with a
+    low heavy threshold so that many rows use them."""
+    wl = inputs.workload(name)
+    n, s, d = wl.graph()
+    sg.sg_set_heavy_threshold(4)
+    g, o = _both(sg, n, s, d, wl.model, wl.p)
+    sg.sg_set_snapshot_lists(lists)
+    ref = o.select(wl.R, 12, wl.seed, mode=oracle.DU)
+    for t1, t2 in [(256, 4096), (2, 16)]:
+        limits(t1, t2)
+        res = g.select(wl.R, 12, wl.model, wl.p, wl.seed, stats=True)
+        assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+        got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+        assert got == [int(x) for x in ref["counters"]]
 
 
 @pytest.mark.parametrize("lmk", [0, 1])
