@@ -189,6 +189,30 @@ sg_status sg_live_masks(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
  * row_ptr int64[n+1], col int32[m_canonical]. */
 sg_status sg_graph_csr(const sg_graph *g, void *stream, int64_t *row_ptr, int32_t *col);
 
+/* Argmax over a gain vector the caller owns, with no device allocation.
+ * The paper has no counterpart: this exists for callers that cannot
+ * allocate device memory where they need the argmax -- code recording a
+ * CUDA graph (an allocation would break the capture), latency-bound serving
+ * loops that must not stall on an allocation, or plug-ins whose host
+ * framework owns all device memory.
+ *   s         int64[n] in device-accessible memory; entries < 0 are
+ *             excluded (sg_select marks seeds that way)
+ *   n         1 <= n <= 2^31 - 1
+ *   out_id    int32 (device-accessible): the lowest v with the largest
+ *             s[v] >= 0, or -1 if every entry is negative
+ *   out_gain  int64 (device-accessible): s[out_id], or -1
+ * Work is enqueued on `stream`; the call returns without waiting.
+ * Scratch: one statically sized array of about 12 KB per device (1024
+ * block partials and a counter), held until the process exits.  The first
+ * call on a device looks up that array's address (cudaGetSymbolAddress), so
+ * make the first call before any stream capture.  Every call shares the
+ * array: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  No cudaMalloc, cudaFree or other
+ * allocating routine is called.
+ * Errors: SG_EINVAL (NULL pointer, n out of range, device ordinal >= 64),
+ * SG_ECUDA. */
+sg_status sg_argmax_noalloc(const int64_t *s, int64_t n, void *stream, int32_t *out_id, int64_t *out_gain);
+
 /* Free a graph handle (NULL is a no-op).  Waits for the device. */
 void sg_free_graph(sg_graph *g);
 

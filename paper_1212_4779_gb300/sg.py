@@ -28,7 +28,7 @@ _STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ETI
 
 # exported entry points, as declared in include/sg.h
 EXPORTS = ("sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-           "sg_set_snapshot_lists", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+           "sg_set_snapshot_lists", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
            "sg_init_gains", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
 
 
@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
         L.sg_set_engine_limits.argtypes = [i32, i32]
         L.sg_set_landmarks.argtypes = [i32]
         L.sg_set_snapshot_lists.argtypes = [i32]
+        L.sg_argmax_noalloc.argtypes = [P, i64, P, P, P]
         L.sg_load_graph.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_load_graph_coo.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -101,7 +102,7 @@ def lib() -> ctypes.CDLL:
         L.sg_last_error.restype = ctypes.c_char_p
         L.sg_version.restype = ctypes.c_char_p
         for name in ("sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-                     "sg_set_snapshot_lists", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+                     "sg_set_snapshot_lists", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
                      "sg_init_gains", "sg_live_masks", "sg_graph_csr"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -221,6 +222,14 @@ def sg_set_engine_limits(tier1_keys: int = 256, tier2_keys: int = 4096):
 def sg_set_snapshot_lists(enable: int = 1):
     """Per-snapshot live in-lists of heavy rows for the reverse pass (0: off)."""
     _check(lib().sg_set_snapshot_lists(int(enable)))
+
+
+def sg_argmax_noalloc(s, out_id, out_gain, stream=None):
+    """Argmax of a device int64 gain tensor into device int32/int64 outputs
+    without any allocation (for callers that cannot allocate at that
+    point, e.g. while recording a CUDA graph)."""
+    _check(lib().sg_argmax_noalloc(ctypes.c_void_p(_addr(s)[0]), int(s.numel()), _stream_ptr(stream),
+                                   ctypes.c_void_p(_addr(out_id)[0]), ctypes.c_void_p(_addr(out_gain)[0])))
 
 
 def sg_set_landmarks(count: int = 1):
