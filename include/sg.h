@@ -128,11 +128,13 @@ sg_status sg_set_heavy_threshold(int32_t min_degree);
  * Errors: SG_EINVAL if either is < 1. */
 sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys);
 
-/* Landmarks for the initial gains: with 1 (the default), the reach set of
- * the node of largest out-degree is computed once per snapshot, and a
- * source that reaches that node in a snapshot is credited with the whole
- * set instead of traversing it again.  0 disables it.  Results do not
- * depend on it.  Applies to later calls.  Errors: SG_EINVAL unless 0 or 1. */
+/* Landmarks for the initial gains: the reach sets of the `count` nodes of
+ * largest out-degree (default 8, at most 8, degree >= 32) are computed once
+ * per snapshot, together with the size of the union of every subset of
+ * them; a source that reaches some landmarks in a snapshot is credited with
+ * the union of their sets instead of traversing them again.  0 disables
+ * it.  Results do not depend on it.  Applies to later calls.
+ * Errors: SG_EINVAL unless 0 <= count <= 8. */
 sg_status sg_set_landmarks(int32_t count);
 
 /* Per-snapshot live in-arc lists of heavy rows for the reverse (dynamic

@@ -164,8 +164,10 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.anc_list, st);
     dbuf_free(ws.anc_cnt, st);
     dbuf_free(ws.lmk_rx, st);
-    dbuf_free(ws.lmk_cnt, st);
-    dbuf_free(ws.lmk_edges, st);
+    dbuf_free(ws.lmk_U, st);
+    dbuf_free(ws.lmk_H, st);
+    dbuf_free(ws.lmk_E, st);
+    dbuf_free(ws.lmk_HE, st);
     dbuf_free(ws.hcnt_out, st);
     dbuf_free(ws.hnbr_out, st);
     dbuf_free(ws.hmask_out, st);
@@ -279,15 +281,22 @@ sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> 
     const HeavyHost hi = heavy_rows(n, crp, g_heavy_min_deg);
     g->heavy_min_deg = g_heavy_min_deg;
     {
-        int32_t best = -1, bestd = 31;
+        // landmarks: the 8 largest out-degrees (at least 32), lowest id first on ties
+        std::vector<std::pair<int32_t, int32_t>> top;  // (degree, node)
         for (int64_t v = 0; v < n; ++v) {
             const int32_t d = rp[(size_t)v + 1] - rp[(size_t)v];
-            if (d > bestd) {
-                bestd = d;
-                best = (int32_t)v;
+            if (d < 32) continue;
+            if (top.size() < 8 || d > top.back().first) {
+                top.emplace_back(d, (int32_t)v);
+                std::stable_sort(top.begin(), top.end(),
+                                 [](const std::pair<int32_t, int32_t> &x, const std::pair<int32_t, int32_t> &y) {
+                                     return x.first > y.first;
+                                 });
+                if (top.size() > 8) top.pop_back();
             }
         }
-        g->lmk_node = best;
+        g->lmk_count = (int32_t)top.size();
+        for (size_t i = 0; i < top.size(); ++i) g->lmk_nodes[i] = top[i].second;
     }
     g->nh_out = (int32_t)ho.hrow.size();
     g->nh_in = (int32_t)hi.hrow.size();
@@ -426,9 +435,11 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
         SG_TRY(dbuf_alloc(ws.anc, nw, st));
         SG_TRY(dbuf_alloc(ws.anc_list, nw, st));
         SG_TRY(dbuf_alloc(ws.anc_cnt, (size_t)W, st));
-        SG_TRY(dbuf_alloc(ws.lmk_rx, nw, st));
-        SG_TRY(dbuf_alloc(ws.lmk_cnt, (size_t)64 * W, st));
-        SG_TRY(dbuf_alloc(ws.lmk_edges, (size_t)64 * W, st));
+        SG_TRY(dbuf_alloc(ws.lmk_rx, nw * 8, st));
+        SG_TRY(dbuf_alloc(ws.lmk_U, ((size_t)64 * W) << 8, st));
+        SG_TRY(dbuf_alloc(ws.lmk_H, ((size_t)64 * W) << 8, st));
+        SG_TRY(dbuf_alloc(ws.lmk_E, ((size_t)64 * W) << 8, st));
+        SG_TRY(dbuf_alloc(ws.lmk_HE, ((size_t)64 * W) << 8, st));
         SG_TRY(dbuf_alloc(ws.ctl, 1, st));
 
         SG_CUDA_TRY(cudaMemsetAsync(ws.nbits.p, 0, ws.nbits.bytes, st));
@@ -609,8 +620,8 @@ sg_status sg_set_snapshot_lists(int32_t enable)
 
 sg_status sg_set_landmarks(int32_t count)
 {
-    if (count < 0 || count > 1) {
-        set_error("landmark count must be 0 or 1");
+    if (count < 0 || count > 8) {
+        set_error("landmark count must be in [0, 8]");
         return SG_EINVAL;
     }
     g_landmarks = count;

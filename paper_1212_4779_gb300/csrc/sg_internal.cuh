@@ -166,9 +166,9 @@ struct sg_workspace {
     sgi::DBuf<unsigned long long> anc;   // [W][n] ancestors of the round's seed, per snapshot bit
     sgi::DBuf<int32_t> anc_list;         // [W][n] nodes with ancestor bits set
     sgi::DBuf<int32_t> anc_cnt;          // [W]
-    sgi::DBuf<unsigned long long> lmk_rx;    // [W][n] landmark reach bits
-    sgi::DBuf<int32_t> lmk_cnt;              // [64W] |R(G'_r, x)|
-    sgi::DBuf<unsigned long long> lmk_edges; // [64W] out-degree sum over R(G'_r, x)
+    sgi::DBuf<unsigned long long> lmk_rx;    // [K][W][n] landmark reach bits
+    sgi::DBuf<int32_t> lmk_U, lmk_H;         // [64W << K] union sizes / membership histogram
+    sgi::DBuf<unsigned long long> lmk_E, lmk_HE;  // ... their out-degree sums
     sgi::DBuf<unsigned long long> slot_vis, slot_pend;
     sgi::DBuf<int32_t> slot_qa, slot_touched;
     int32_t slot_qmask = 0;              // tier-3 per-slot queue: ring of slot_qmask+1 entries (in slot_qa)
@@ -200,7 +200,8 @@ struct sg_graph {
     sgi::DBuf<int2> cin;
     sgi::DBuf<uint32_t> tmi;
     sgi::DBuf<uint2> fw;      // built on first WIC query
-    int32_t lmk_node = -1;    // landmark: node of largest out-degree (if >= 32)
+    int32_t lmk_nodes[8] = {-1, -1, -1, -1, -1, -1, -1, -1};  // landmarks: largest out-degrees (>= 32)
+    int32_t lmk_count = 0;
     // heavy rows (static)
     int32_t heavy_min_deg = 0;
     int32_t nh_out = 0, nh_in = 0;
@@ -225,7 +226,7 @@ bool heavy_index_enabled(const sg_graph *g, int32_t W);
 extern thread_local int g_launches;
 // keys a tier-1 / tier-2 warp table may hold (clamped to half its slots)
 extern int g_tier_limit[2];
-// landmark nodes used for the initial gains (0 or 1)
+// landmark nodes used for the initial gains (0 .. 8)
 extern int g_landmarks;
 // per-snapshot live in-lists of heavy rows for the reverse update (0 or 1)
 extern int g_snapshot_lists;

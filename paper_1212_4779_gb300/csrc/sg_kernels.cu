@@ -52,6 +52,7 @@ enum { SLICE_SNAP = 0, SLICE_TGT = 1 };
 constexpr int T1_LOGC = 9;   // tier-1 table: 512 slots per warp (shared memory)
 constexpr int WE_THREADS = 128;
 constexpr int HB_ARCS = 1024;  // heavy-index build: arcs per work item
+constexpr int MAX_LMK = 8;     // landmarks for the initial gains
 
 // ------------------------------------------------------------------ coins
 // High 32 bits of splitmix64(base ^ (r << 40)) (Steele, Lea, Flood 2014,
@@ -213,52 +214,83 @@ struct EngineArgs {
     const long long *coff;  // [64W+1] chunk-task offsets
     int32_t *list1, *list2;
     const unsigned long long *anc;  // [W][n] ancestors of v*, per snapshot bit (this round)
-    // landmark x (initial gains): bit b of lmk_rx[w][y] = y in R(G'_{64w+b}, x);
-    // lmk_cnt / lmk_edges: |R(G'_r, x)| and sum of outdeg over it, per snapshot
-    int lmk_x;
+    // landmarks x_0..x_{K-1} (initial gains): bit b of lmk_rx[(i*W + w)*n + y]
+    // = y in R(G'_{64w+b}, x_i); lmk_U / lmk_E [(r << K) + I]: the size of the
+    // union over i in I of R(G'_r, x_i), and the out-degree sum over it
+    int lmk_k;
+    int lmk_x[MAX_LMK];
     const unsigned long long *lmk_rx;
-    const int32_t *lmk_cnt;
-    const unsigned long long *lmk_edges;
+    const int32_t *lmk_U;
+    const unsigned long long *lmk_E;
     long long ntasks;       // TASK_INIT: n * W
     int limit;              // keys a warp table may hold before the task moves up a tier
 };
 
 
-// Initial gains with a landmark x: a task that reaches x in snapshot r gets
-// all of R(G'_r, x) at once (|R(G'_r, x)| added at the end), so bits of
-// such snapshots need not travel inside R(G'_r, x).  Returns the bits of ml
-// that still have to be recorded at y; bits reaching x itself are recorded
-// in *xbits.  Bits that arrive before x does are masked out at the end.
+// Initial gains with landmarks x_i: a task that reaches x_i in snapshot r
+// gets all of R(G'_r, x_i) at once -- at the end it adds the size of the
+// union of the landmark sets it reached in each snapshot -- so bits of such
+// snapshots need not travel inside those sets.  lmk_filter returns the bits
+// of ml that still have to be recorded at y; bits reaching a landmark itself
+// are recorded in xbits[i].  Bits that arrived before the landmark did are
+// masked out at the end (lmk_effective).
+__device__ __forceinline__ const unsigned long long *lmk_bits(const EngineArgs &a, int i, int word)
+{
+    return a.lmk_rx + ((size_t)i * a.co.W + word) * (size_t)a.g.n;
+}
+
 __device__ __forceinline__ uint64_t lmk_filter(const EngineArgs &a, int word, int y, uint64_t ml,
                                                unsigned long long *xbits)
 {
-    if (y == a.lmk_x) {
-        atomicOr(xbits, (unsigned long long)ml);
-        return 0;
+#pragma unroll
+    for (int i = 0; i < MAX_LMK; ++i)
+        if (i < a.lmk_k && y == a.lmk_x[i]) {
+            atomicOr(&xbits[i], (unsigned long long)ml);
+            return 0;
+        }
+    uint64_t drop = 0;
+#pragma unroll
+    for (int i = 0; i < MAX_LMK; ++i) {
+        if (i >= a.lmk_k) break;
+        const uint64_t xb = *(volatile unsigned long long *)&xbits[i];
+        if (xb & ml) drop |= __ldg(lmk_bits(a, i, word) + y) & xb;
     }
-    const uint64_t xb = *(volatile unsigned long long *)xbits;
-    if (xb & ml) ml &= ~(__ldg(a.lmk_rx + (size_t)word * a.g.n + y) & xb);
-    return ml;
+    return ml & ~drop;
 }
 
 // State bits of a finished initial-gain task that count at u: those not
-// accounted for by the landmark.
+// credited through a landmark.
 __device__ __forceinline__ uint64_t lmk_effective(const EngineArgs &a, int word, int u, uint64_t vis,
-                                                  uint64_t xbits)
+                                                  const uint64_t *xb)
 {
-    if (a.lmk_x < 0 || !xbits) return vis;
-    return vis & ~(__ldg(a.lmk_rx + (size_t)word * a.g.n + u) & xbits);
+    uint64_t drop = 0;
+#pragma unroll
+    for (int i = 0; i < MAX_LMK; ++i) {
+        if (i >= a.lmk_k) break;
+        if (xb[i]) drop |= __ldg(lmk_bits(a, i, word) + u) & xb[i];
+    }
+    return vis & ~drop;
 }
 
-// sum over the snapshots in xbits of |R(G'_r, x)| and of its out-degree sum
-__device__ __forceinline__ void lmk_totals(const EngineArgs &a, int word, uint64_t xbits, long long &cnt,
+// For every snapshot some landmark was reached in: the size of the union of
+// the reached landmarks' sets, and its out-degree sum.
+__device__ __forceinline__ void lmk_totals(const EngineArgs &a, int word, const uint64_t *xb, long long &cnt,
                                            unsigned long long &edges)
 {
-    while (xbits) {
-        const int b = __ffsll((long long)xbits) - 1;
-        xbits &= xbits - 1;
-        cnt += a.lmk_cnt[64 * word + b];
-        edges += a.lmk_edges[64 * word + b];
+    uint64_t any = 0;
+#pragma unroll
+    for (int i = 0; i < MAX_LMK; ++i)
+        if (i < a.lmk_k) any |= xb[i];
+    while (any) {
+        const int b = __ffsll((long long)any) - 1;
+        any &= any - 1;
+        int I = 0;
+#pragma unroll
+        for (int i = 0; i < MAX_LMK; ++i)
+            if (i < a.lmk_k) I |= (int)((xb[i] >> b) & 1ull) << i;
+        const long long q = ((long long)(64 * word + b) << a.lmk_k) + I;
+        cnt += a.lmk_U[q];
+        edges += a.lmk_E[q];
     }
 }
 
@@ -269,13 +301,13 @@ struct WTab {
     int *key;
     unsigned short *queue, *touched;
     int *ctr;                  // [0] queue tail, [1] keys, [2] overflow
-    unsigned long long *xbits; // snapshots in which the task reached the landmark
+    unsigned long long *xbits; // [MAX_LMK] snapshots in which the task reached each landmark
 };
 
 template <int LOGC>
 __host__ __device__ constexpr size_t tab_bytes()
 {
-    return (size_t)(1 << LOGC) * 24 + 32;
+    return (size_t)(1 << LOGC) * 24 + 16 + 8 * MAX_LMK;
 }
 
 template <int LOGC>
@@ -347,18 +379,24 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         x0 = (int)(t / co.W);
         word = (int)(t - (long long)x0 * co.W);
         rs = (uint32_t)word * 64u;
-        if (x0 == a.lmk_x) {  // the landmark's own task: its reach is known
+        int own = -1;
+#pragma unroll
+        for (int i = 0; i < MAX_LMK; ++i)
+            if (i < a.lmk_k && x0 == a.lmk_x[i]) own = i;
+        if (own >= 0) {  // a landmark's own task: its reach is known
             if (lane == 0) {
+                uint64_t xb[MAX_LMK] = {};
+                xb[own] = word_mask(word, co.R);
                 long long c = 0;
                 unsigned long long e = 0;
-                lmk_totals(a, word, word_mask(word, co.R), c, e);
+                lmk_totals(a, word, xb, c, e);
                 atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)c);
                 edges_acc += e;
             }
             return false;
         }
+        if (lane < MAX_LMK) T.xbits[lane] = 0;
         if (lane == 0) {
-            *T.xbits = 0;
             const uint64_t M0 = word_mask(word, co.R);
             const uint32_t h = slot_of<LOGC>(x0);
             T.key[h] = x0;
@@ -441,7 +479,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
                 // nodes reaching v* in this snapshot were settled by the ancestor pass
                 if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                     ml = 0;
-                if (TASK == TASK_INIT && ml && a.lmk_x >= 0) ml = lmk_filter(a, word, y, ml, T.xbits);
+                if (TASK == TASK_INIT && ml && a.lmk_k > 0) ml = lmk_filter(a, word, y, ml, T.xbits);
                 if (ml) {
                     const int h = table_slot<LOGC>(T, y, LIMIT);
                     if (h >= 0) {
@@ -464,7 +502,9 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
     const int ovf = *(volatile int *)&T.ctr[2];
     const int nt = *(volatile int *)&T.ctr[1];
     if (lane == 0) wk += (unsigned long long)nt;  // lane 0: keys, lane 1: elements
-    const uint64_t xb = TASK == TASK_INIT ? *(volatile unsigned long long *)T.xbits : 0ull;
+    uint64_t xb[MAX_LMK];
+#pragma unroll
+    for (int i = 0; i < MAX_LMK; ++i) xb[i] = (TASK == TASK_INIT && i < a.lmk_k) ? *(volatile unsigned long long *)&T.xbits[i] : 0ull;
     long long cnt = 0;
     unsigned long long redges = 0;
     for (int i = lane; i < nt; i += 32) {
@@ -671,7 +711,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                 atomicOr(&w.pend[x0], (unsigned long long)M);
                 w.qa[0] = x0;
                 S.qlen = 1;
-                if (atomicOr(&w.nbits[x0], (unsigned long long)M) == 0) w.du_x[atomicAdd(w.ndu, 1)] = x0;
+                if (w.du_x && atomicOr(&w.nbits[x0], (unsigned long long)M) == 0) w.du_x[atomicAdd(w.ndu, 1)] = x0;
             }
         } else if (M) {
             w.vis[x0] |= M;
@@ -733,7 +773,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                             if (TASK == TASK_INIT) cnt += __popcll(nw);
                             if (TASK != TASK_FWD && TASK != TASK_LMK && old == 0)
                                 w.touched[atomicAdd(&S.ntouch, 1)] = y;
-                            if (TASK == TASK_FWD || TASK == TASK_LMK) {
+                            if ((TASK == TASK_FWD || TASK == TASK_LMK) && w.du_x) {
                                 const uint64_t ob = atomicOr(&w.nbits[y], (unsigned long long)nw);
                                 if (ob == 0) w.du_x[atomicAdd(w.ndu, 1)] = y;
                             }
@@ -823,7 +863,7 @@ enum { TAB_HASH = 0, TAB_DENSE = 1 };
 
 struct CoopCtl {
     int head, tail, busy, nkeys, overflow, err;
-    unsigned long long xbits;  // initial gains: snapshots in which the task reached the landmark
+    unsigned long long xbits[MAX_LMK];  // initial gains: snapshots in which the task reached each landmark
 };
 
 template <int TAB>
@@ -1052,7 +1092,7 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                 uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y);
                 if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                     ml = 0;
-                if (TASK == TASK_INIT && ml && a.lmk_x >= 0) ml = lmk_filter(a, word, y, ml, &c.xbits);
+                if (TASK == TASK_INIT && ml && a.lmk_k > 0) ml = lmk_filter(a, word, y, ml, c.xbits);
                 if (ml) {
                     const int idx = T.slot(y, limit, c);
                     if (idx >= 0) {
@@ -1129,7 +1169,7 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
             c.nkeys = 0;
             c.overflow = 0;
             c.err = 0;
-            c.xbits = 0;
+            for (int i = 0; i < MAX_LMK; ++i) c.xbits[i] = 0;
         }
         __syncthreads();
         if (TASK == TASK_INIT) {
@@ -1151,7 +1191,9 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
         __syncthreads();
         const int ovf = c.overflow | c.err;
         const int nt = c.nkeys;
-        const uint64_t xb = TASK == TASK_INIT ? c.xbits : 0ull;
+        uint64_t xb[MAX_LMK];
+#pragma unroll
+        for (int i = 0; i < MAX_LMK; ++i) xb[i] = (TASK == TASK_INIT && i < a.lmk_k) ? c.xbits[i] : 0ull;
         long long cnt = 0;
         unsigned long long redges = 0;
         for (int i = tid; i < nt; i += CO_T) {
@@ -1407,56 +1449,106 @@ __global__ void __launch_bounds__(BT) fwd_post_kernel(EngineArgs a, FwdArgs f)
 }
 
 
-// Landmark reach sets (initial gains): block `word` walks from x over the
-// live arcs of its 64 snapshots into lmk_rx (zero on entry), then records
-// per snapshot |R(G'_r, x)| and the out-degree sum over it.
+// Landmark reach sets (initial gains).  landmark_walk_kernel: block
+// (word, group) walks from landmark i over the live arcs of the snapshots it
+// owns into that landmark's reach bits (zero on entry).
 struct LmkArgs {
-    unsigned long long *rx, *pendf, *nbits, *edges;
-    int32_t *fq_a, *fq_b, *list, *cnt, *ndu;
+    unsigned long long *rx, *pendf, *E, *HE;
+    int32_t *fq_a, *fq_b, *U, *H;
 };
 
 template <int MODEL>
-__global__ void __launch_bounds__(BT) landmark_kernel(EngineArgs a, LmkArgs l)
+__global__ void __launch_bounds__(BT) landmark_walk_kernel(EngineArgs a, LmkArgs l, int i)
 {
     __shared__ CtaShared S;
-    __shared__ unsigned long long esum[64];
-    const int word = blockIdx.x;
-    const int tid = threadIdx.x;
-    const size_t so = (size_t)word * (size_t)a.g.n;
+    const int n = a.g.n;
+    const int word = blockIdx.x / FWD_GROUPS;
+    const int grp = blockIdx.x - word * FWD_GROUPS;
+    constexpr int GB = 64 / FWD_GROUPS;
+    const size_t qo = (size_t)blockIdx.x * (size_t)n;
     CtaState w;
-    w.vis = l.rx + so;
-    w.pend = l.pendf + so;
-    w.qa = l.fq_a + so;
-    w.qb = l.fq_b + so;
+    w.vis = l.rx + ((size_t)i * a.co.W + word) * (size_t)n;
+    w.pend = l.pendf + (size_t)word * (size_t)n;
+    w.qa = l.fq_a + qo;
+    w.qb = l.fq_b + qo;
     w.touched = nullptr;
-    w.nbits = l.nbits + so;
-    w.du_x = l.list + so;
-    w.ndu = l.ndu + word;
-    w.gm = ~0ull;
-    cta_bfs<DIR_FWD, MODEL, TASK_LMK>(a, w, a.lmk_x, word_mask(word, a.co.R), word, (uint32_t)word * 64u, nullptr, 0,
-                                      nullptr, S);
-    if (tid < 64) {
-        S.bcnt[tid] = 0;
-        esum[tid] = 0;
-    }
-    __syncthreads();
-    const int nd = *(volatile int32_t *)w.ndu;
-    for (int i = tid; i < nd; i += BT) {
-        const int y = w.du_x[i];
-        w.nbits[y] = 0;
-        uint64_t M = w.vis[y];
+    w.nbits = nullptr;
+    w.du_x = nullptr;
+    w.ndu = nullptr;
+    w.gm = (GB == 64 ? ~0ull : ((1ull << GB) - 1ull)) << (grp * GB);
+    cta_bfs<DIR_FWD, MODEL, TASK_LMK>(a, w, a.lmk_x[i], word_mask(word, a.co.R), word, (uint32_t)word * 64u, nullptr,
+                                      0, nullptr, S);
+}
+
+// Histogram, per snapshot r, of the landmark-membership mask
+// m_r(y) = {i : y in R(G'_r, x_i)} over the nodes with m_r(y) nonempty
+// (count and out-degree sum), in H / HE [(r << K) + m].
+__global__ void __launch_bounds__(256) landmark_hist_kernel(EngineArgs a, LmkArgs l)
+{
+    const int n = a.g.n, K = a.lmk_k, W = a.co.W;
+    const long long total = (long long)W * n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int word = (int)(t / n);
+        const int y = (int)(t - (long long)word * n);
+        uint64_t rx[MAX_LMK];
+        uint64_t any = 0;
+#pragma unroll
+        for (int i = 0; i < MAX_LMK; ++i) {
+            rx[i] = i < K ? l.rx[((size_t)i * W + word) * (size_t)n + y] : 0ull;
+            any |= rx[i];
+        }
+        if (!any) continue;
         const unsigned long long d = (unsigned long long)(__ldg(a.g.rp + y + 1) - __ldg(a.g.rp + y));
-        while (M) {
-            const int b = __ffsll((long long)M) - 1;
-            M &= M - 1;
-            atomicAdd(&S.bcnt[b], 1);
-            atomicAdd(&esum[b], d);
+        while (any) {
+            const int b = __ffsll((long long)any) - 1;
+            any &= any - 1;
+            int m = 0;
+#pragma unroll
+            for (int i = 0; i < MAX_LMK; ++i) m |= (int)((rx[i] >> b) & 1ull) << i;
+            const long long q = ((long long)(64 * word + b) << K) + m;
+            atomicAdd(&l.H[q], 1);
+            atomicAdd(&l.HE[q], d);
         }
     }
+}
+
+// Per snapshot (one block each, 2^K threads): subset sums over the
+// histogram, Z[J] = sum over m within J of H[m]; the union of the sets of
+// the landmarks in I holds every node whose mask meets I, i.e.
+// U[I] = Z[all] - Z[all minus I].
+__global__ void landmark_union_kernel(int K, LmkArgs l)
+{
+    __shared__ long long zc[1 << MAX_LMK];
+    __shared__ unsigned long long ze[1 << MAX_LMK];
+    const int r = blockIdx.x;
+    const int S = 1 << K;
+    const int J = threadIdx.x;
+    const long long base = (long long)r << K;
+    if (J < S) {
+        zc[J] = l.H[base + J];
+        ze[J] = l.HE[base + J];
+    }
     __syncthreads();
-    if (tid < 64) {
-        l.cnt[64 * word + tid] = S.bcnt[tid];
-        l.edges[64 * word + tid] = esum[tid];
+    for (int i = 0; i < K; ++i) {
+        long long c = 0;
+        unsigned long long e = 0;
+        const bool has = J < S && ((J >> i) & 1);
+        if (has) {
+            c = zc[J ^ (1 << i)];
+            e = ze[J ^ (1 << i)];
+        }
+        __syncthreads();
+        if (has) {
+            zc[J] += c;
+            ze[J] += e;
+        }
+        __syncthreads();
+    }
+    if (J < S) {
+        const int all = S - 1;
+        l.U[base + J] = (int32_t)(zc[all] - zc[all ^ J]);
+        l.E[base + J] = ze[all] - ze[all ^ J];
     }
 }
 
@@ -1750,10 +1842,11 @@ EngineArgs engine_args(sg_graph *g, const Coins &co, int heavy_on)
     a.list1 = ws.list1.p;
     a.list2 = ws.list2.p;
     a.anc = ws.anc.p;
-    a.lmk_x = -1;
+    a.lmk_k = 0;
+    for (int i = 0; i < MAX_LMK; ++i) a.lmk_x[i] = -1;
     a.lmk_rx = ws.lmk_rx.p;
-    a.lmk_cnt = ws.lmk_cnt.p;
-    a.lmk_edges = ws.lmk_edges.p;
+    a.lmk_U = ws.lmk_U.p;
+    a.lmk_E = ws.lmk_E.p;
     a.ntasks = 0;
     a.limit = 1;
     return a;
@@ -1827,24 +1920,35 @@ sg_status init_gains_t(sg_graph *g, const Coins &co, int heavy_on, cudaStream_t 
 {
     EngineArgs a = engine_args(g, co, heavy_on);
     a.ntasks = (long long)g->n * co.W;
-    if (g->lmk_node >= 0 && g_landmarks > 0) {
+    const int K = std::min(std::min(g_landmarks, g->lmk_count), MAX_LMK);
+    if (K > 0) {
         sg_workspace &ws = g->ws;
-        a.lmk_x = g->lmk_node;
-        SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_rx.p, 0, (size_t)g->n * co.W * 8, st));
+        a.lmk_k = K;
+        for (int i = 0; i < K; ++i) a.lmk_x[i] = g->lmk_nodes[i];
+        const size_t nw = (size_t)g->n * co.W;
+        SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_rx.p, 0, (size_t)K * nw * 8, st));
         LmkArgs l;
         l.rx = ws.lmk_rx.p;
         l.pendf = ws.pendf.p;
-        l.nbits = ws.nbits.p;
-        l.edges = ws.lmk_edges.p;
         l.fq_a = ws.fq_a.p;
         l.fq_b = ws.fq_b.p;
-        l.list = ws.du_x.p;
-        l.cnt = ws.lmk_cnt.p;
-        l.ndu = ws.du_cnt.p;
-        SG_CUDA_TRY(cudaMemsetAsync(ws.du_cnt.p, 0, (size_t)co.W * 4, st));
-        landmark_kernel<MODEL><<<co.W, BT, 0, st>>>(a, l);
+        l.U = ws.lmk_U.p;
+        l.E = ws.lmk_E.p;
+        l.H = ws.lmk_H.p;
+        l.HE = ws.lmk_HE.p;
+        for (int i = 0; i < K; ++i) {
+            landmark_walk_kernel<MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, l, i);
+            SG_CUDA_TRY(cudaGetLastError());
+        }
+        const size_t nq = ((size_t)64 * co.W) << K;
+        SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_H.p, 0, nq * 4, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_HE.p, 0, nq * 8, st));
+        const int blocks = (int)std::min<long long>(((long long)nw + 255) / 256, (long long)g->num_sms * 16);
+        landmark_hist_kernel<<<blocks, 256, 0, st>>>(a, l);
         SG_CUDA_TRY(cudaGetLastError());
-        ++g_launches;
+        landmark_union_kernel<<<64 * co.W, 1 << MAX_LMK, 0, st>>>(K, l);
+        SG_CUDA_TRY(cudaGetLastError());
+        g_launches += K + 2;
     }
     return launch_tiers<DIR_FWD, MODEL, TASK_INIT>(g, a, st, after_t1);
 }
@@ -1888,7 +1992,7 @@ sg_status round_t(sg_graph *g, const Coins &co, int heavy_on, int32_t round, cud
 
 thread_local int g_launches = 0;
 int g_tier_limit[2] = {(1 << T1_LOGC) / 2, (1 << CO_LOGC) / 2};
-int g_landmarks = 1;
+int g_landmarks = 8;
 
 sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t st)
 {

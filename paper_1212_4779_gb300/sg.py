@@ -232,8 +232,8 @@ def sg_argmax_noalloc(s, out_id, out_gain, stream=None):
                                    ctypes.c_void_p(_addr(out_id)[0]), ctypes.c_void_p(_addr(out_gain)[0])))
 
 
-def sg_set_landmarks(count: int = 1):
-    """Landmark reach sets for the initial gains (0: off, 1: on)."""
+def sg_set_landmarks(count: int = 8):
+    """Landmark reach sets for the initial gains (0: off, up to 8)."""
     _check(lib().sg_set_landmarks(int(count)))
 
 

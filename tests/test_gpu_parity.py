@@ -119,7 +119,7 @@ def limits(sg):
     yield sg.sg_set_engine_limits
     sg.sg_set_engine_limits(256, 4096)
     sg.sg_set_heavy_threshold(64)
-    sg.sg_set_landmarks(1)
+    sg.sg_set_landmarks(8)
     sg.sg_set_snapshot_lists(1)
 
 
@@ -143,7 +143,7 @@ def test_snapshot_lists_give_identical_results(sg, limits, name, lists):
         assert got == [int(x) for x in ref["counters"]]
 
 
-@pytest.mark.parametrize("lmk", [0, 1])
+@pytest.mark.parametrize("lmk", [0, 1, 3, 8])
 @pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01", "er2k_uic0.1"])
 def test_landmark_gives_identical_results(sg, limits, name, lmk):
     """Crediting the landmark's reach set is exact: same initial gains, seeds,
@@ -219,7 +219,7 @@ def test_giant_component_reaches_tier3_and_agrees(sg, limits):
     d = np.concatenate([d, p_ + 1, p_])
     g, o = _both(sg, n, s, d, "uic", 1.0)
     ref = o.select(2, 3, 5, mode=oracle.DU)
-    for lmk in (0, 1):
+    for lmk in (0, 1, 8):
         sg.sg_set_landmarks(lmk)
         res = g.select(2, 3, "uic", 1.0, 5, stats=True)
         if lmk == 0:
