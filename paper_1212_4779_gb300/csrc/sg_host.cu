@@ -183,7 +183,6 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     ws.slists_on = 0;
     ws.hw_cap = 0;
     dbuf_free(ws.slot_vis, st);
-    dbuf_free(ws.slot_pend, st);
     dbuf_free(ws.slot_qa, st);
     dbuf_free(ws.slot_touched, st);
     dbuf_free(ws.ctl, st);
@@ -451,12 +450,10 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
         const size_t budget = (size_t)4 << 30;
         int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms * 2, budget / per_slot));
         const size_t ns = (size_t)slots * (size_t)n;
-        SG_TRY(dbuf_alloc(ws.slot_vis, ns, st));
-        SG_TRY(dbuf_alloc(ws.slot_pend, ns, st));
+        SG_TRY(dbuf_alloc(ws.slot_vis, 2 * ns, st));  // per node: visited and pending words side by side
         SG_TRY(dbuf_alloc(ws.slot_qa, (size_t)slots * (size_t)qcap, st));
         SG_TRY(dbuf_alloc(ws.slot_touched, ns, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.slot_vis.p, 0, ws.slot_vis.bytes, st));
-        SG_CUDA_TRY(cudaMemsetAsync(ws.slot_pend.p, 0, ws.slot_pend.bytes, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.slot_qa.p, 0xff, ws.slot_qa.bytes, st));
         ws.slot_qmask = qcap - 1;
         ws.am_blocks = g->num_sms * 2;

@@ -169,7 +169,7 @@ struct sg_workspace {
     sgi::DBuf<unsigned long long> lmk_rx;    // [K][W][n] landmark reach bits
     sgi::DBuf<int32_t> lmk_U, lmk_H;         // [64W << K] union sizes / membership histogram
     sgi::DBuf<unsigned long long> lmk_E, lmk_HE;  // ... their out-degree sums
-    sgi::DBuf<unsigned long long> slot_vis, slot_pend;
+    sgi::DBuf<unsigned long long> slot_vis;  // tier-3 slots: [slot][n][2] visited / pending words
     sgi::DBuf<int32_t> slot_qa, slot_touched;
     int32_t slot_qmask = 0;              // tier-3 per-slot queue: ring of slot_qmask+1 entries (in slot_qa)
     sgi::DBuf<sgi::Ctl> ctl;

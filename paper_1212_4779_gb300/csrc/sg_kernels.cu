@@ -854,12 +854,22 @@ struct SlotArgs {
 //   TAB_DENSE  dense per-block arrays in global memory indexed by node
 //              (tier 3; never overflows)
 
-constexpr int CO_T = 512;
-constexpr int CO_W = CO_T / 32;
+// block size: the shared-memory tier runs one 1024-thread block per SM (its
+// table fills shared memory); the dense tier runs two 512-thread blocks
+template <int TAB>
+struct CoopShape;
 constexpr int CO_LOGC = 13;
 constexpr long long CO_SPIN = 1LL << 22;
 constexpr unsigned short QE16 = 0xFFFF;
 enum { TAB_HASH = 0, TAB_DENSE = 1 };
+template <>
+struct CoopShape<TAB_HASH> {
+    static constexpr int T = 1024, MINB = 1;
+};
+template <>
+struct CoopShape<TAB_DENSE> {
+    static constexpr int T = 512, MINB = 2;
+};
 
 struct CoopCtl {
     int head, tail, busy, nkeys, overflow, err;
@@ -877,6 +887,8 @@ struct CoopTab<TAB_HASH> {
     unsigned short *queue, *touched;
 
     __device__ __forceinline__ static size_t bytes() { return (size_t)C * 24; }
+    __device__ __forceinline__ unsigned long long &visr(int idx) { return vis[idx]; }
+    __device__ __forceinline__ unsigned long long &pendr(int idx) { return pend[idx]; }
     __device__ __forceinline__ void bind(unsigned char *p)
     {
         vis = reinterpret_cast<unsigned long long *>(p);
@@ -942,10 +954,13 @@ struct CoopTab<TAB_HASH> {
 
 template <>
 struct CoopTab<TAB_DENSE> {
-    unsigned long long *vis, *pend;
+    // vis(y) and pend(y) share one 16-byte record: st[2y], st[2y + 1]
+    unsigned long long *st;
     int *queue, *touched;
     int qmask;
 
+    __device__ __forceinline__ unsigned long long &visr(int idx) { return st[2 * (size_t)idx]; }
+    __device__ __forceinline__ unsigned long long &pendr(int idx) { return st[2 * (size_t)idx + 1]; }
     __device__ __forceinline__ int slot(int y, int, CoopCtl &) { return y; }
     __device__ __forceinline__ void note_new(int y, CoopCtl &c) { touched[atomicAdd(&c.nkeys, 1)] = y; }
     __device__ __forceinline__ int node(int idx) const { return idx; }
@@ -966,8 +981,8 @@ struct CoopTab<TAB_DENSE> {
     }
     __device__ __forceinline__ void clear_slot(int idx)
     {
-        vis[idx] = 0;
-        pend[idx] = 0;
+        visr(idx) = 0;
+        pendr(idx) = 0;
     }
     __device__ __forceinline__ int touched_at(int i) const { return touched[i]; }
     __device__ __forceinline__ void clear_queue(int head, int tail)
@@ -983,8 +998,8 @@ __device__ __forceinline__ void coop_seed(CoopTab<TAB> &T, CoopCtl &c, int y, ui
     const int idx = T.slot(y, limit, c);
     if (idx < 0) return;
     if (TAB == TAB_DENSE) T.note_new(y, c);
-    T.vis[idx] = M;
-    T.pend[idx] = M;
+    T.visr(idx) = M;
+    T.pendr(idx) = M;
     T.put(atomicAdd(&c.tail, 1), idx);
 }
 
@@ -1055,7 +1070,7 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
         if (lane < nb) {
             const int idx = T.take(qb + lane, c);
             if (idx >= 0) {
-                F = atomicExch(&T.pend[idx], 0ull);
+                F = atomicExch(&T.pendr(idx), 0ull);
                 const Row rr = row_ref<DIR, MODEL, SLICE>(g, co, T.node(idx), word, rs);
                 base = rr.base;
                 vdeg = F ? rr.vdeg : 0;
@@ -1096,11 +1111,11 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                 if (ml) {
                     const int idx = T.slot(y, limit, c);
                     if (idx >= 0) {
-                        const uint64_t old = atomicOr(&T.vis[idx], (unsigned long long)ml);
+                        const uint64_t old = atomicOr(&T.visr(idx), (unsigned long long)ml);
                         const uint64_t nw = ml & ~old;
                         if (nw) {
                             if (TAB == TAB_DENSE && old == 0) T.note_new(y, c);
-                            const uint64_t oldp = atomicOr(&T.pend[idx], (unsigned long long)nw);
+                            const uint64_t oldp = atomicOr(&T.pendr(idx), (unsigned long long)nw);
                             if (oldp == 0) T.put(atomicAdd(&c.tail, 1), idx);
                         }
                     }
@@ -1118,8 +1133,10 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
 
 // Tier 2 (TAB_HASH, tasks of list1) and tier 3 (TAB_DENSE, tasks of list2).
 template <int TAB, int DIR, int MODEL, int TASK>
-__global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, SlotArgs sl)
+__global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_engine_kernel(EngineArgs a, SlotArgs sl)
 {
+    constexpr int CO_T = CoopShape<TAB>::T;
+    constexpr int CO_W = CO_T / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ CoopCtl c;
     __shared__ long long sh_t;
@@ -1143,8 +1160,7 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
         limit = a.limit;
     } else {
         const size_t so = (size_t)blockIdx.x * (size_t)g.n;
-        T.vis = sl.vis + so;
-        T.pend = sl.pend + so;
+        T.st = sl.vis + 2 * so;
         T.touched = sl.touched + so;
         T.queue = sl.qa + (size_t)blockIdx.x * (size_t)(sl.qmask + 1);
         T.qmask = sl.qmask;
@@ -1201,14 +1217,14 @@ __global__ void __launch_bounds__(CO_T, 1) coop_engine_kernel(EngineArgs a, Slot
             if (!ovf) {
                 const int u = T.node(idx);
                 if (TASK == TASK_INIT) {
-                    const uint64_t v = T.vis[idx];
+                    const uint64_t v = T.visr(idx);
                     const uint64_t ve = lmk_effective(a, word, u, v, xb);
                     cnt += __popcll(ve);
                     if (ve != v)
                         tedges -= (unsigned long long)__popcll(v & ~ve) *
                                   (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
                 } else {
-                    const int cc = __popcll(T.vis[idx]);
+                    const int cc = __popcll(T.visr(idx));
                     atomicAdd((unsigned long long *)&a.s[u], (unsigned long long)(-(long long)cc));
                     redges += (unsigned long long)cc * (unsigned long long)(__ldg(g.crp + u + 1) - __ldg(g.crp + u));
                 }
@@ -1857,7 +1873,7 @@ SlotArgs slot_args(sg_graph *g)
     sg_workspace &ws = g->ws;
     SlotArgs s;
     s.vis = ws.slot_vis.p;
-    s.pend = ws.slot_pend.p;
+    s.pend = nullptr;
     s.qa = ws.slot_qa.p;
     s.touched = ws.slot_touched.p;
     s.qmask = ws.slot_qmask;
@@ -1887,11 +1903,11 @@ sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, cudaE
         auto kern = coop_engine_kernel<TAB_HASH, DIR, MODEL, TASK>;
         const size_t smem = coop_hash_smem();
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<g->num_sms, CO_T, smem, st>>>(a, slot_args(g));
+        kern<<<g->num_sms, CoopShape<TAB_HASH>::T, smem, st>>>(a, slot_args(g));
         SG_CUDA_TRY(cudaGetLastError());
         ++g_launches;
     }
-    coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK><<<g->ws.nslots, CO_T, 0, st>>>(a, slot_args(g));
+    coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK><<<g->ws.nslots, CoopShape<TAB_DENSE>::T, 0, st>>>(a, slot_args(g));
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
     return SG_OK;
