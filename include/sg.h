@@ -73,7 +73,7 @@ typedef struct {
     uint64_t rev_tier3_tasks;
     uint64_t rev_tasks;         /* reverse tasks (one snapshot, <= 64 targets), all rounds */
     uint64_t du_entries;        /* (node, 64-snapshot word) pairs newly covered, all rounds */
-    float ms_index;             /* device time building the heavy-row live index */
+    float ms_index;             /* device time building the heavy-row live index and lists */
     float ms_init;              /* device time of the initial gains (index included) */
     float ms_init_tier1;        /* device time of the initial-gain tier-1 launch */
     float ms_rounds;            /* device time of the k selection rounds */
@@ -85,6 +85,10 @@ typedef struct {
     int32_t reserved;
     uint64_t work_keys[2][3];   /* [initial, reverse][tier 1..3]: nodes held in task tables */
     uint64_t work_elems[2][3];  /* [initial, reverse][tier 1..3]: arcs / index entries expanded */
+    float ms_landmarks;         /* device time of the landmark reach sets */
+    float ms_init_tier2;        /* device time of the initial-gain tier-2 launch */
+    float ms_init_tier3;        /* device time of the initial-gain tier-3 launch */
+    int32_t reserved2;
 } sg_stats;
 
 /* Opaque graph handle; owns its device memory until sg_free_graph. */

@@ -795,7 +795,12 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
             for (auto e : v) cudaEventDestroy(e);
         }
     } guard{ev};
-    cudaEvent_t e_start = mark(), e_index = mark(), e_t1 = mark(), e_init = mark(), e_end = mark();
+    cudaEvent_t e_start = mark(), e_index = mark(), e_init = mark(), e_end = mark();
+    TierEvents tev;
+    tev.start = mark();
+    tev.t1 = mark();
+    tev.t2 = mark();
+    tev.t3 = mark();
     std::vector<cudaEvent_t> e_round(stats ? (size_t)k + 1 : 0), e_fwd(stats ? (size_t)k : 0);
     if (stats) {
         for (auto &e : e_round) e = mark();
@@ -810,7 +815,7 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     if (heavy_on) SG_TRY(run_heavy_index(g, co, model, st));
     if (ws.slists_on) SG_TRY(run_snapshot_lists(g, co, st));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_index, st));
-    SG_TRY(run_init_gains(g, co, model, heavy_on, st, e_t1));
+    SG_TRY(run_init_gains(g, co, model, heavy_on, st, stats ? &tev : nullptr));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_init, st));
     for (int32_t i = 0; i < k; ++i) {
         if (stats) SG_CUDA_TRY(cudaEventRecord(e_round[(size_t)i], st));
@@ -843,7 +848,10 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
         memcpy(stats->work_elems, h.work_elems, sizeof(h.work_elems));
         cudaEventElapsedTime(&stats->ms_index, e_start, e_index);
         cudaEventElapsedTime(&stats->ms_init, e_start, e_init);
-        cudaEventElapsedTime(&stats->ms_init_tier1, e_index, e_t1);
+        cudaEventElapsedTime(&stats->ms_landmarks, e_index, tev.start);
+        cudaEventElapsedTime(&stats->ms_init_tier1, tev.start, tev.t1);
+        cudaEventElapsedTime(&stats->ms_init_tier2, tev.t1, tev.t2);
+        cudaEventElapsedTime(&stats->ms_init_tier3, tev.t2, tev.t3);
         cudaEventElapsedTime(&stats->ms_rounds, e_init, e_end);
         cudaEventElapsedTime(&stats->ms_total, e_start, e_end);
         float fsum = 0.f;

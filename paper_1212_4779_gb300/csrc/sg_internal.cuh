@@ -235,8 +235,12 @@ extern int g_snapshot_lists;
 sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t st);
 sg_status run_snapshot_lists(sg_graph *g, const Coins &co, cudaStream_t st);
 sg_status ensure_snapshot_lists(sg_graph *g, const Coins &co, double p_uic, int model, cudaStream_t st);
+// events recorded around the initial-gain tier launches (any may be null)
+struct TierEvents {
+    cudaEvent_t start = nullptr, t1 = nullptr, t2 = nullptr, t3 = nullptr;
+};
 sg_status run_init_gains(sg_graph *g, const Coins &co, int model, int heavy_on, cudaStream_t st,
-                         cudaEvent_t after_t1 = nullptr);
+                         const TierEvents *ev = nullptr);
 sg_status run_round(sg_graph *g, const Coins &co, int model, int heavy_on, int32_t round, cudaStream_t st,
                     cudaEvent_t after_fwd = nullptr);
 sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st);

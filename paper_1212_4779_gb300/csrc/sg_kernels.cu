@@ -1882,8 +1882,9 @@ SlotArgs slot_args(sg_graph *g)
 
 // tier 1 -> tier 2 -> tier 3 for one task family
 template <int DIR, int MODEL, int TASK>
-sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, cudaEvent_t after_t1)
+sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, const TierEvents *ev)
 {
+    if (ev && ev->start) SG_CUDA_TRY(cudaEventRecord(ev->start, st));
     EngineArgs a = a0;
     {
         a.limit = std::max(1, std::min(g_tier_limit[0], (1 << T1_LOGC) / 2));
@@ -1897,7 +1898,7 @@ sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, cudaE
         SG_CUDA_TRY(cudaGetLastError());
         ++g_launches;
     }
-    if (after_t1) SG_CUDA_TRY(cudaEventRecord(after_t1, st));
+    if (ev && ev->t1) SG_CUDA_TRY(cudaEventRecord(ev->t1, st));
     {
         a.limit = std::max(1, std::min(g_tier_limit[1], (1 << CO_LOGC) / 2));
         auto kern = coop_engine_kernel<TAB_HASH, DIR, MODEL, TASK>;
@@ -1907,9 +1908,11 @@ sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, cudaE
         SG_CUDA_TRY(cudaGetLastError());
         ++g_launches;
     }
+    if (ev && ev->t2) SG_CUDA_TRY(cudaEventRecord(ev->t2, st));
     coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK><<<g->ws.nslots, CoopShape<TAB_DENSE>::T, 0, st>>>(a, slot_args(g));
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
+    if (ev && ev->t3) SG_CUDA_TRY(cudaEventRecord(ev->t3, st));
     return SG_OK;
 }
 
@@ -1932,7 +1935,7 @@ sg_status launch_index(sg_graph *g, const Coins &co, cudaStream_t st)
 }
 
 template <int MODEL>
-sg_status init_gains_t(sg_graph *g, const Coins &co, int heavy_on, cudaStream_t st, cudaEvent_t after_t1)
+sg_status init_gains_t(sg_graph *g, const Coins &co, int heavy_on, cudaStream_t st, const TierEvents *ev)
 {
     EngineArgs a = engine_args(g, co, heavy_on);
     a.ntasks = (long long)g->n * co.W;
@@ -1966,7 +1969,7 @@ sg_status init_gains_t(sg_graph *g, const Coins &co, int heavy_on, cudaStream_t 
         SG_CUDA_TRY(cudaGetLastError());
         g_launches += K + 2;
     }
-    return launch_tiers<DIR_FWD, MODEL, TASK_INIT>(g, a, st, after_t1);
+    return launch_tiers<DIR_FWD, MODEL, TASK_INIT>(g, a, st, ev);
 }
 
 template <int MODEL>
@@ -2051,10 +2054,10 @@ sg_status run_snapshot_lists(sg_graph *g, const Coins &co, cudaStream_t st)
 }
 
 sg_status run_init_gains(sg_graph *g, const Coins &co, int model, int heavy_on, cudaStream_t st,
-                         cudaEvent_t after_t1)
+                         const TierEvents *ev)
 {
-    return model == MODEL_WIC ? init_gains_t<MODEL_WIC>(g, co, heavy_on, st, after_t1)
-                              : init_gains_t<MODEL_UIC>(g, co, heavy_on, st, after_t1);
+    return model == MODEL_WIC ? init_gains_t<MODEL_WIC>(g, co, heavy_on, st, ev)
+                              : init_gains_t<MODEL_UIC>(g, co, heavy_on, st, ev);
 }
 
 sg_status run_round(sg_graph *g, const Coins &co, int model, int heavy_on, int32_t round, cudaStream_t st,

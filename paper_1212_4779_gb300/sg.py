@@ -51,7 +51,9 @@ class sg_stats(ctypes.Structure):
                 ("ms_rounds", ctypes.c_float), ("ms_fwd", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("status_flags", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("heavy_index", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("work_keys", (ctypes.c_uint64 * 3) * 2), ("work_elems", (ctypes.c_uint64 * 3) * 2)]
+                ("work_keys", (ctypes.c_uint64 * 3) * 2), ("work_elems", (ctypes.c_uint64 * 3) * 2),
+                ("ms_landmarks", ctypes.c_float), ("ms_init_tier2", ctypes.c_float),
+                ("ms_init_tier3", ctypes.c_float), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self):
         out = {}
