@@ -177,6 +177,91 @@ sg_status sg_graph_info(const sg_graph *g, int64_t *n, int64_t *m_canonical);
 sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
                     int32_t *out_seeds, int64_t *out_gains, sg_stats *stats);
 
+/* Per-query device state (gains, coverage bitsets, task lists, caches).
+ * sg_select uses one owned by the graph; several queries can run on one
+ * graph at the same time only with workspaces of their own.
+ * sg_workspace_create sizes one for queries on g with R <= R_max and
+ * k <= k_max (device memory taken through the allocator hooks, cleared;
+ * synchronises `stream`).  sg_workspace_bytes reports that size without
+ * allocating.  A workspace belongs to the graph it was created for until
+ * sg_workspace_free (waits for the device). */
+typedef struct sg_workspace sg_workspace;
+sg_status sg_workspace_create(const sg_graph *g, int32_t R_max, int32_t k_max, void *stream,
+                              sg_workspace **out);
+sg_status sg_workspace_bytes(const sg_graph *g, int32_t R_max, int32_t k_max, size_t *bytes);
+void sg_workspace_free(sg_workspace *ws);
+
+/* sg_select with an explicit workspace (same arguments and results).
+ * Calls with different workspaces may run concurrently on different
+ * streams; one workspace serves one call at a time. */
+sg_status sg_select_ws(sg_graph *g, sg_workspace *ws, int32_t R, int32_t k, sg_cascade c, uint64_t seed,
+                       void *stream, int32_t *out_seeds, int64_t *out_gains, sg_stats *stats);
+
+/* One query of a batch. */
+typedef struct {
+    sg_graph *graph;
+    sg_workspace *ws;     /* NULL: the graph's own (then one query per graph in a batch) */
+    int32_t R;
+    int32_t k;
+    sg_cascade cascade;
+    uint64_t seed;
+    int32_t *out_seeds;   /* int32[k], device or pinned host memory */
+    int64_t *out_gains;   /* int64[k], device or pinned host memory */
+    sg_status status;     /* written by the call */
+} sg_query;
+
+/* Run nq independent queries (different graphs, R, k, cascades) at once:
+ * they are spread over `concurrency` internal streams that start after the
+ * work already queued on `stream` and that `stream` waits for at the end,
+ * so their kernels overlap on the device.  Returns once everything is
+ * enqueued.  Results are identical to running each query alone.
+ * Errors: SG_EINVAL (bad query; its status says which), others as
+ * sg_select.  The first failing status is returned. */
+sg_status sg_select_batch(int32_t nq, sg_query *q, int32_t concurrency, void *stream);
+
+/* The same batch recorded once as a CUDA graph (stream capture over the
+ * internal streams) and replayed with a single graph launch per
+ * sg_batch_launch.  Buffers and parameters are fixed at capture; every
+ * query needs its own workspace sized for it, and outputs must be device
+ * or pinned host memory.  sg_batch_capture runs nothing on the device. */
+typedef struct sg_batch sg_batch;
+sg_status sg_batch_capture(int32_t nq, sg_query *q, int32_t concurrency, void *stream, sg_batch **out);
+sg_status sg_batch_launch(sg_batch *b, void *stream);
+void sg_batch_free(sg_batch *b);
+
+/* Serving loop with continuous batching.  A worker thread keeps up to
+ * max_running queries on the device at once, each on its own stream and
+ * workspace; queued requests are admitted in arrival order as soon as a
+ * slot and device memory (memory_budget bytes for workspaces) allow, so
+ * requests arriving while others run overlap with them on the device.
+ * Idle workspaces are kept per graph and reused; when memory is short the
+ * least recently used idle ones are released.  Graphs must stay loaded
+ * while requests on them are pending.  Results are identical to sg_select
+ * on the same query.  The worker uses the library's built-in allocator
+ * (cudaMallocAsync), not the allocator hooks. */
+typedef struct sg_server sg_server;
+typedef struct {
+    int32_t max_running;   /* >= 1 */
+    size_t memory_budget;  /* bytes for workspaces; 0: 80% of free device memory at creation */
+    int32_t k_cap;         /* largest k a request may ask for */
+} sg_server_cfg;
+sg_status sg_server_create(const sg_server_cfg *cfg, sg_server **out);
+/* Queue a request; *request_id identifies it.  SG_EINVAL for bad
+ * arguments, SG_EBUSY if the server is shutting down. */
+sg_status sg_server_submit(sg_server *srv, sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed,
+                           int64_t *request_id);
+/* *done = 1 and the results (host memory, k entries) once the request has
+ * finished; latency_ms = completion minus submission (host clock).
+ * *done = 0 while pending; SG_EINVAL for an unknown id.  A finished
+ * request is forgotten after its results are returned.  If it failed, its
+ * status is returned. */
+sg_status sg_server_poll(sg_server *srv, int64_t request_id, int32_t *done, int32_t *out_seeds,
+                         int64_t *out_gains, double *latency_ms);
+/* Requests queued, running, finished-but-unpolled. */
+sg_status sg_server_counts(sg_server *srv, int64_t *queued, int64_t *running, int64_t *finished);
+/* Stop accepting, finish everything queued, free every resource. */
+void sg_server_destroy(sg_server *srv);
+
 /* Initial gains only (Algorithm 2, first loop): s[v] = sum_r |R(G'_r, v)|
  * for every v, written to out_s (int64[n], device or host memory), and the
  * init snapshot-edge count to *init_edges (NULL allowed; non-NULL

@@ -41,9 +41,11 @@ sg_release_fn g_release = nullptr;
 void *g_alloc_ctx = nullptr;
 }  // namespace
 
+thread_local int g_builtin_alloc = 0;
+
 void *dalloc(size_t bytes, cudaStream_t st)
 {
-    if (g_alloc) return g_alloc(bytes, st, g_alloc_ctx);
+    if (g_alloc && !g_builtin_alloc) return g_alloc(bytes, st, g_alloc_ctx);
     void *p = nullptr;
     if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
         cudaGetLastError();
@@ -55,12 +57,15 @@ void *dalloc(size_t bytes, cudaStream_t st)
 void dfree(void *p, size_t bytes, cudaStream_t st)
 {
     if (!p) return;
-    if (g_release) {
+    if (g_release && !g_builtin_alloc) {
         g_release(p, bytes, st, g_alloc_ctx);
         return;
     }
     cudaFreeAsync(p, st);
 }
+
+void free_workspace(sg_workspace &ws, cudaStream_t st);
+sg_status ensure_wic(sg_graph *g, cudaStream_t st);
 
 namespace {
 
@@ -141,58 +146,6 @@ sg_status upload(sgi::DBuf<T> &b, const T *host, size_t count, cudaStream_t st)
     SG_TRY(dbuf_alloc(b, count, st));
     if (count) SG_CUDA_TRY(cudaMemcpyAsync(b.p, host, count * sizeof(T), cudaMemcpyHostToDevice, st));
     return SG_OK;
-}
-
-void free_workspace(sg_workspace &ws, cudaStream_t st)
-{
-    dbuf_free(ws.s, st);
-    dbuf_free(ws.cov, st);
-    dbuf_free(ws.nbits, st);
-    dbuf_free(ws.pendf, st);
-    dbuf_free(ws.du_m, st);
-    dbuf_free(ws.fq_a, st);
-    dbuf_free(ws.fq_b, st);
-    dbuf_free(ws.du_x, st);
-    dbuf_free(ws.list1, st);
-    dbuf_free(ws.list2, st);
-    dbuf_free(ws.tl, st);
-    dbuf_free(ws.toff, st);
-    dbuf_free(ws.coff, st);
-    dbuf_free(ws.tcnt, st);
-    dbuf_free(ws.du_cnt, st);
-    dbuf_free(ws.anc, st);
-    dbuf_free(ws.anc_list, st);
-    dbuf_free(ws.anc_cnt, st);
-    dbuf_free(ws.lmk_rx, st);
-    dbuf_free(ws.lmk_U, st);
-    dbuf_free(ws.lmk_H, st);
-    dbuf_free(ws.lmk_E, st);
-    dbuf_free(ws.lmk_HE, st);
-    dbuf_free(ws.hcnt_out, st);
-    dbuf_free(ws.hnbr_out, st);
-    dbuf_free(ws.hmask_out, st);
-    dbuf_free(ws.hcnt_in, st);
-    dbuf_free(ws.hnbr_in, st);
-    dbuf_free(ws.hmask_in, st);
-    dbuf_free(ws.soff, st);
-    dbuf_free(ws.snbr, st);
-    dbuf_free(ws.svalid, st);
-    dbuf_free(ws.scan_tmp, st);
-    ws.soff_cap = 0;
-    ws.snbr_cap = 0;
-    ws.slists_on = 0;
-    ws.hw_cap = 0;
-    dbuf_free(ws.slot_vis, st);
-    dbuf_free(ws.slot_qa, st);
-    dbuf_free(ws.slot_touched, st);
-    dbuf_free(ws.ctl, st);
-    dbuf_free(ws.am_gain, st);
-    dbuf_free(ws.am_id, st);
-    dbuf_free(ws.out_seeds, st);
-    dbuf_free(ws.out_gains, st);
-    ws.wcap = 0;
-    ws.kcap = 0;
-    ws.nslots = 0;
 }
 
 void free_graph_buffers(sg_graph *g, cudaStream_t st)
@@ -318,6 +271,11 @@ sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> 
         delete g;
         return rc;
     }
+    if ((rc = ensure_wic(g, st)) != SG_OK) {
+        free_graph_buffers(g, st);
+        delete g;
+        return rc;
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("upload failed: %s", cudaGetErrorString(cudaGetLastError()));
         free_graph_buffers(g, st);
@@ -340,7 +298,59 @@ bool is_pageable(const void *p)
 
 }  // namespace
 
-GraphView view_of(const sg_graph *g, int heavy_on)
+void free_workspace(sg_workspace &ws, cudaStream_t st)
+{
+    dbuf_free(ws.s, st);
+    dbuf_free(ws.cov, st);
+    dbuf_free(ws.nbits, st);
+    dbuf_free(ws.pendf, st);
+    dbuf_free(ws.du_m, st);
+    dbuf_free(ws.fq_a, st);
+    dbuf_free(ws.fq_b, st);
+    dbuf_free(ws.du_x, st);
+    dbuf_free(ws.list1, st);
+    dbuf_free(ws.list2, st);
+    dbuf_free(ws.tl, st);
+    dbuf_free(ws.toff, st);
+    dbuf_free(ws.coff, st);
+    dbuf_free(ws.tcnt, st);
+    dbuf_free(ws.du_cnt, st);
+    dbuf_free(ws.anc, st);
+    dbuf_free(ws.anc_list, st);
+    dbuf_free(ws.anc_cnt, st);
+    dbuf_free(ws.lmk_rx, st);
+    dbuf_free(ws.lmk_U, st);
+    dbuf_free(ws.lmk_H, st);
+    dbuf_free(ws.lmk_E, st);
+    dbuf_free(ws.lmk_HE, st);
+    dbuf_free(ws.hcnt_out, st);
+    dbuf_free(ws.hnbr_out, st);
+    dbuf_free(ws.hmask_out, st);
+    dbuf_free(ws.hcnt_in, st);
+    dbuf_free(ws.hnbr_in, st);
+    dbuf_free(ws.hmask_in, st);
+    dbuf_free(ws.soff, st);
+    dbuf_free(ws.snbr, st);
+    dbuf_free(ws.svalid, st);
+    dbuf_free(ws.scan_tmp, st);
+    ws.soff_cap = 0;
+    ws.snbr_cap = 0;
+    ws.slists_on = 0;
+    ws.hw_cap = 0;
+    dbuf_free(ws.slot_vis, st);
+    dbuf_free(ws.slot_qa, st);
+    dbuf_free(ws.slot_touched, st);
+    dbuf_free(ws.ctl, st);
+    dbuf_free(ws.am_gain, st);
+    dbuf_free(ws.am_id, st);
+    dbuf_free(ws.out_seeds, st);
+    dbuf_free(ws.out_gains, st);
+    ws.wcap = 0;
+    ws.kcap = 0;
+    ws.nslots = 0;
+}
+
+GraphView view_of(const sg_graph *g, const sg_workspace &ws, int heavy_on)
 {
     GraphView v;
     v.n = (int32_t)g->n;
@@ -351,7 +361,6 @@ GraphView view_of(const sg_graph *g, int heavy_on)
     v.crp = g->crp.p;
     v.cin = g->cin.p;
     v.tmi = g->tmi.p;
-    const sg_workspace &ws = g->ws;
     v.hout = HeavyView{g->hid_out.p, g->hpref_out.p, ws.hcnt_out.p, ws.hnbr_out.p, ws.hmask_out.p,
                        nullptr, nullptr, nullptr};
     v.hin = HeavyView{g->hid_in.p, g->hpref_in.p, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p,
@@ -369,9 +378,8 @@ bool heavy_index_enabled(const sg_graph *g, int32_t W)
     return bytes <= 8.0 * (double)(1ull << 30);
 }
 
-sg_status ensure_heavy_index(sg_graph *g, int32_t W, cudaStream_t st)
+sg_status ensure_heavy_index(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st)
 {
-    sg_workspace &ws = g->ws;
     if (ws.hw_cap >= W) return SG_OK;
     dbuf_free(ws.hcnt_out, st);
     dbuf_free(ws.hnbr_out, st);
@@ -408,9 +416,43 @@ sg_status ensure_wic(sg_graph *g, cudaStream_t st)
     return SG_OK;
 }
 
-sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
+// Tier-3 slot memory: 4 KB per node, between 64 MB and 4 GiB.
+size_t tier3_budget(int64_t n)
 {
-    sg_workspace &ws = g->ws;
+    const size_t b = (size_t)n * 4096;
+    return std::min<size_t>((size_t)4 << 30, std::max<size_t>((size_t)64 << 20, b));
+}
+
+// Device bytes a workspace for (W, k) takes, as ensure_workspace /
+// ensure_heavy_index / ensure_snapshot_lists allocate them (upper bound).
+size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
+{
+    const size_t n = (size_t)g->n, nw = n * (size_t)W, W64 = (size_t)64 * W;
+    size_t b = 8 * n;                                  // s
+    b += 8 * nw * 4;                                   // cov, nbits, pendf, du_m
+    b += 4 * nw * 8 * 2;                               // forward queues
+    b += 4 * nw;                                       // du_x
+    b += 4 * (nw + W64 + 64) * 2;                      // task lists
+    b += 4 * nw * 64;                                  // per-snapshot targets
+    b += (8 + 8 + 4) * W64 + 4 * (size_t)W;            // offsets, counts
+    b += 8 * nw + 4 * nw + 4 * (size_t)W;              // ancestors
+    b += 8 * nw * 8 + (W64 << 8) * (4 + 4 + 8 + 8);    // landmarks
+    int qcap = 1;
+    while ((size_t)qcap < n) qcap <<= 1;
+    const size_t per_slot = n * 20 + (size_t)qcap * 4;
+    const size_t slots = std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms * 2, tier3_budget(g->n) / per_slot));
+    b += slots * per_slot;
+    b += (size_t)g->num_sms * 2 * 12 + (size_t)k * 12 + 4096;
+    if (heavy_index_enabled(g, W)) {
+        b += (size_t)(g->hsum_out + g->hsum_in) * W * 12 + (size_t)(g->nh_out + g->nh_in) * W * 4;
+        const size_t nq = (size_t)g->nh_in * W64 + 1;
+        b += nq * 16 + ((size_t)1 << 20) * 4 + (size_t)(1.5 * 64.0 * W * (double)g->nh_in) * 4;
+    }
+    return b;
+}
+
+sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, cudaStream_t st)
+{
     const int64_t n = g->n;
     if (ws.wcap < W) {
         free_workspace(ws, st);
@@ -447,7 +489,7 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
         int qcap = 1;
         while (qcap < n) qcap <<= 1;
         const size_t per_slot = (size_t)n * (2 * sizeof(unsigned long long) + sizeof(int32_t)) + (size_t)qcap * 4;
-        const size_t budget = (size_t)4 << 30;
+        const size_t budget = tier3_budget(n);
         int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms * 2, budget / per_slot));
         const size_t ns = (size_t)slots * (size_t)n;
         SG_TRY(dbuf_alloc(ws.slot_vis, 2 * ns, st));  // per node: visited and pending words side by side
@@ -478,9 +520,9 @@ sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st)
 // row); the list buffer holds 1.5x that plus slack, and if a query exceeds
 // it the device flag marks the lists invalid and the reverse tasks use the
 // per-word index instead.  Skipped when the buffer would pass 2 GiB.
-sg_status ensure_snapshot_lists(sg_graph *g, const Coins &co, double p_uic, int model, cudaStream_t st)
+sg_status ensure_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model,
+                                cudaStream_t st)
 {
-    sg_workspace &ws = g->ws;
     ws.slists_on = 0;
     if (g->nh_in == 0) return SG_OK;
     const double R = 64.0 * co.W;
@@ -538,21 +580,7 @@ sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out)
 
 using namespace sgi;
 
-namespace {
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+namespace sgi {
 
 sg_status check_query(const sg_graph *g, int32_t R, int32_t k)
 {
@@ -576,7 +604,7 @@ sg_status check_query(const sg_graph *g, int32_t R, int32_t k)
     return SG_OK;
 }
 
-}  // namespace
+}  // namespace sgi
 
 extern "C" {
 
@@ -756,10 +784,15 @@ void sg_free_graph(sg_graph *g)
     delete g;
 }
 
-sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
-                    int32_t *out_seeds, int64_t *out_gains, sg_stats *stats)
+}  // extern "C"
+
+namespace sgi {
+
+// Algorithm 2 end to end on graph g with workspace ws.  prepare_only: size
+// the workspace for the query (allocations happen here) and launch nothing.
+sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                      int32_t *out_seeds, int64_t *out_gains, sg_stats *stats, bool prepare_only)
 {
-    clear_error();
     SG_TRY(check_query(g, R, k));
     if (!out_seeds || !out_gains) {
         set_error("sg_select: output pointers must be non-NULL");
@@ -771,13 +804,12 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     cudaStream_t st = (cudaStream_t)stream;
     const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
     const int launches0 = g_launches;
-    if (model == MODEL_WIC) SG_TRY(ensure_wic(g, st));
-    SG_TRY(ensure_workspace(g, co.W, k, st));
+    SG_TRY(ensure_workspace(g, ws, co.W, k, st));
     const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
-    if (heavy_on) SG_TRY(ensure_heavy_index(g, co.W, st));
-    g->ws.slists_on = 0;
-    if (heavy_on && g_snapshot_lists) SG_TRY(ensure_snapshot_lists(g, co, c.p, model, st));
-    sg_workspace &ws = g->ws;
+    if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
+    ws.slists_on = 0;
+    if (heavy_on && g_snapshot_lists) SG_TRY(ensure_snapshot_lists(g, ws, co, c.p, model, st));
+    if (prepare_only) return SG_OK;
     // events: 0 start, 1 after index, 2 after init tier 1, 3 after init,
     // 4 end; per round: after forward update
     std::vector<cudaEvent_t> ev;
@@ -812,14 +844,14 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     SG_CUDA_TRY(cudaMemsetAsync(ws.anc.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.anc_cnt.p, 0, (size_t)co.W * 4, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
-    if (heavy_on) SG_TRY(run_heavy_index(g, co, model, st));
-    if (ws.slists_on) SG_TRY(run_snapshot_lists(g, co, st));
+    if (heavy_on) SG_TRY(run_heavy_index(g, ws, co, model, st));
+    if (ws.slists_on) SG_TRY(run_snapshot_lists(g, ws, co, st));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_index, st));
-    SG_TRY(run_init_gains(g, co, model, heavy_on, st, stats ? &tev : nullptr));
+    SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st, stats ? &tev : nullptr));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_init, st));
     for (int32_t i = 0; i < k; ++i) {
         if (stats) SG_CUDA_TRY(cudaEventRecord(e_round[(size_t)i], st));
-        SG_TRY(run_round(g, co, model, heavy_on, i, st, stats ? e_fwd[(size_t)i] : nullptr));
+        SG_TRY(run_round(g, ws, co, model, heavy_on, i, st, stats ? e_fwd[(size_t)i] : nullptr));
     }
     if (stats) {
         SG_CUDA_TRY(cudaEventRecord(e_round[(size_t)k], st));
@@ -871,6 +903,100 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     return SG_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                    int32_t *out_seeds, int64_t *out_gains, sg_stats *stats)
+{
+    clear_error();
+    if (!g) {
+        set_error("graph handle is NULL");
+        return SG_EINVAL;
+    }
+    return select_impl(g, g->ws, R, k, c, seed, stream, out_seeds, out_gains, stats, false);
+}
+
+sg_status sg_workspace_create(const sg_graph *g, int32_t R_max, int32_t k_max, void *stream, sg_workspace **out)
+{
+    clear_error();
+    if (!g || !out) {
+        set_error("sg_workspace_create: NULL argument");
+        return SG_EINVAL;
+    }
+    SG_TRY(check_query(g, R_max, k_max));
+    if (R_max < 1 || R_max >= (1 << 24)) {
+        set_error("R_max must satisfy 1 <= R_max < 2^24");
+        return SG_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    sg_workspace *ws = new (std::nothrow) sg_workspace();
+    if (!ws) {
+        set_error("host allocation failed");
+        return SG_ENOMEM;
+    }
+    sg_graph *gm = const_cast<sg_graph *>(g);
+    const int32_t W = (R_max + 63) / 64;
+    sg_status rc = ensure_workspace(gm, *ws, W, k_max, st);
+    if (rc == SG_OK && heavy_index_enabled(g, W)) rc = ensure_heavy_index(gm, *ws, W, st);
+    if (rc == SG_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+        set_error("sg_workspace_create: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = SG_ECUDA;
+    }
+    if (rc != SG_OK) {
+        free_workspace(*ws, st);
+        delete ws;
+        return rc;
+    }
+    ws->owner_n = g->n;
+    ws->device = g->device;
+    *out = ws;
+    return SG_OK;
+}
+
+sg_status sg_select_ws(sg_graph *g, sg_workspace *ws, int32_t R, int32_t k, sg_cascade c, uint64_t seed,
+                       void *stream, int32_t *out_seeds, int64_t *out_gains, sg_stats *stats)
+{
+    clear_error();
+    if (!g || !ws) {
+        set_error("sg_select_ws: NULL handle");
+        return SG_EINVAL;
+    }
+    if (ws->owner_n != g->n || ws->device != g->device) {
+        set_error("sg_select_ws: workspace was created for another graph");
+        return SG_EINVAL;
+    }
+    return select_impl(g, *ws, R, k, c, seed, stream, out_seeds, out_gains, stats, false);
+}
+
+sg_status sg_workspace_bytes(const sg_graph *g, int32_t R_max, int32_t k_max, size_t *bytes)
+{
+    clear_error();
+    if (!g || !bytes) {
+        set_error("sg_workspace_bytes: NULL argument");
+        return SG_EINVAL;
+    }
+    SG_TRY(check_query(g, R_max, k_max));
+    if (R_max < 1 || R_max >= (1 << 24)) {
+        set_error("R_max must satisfy 1 <= R_max < 2^24");
+        return SG_EINVAL;
+    }
+    *bytes = workspace_bytes(g, (R_max + 63) / 64, k_max);
+    return SG_OK;
+}
+
+void sg_workspace_free(sg_workspace *ws)
+{
+    if (!ws) return;
+    DeviceGuard dg(ws->device);
+    cudaDeviceSynchronize();
+    free_workspace(*ws, (cudaStream_t)0);
+    cudaDeviceSynchronize();
+    delete ws;
+}
+
 sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, void *stream, int64_t *out_s,
                         uint64_t *init_edges)
 {
@@ -885,16 +1011,15 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
-    if (model == MODEL_WIC) SG_TRY(ensure_wic(g, st));
-    SG_TRY(ensure_workspace(g, co.W, 1, st));
-    const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
-    if (heavy_on) SG_TRY(ensure_heavy_index(g, co.W, st));
-    g->ws.slists_on = 0;
     sg_workspace &ws = g->ws;
+    SG_TRY(ensure_workspace(g, ws, co.W, 1, st));
+    const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
+    if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
+    ws.slists_on = 0;
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
-    if (heavy_on) SG_TRY(run_heavy_index(g, co, model, st));
-    SG_TRY(run_init_gains(g, co, model, heavy_on, st));
+    if (heavy_on) SG_TRY(run_heavy_index(g, ws, co, model, st));
+    SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));
     if (init_edges) {
         Ctl h;
@@ -923,7 +1048,6 @@ sg_status sg_live_masks(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
-    if (model == MODEL_WIC) SG_TRY(ensure_wic(g, st));
     const size_t count = (size_t)g->m * (size_t)co.W;
     if (count == 0) return SG_OK;
     if (!is_pageable(out_masks)) {

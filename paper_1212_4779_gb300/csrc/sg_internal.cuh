@@ -56,6 +56,8 @@ void clear_error();
     } while (0)
 
 // ------------------------------------------------------------------ memory
+// nonzero: this thread allocates with cudaMallocAsync even when hooks are set
+extern thread_local int g_builtin_alloc;
 void *dalloc(size_t bytes, cudaStream_t st);
 void dfree(void *p, size_t bytes, cudaStream_t st);
 
@@ -154,6 +156,8 @@ struct Ctl {
 
 // Workspace owned by a graph handle and reused by every call on it.
 struct sg_workspace {
+    int64_t owner_n = -1;  // node count of the graph it was created for (explicit workspaces)
+    int device = 0;
     int64_t n = 0;
     int32_t wcap = 0;     // words of capacity of the [W][n] arrays
     int32_t nslots = 0;   // tier-3 (CTA engine) slots
@@ -214,10 +218,11 @@ struct sg_graph {
 
 namespace sgi {
 
-GraphView view_of(const sg_graph *g, int heavy_on);
+GraphView view_of(const sg_graph *g, const sg_workspace &ws, int heavy_on);
 sg_status ensure_wic(sg_graph *g, cudaStream_t st);
-sg_status ensure_workspace(sg_graph *g, int32_t W, int32_t k, cudaStream_t st);
-sg_status ensure_heavy_index(sg_graph *g, int32_t W, cudaStream_t st);
+sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, cudaStream_t st);
+sg_status ensure_heavy_index(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st);
+void free_workspace(sg_workspace &ws, cudaStream_t st);
 sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out);
 bool heavy_index_enabled(const sg_graph *g, int32_t W);
 
@@ -232,18 +237,39 @@ extern int g_landmarks;
 extern int g_snapshot_lists;
 
 // kernels (sg_kernels.cu)
-sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t st);
-sg_status run_snapshot_lists(sg_graph *g, const Coins &co, cudaStream_t st);
-sg_status ensure_snapshot_lists(sg_graph *g, const Coins &co, double p_uic, int model, cudaStream_t st);
+sg_status run_heavy_index(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
+sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
+sg_status ensure_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model,
+                                cudaStream_t st);
 // events recorded around the initial-gain tier launches (any may be null)
 struct TierEvents {
     cudaEvent_t start = nullptr, t1 = nullptr, t2 = nullptr, t3 = nullptr;
 };
-sg_status run_init_gains(sg_graph *g, const Coins &co, int model, int heavy_on, cudaStream_t st,
+sg_status run_init_gains(sg_graph *g, sg_workspace &ws, const Coins &co, int model, int heavy_on, cudaStream_t st,
                          const TierEvents *ev = nullptr);
-sg_status run_round(sg_graph *g, const Coins &co, int model, int heavy_on, int32_t round, cudaStream_t st,
-                    cudaEvent_t after_fwd = nullptr);
+sg_status run_round(sg_graph *g, sg_workspace &ws, const Coins &co, int model, int heavy_on, int32_t round,
+                    cudaStream_t st, cudaEvent_t after_fwd = nullptr);
 sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st);
+
+// host driver (sg_host.cu)
+sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                      int32_t *out_seeds, int64_t *out_gains, sg_stats *stats, bool prepare_only);
+sg_status check_query(const sg_graph *g, int32_t R, int32_t k);
+size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k);
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 
 }  // namespace sgi

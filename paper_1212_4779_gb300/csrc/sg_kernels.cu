@@ -1843,11 +1843,10 @@ __global__ void live_masks_kernel(Coins co, long long m, const uint2 *fw, uint32
 
 // ================================================================ launches
 
-EngineArgs engine_args(sg_graph *g, const Coins &co, int heavy_on)
+EngineArgs engine_args(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy_on)
 {
-    sg_workspace &ws = g->ws;
     EngineArgs a;
-    a.g = view_of(g, heavy_on);
+    a.g = view_of(g, ws, heavy_on);
     a.co = co;
     a.ctl = ws.ctl.p;
     a.s = ws.s.p;
@@ -1868,9 +1867,8 @@ EngineArgs engine_args(sg_graph *g, const Coins &co, int heavy_on)
     return a;
 }
 
-SlotArgs slot_args(sg_graph *g)
+SlotArgs slot_args(sg_workspace &ws)
 {
-    sg_workspace &ws = g->ws;
     SlotArgs s;
     s.vis = ws.slot_vis.p;
     s.pend = nullptr;
@@ -1882,7 +1880,7 @@ SlotArgs slot_args(sg_graph *g)
 
 // tier 1 -> tier 2 -> tier 3 for one task family
 template <int DIR, int MODEL, int TASK>
-sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, const TierEvents *ev)
+sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cudaStream_t st, const TierEvents *ev)
 {
     if (ev && ev->start) SG_CUDA_TRY(cudaEventRecord(ev->start, st));
     EngineArgs a = a0;
@@ -1904,12 +1902,12 @@ sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, const
         auto kern = coop_engine_kernel<TAB_HASH, DIR, MODEL, TASK>;
         const size_t smem = coop_hash_smem();
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<g->num_sms, CoopShape<TAB_HASH>::T, smem, st>>>(a, slot_args(g));
+        kern<<<g->num_sms, CoopShape<TAB_HASH>::T, smem, st>>>(a, slot_args(ws));
         SG_CUDA_TRY(cudaGetLastError());
         ++g_launches;
     }
     if (ev && ev->t2) SG_CUDA_TRY(cudaEventRecord(ev->t2, st));
-    coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK><<<g->ws.nslots, CoopShape<TAB_DENSE>::T, 0, st>>>(a, slot_args(g));
+    coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK><<<ws.nslots, CoopShape<TAB_DENSE>::T, 0, st>>>(a, slot_args(ws));
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
     if (ev && ev->t3) SG_CUDA_TRY(cudaEventRecord(ev->t3, st));
@@ -1917,16 +1915,15 @@ sg_status launch_tiers(sg_graph *g, const EngineArgs &a0, cudaStream_t st, const
 }
 
 template <int DIR, int MODEL>
-sg_status launch_index(sg_graph *g, const Coins &co, cudaStream_t st)
+sg_status launch_index(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st)
 {
-    sg_workspace &ws = g->ws;
     const bool fwd = DIR == DIR_FWD;
     const int nh = fwd ? g->nh_out : g->nh_in;
     if (nh == 0) return SG_OK;
     int32_t *hcnt = fwd ? ws.hcnt_out.p : ws.hcnt_in.p;
     SG_CUDA_TRY(cudaMemsetAsync(hcnt, 0, (size_t)nh * co.W * sizeof(int32_t), st));
     heavy_index_kernel<DIR, MODEL><<<g->num_sms * 8, 256, 0, st>>>(
-        view_of(g, 1), co, fwd ? g->hrow_out.p : g->hrow_in.p, fwd ? g->hcpref_out.p : g->hcpref_in.p, nh, hcnt,
+        view_of(g, ws, 1), co, fwd ? g->hrow_out.p : g->hrow_in.p, fwd ? g->hcpref_out.p : g->hcpref_in.p, nh, hcnt,
         fwd ? ws.hnbr_out.p : ws.hnbr_in.p, fwd ? ws.hmask_out.p : ws.hmask_in.p,
         fwd ? g->hpref_out.p : g->hpref_in.p);
     SG_CUDA_TRY(cudaGetLastError());
@@ -1935,13 +1932,13 @@ sg_status launch_index(sg_graph *g, const Coins &co, cudaStream_t st)
 }
 
 template <int MODEL>
-sg_status init_gains_t(sg_graph *g, const Coins &co, int heavy_on, cudaStream_t st, const TierEvents *ev)
+sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy_on, cudaStream_t st,
+                       const TierEvents *ev)
 {
-    EngineArgs a = engine_args(g, co, heavy_on);
+    EngineArgs a = engine_args(g, ws, co, heavy_on);
     a.ntasks = (long long)g->n * co.W;
     const int K = std::min(std::min(g_landmarks, g->lmk_count), MAX_LMK);
     if (K > 0) {
-        sg_workspace &ws = g->ws;
         a.lmk_k = K;
         for (int i = 0; i < K; ++i) a.lmk_x[i] = g->lmk_nodes[i];
         const size_t nw = (size_t)g->n * co.W;
@@ -1969,18 +1966,18 @@ sg_status init_gains_t(sg_graph *g, const Coins &co, int heavy_on, cudaStream_t 
         SG_CUDA_TRY(cudaGetLastError());
         g_launches += K + 2;
     }
-    return launch_tiers<DIR_FWD, MODEL, TASK_INIT>(g, a, st, ev);
+    return launch_tiers<DIR_FWD, MODEL, TASK_INIT>(g, ws, a, st, ev);
 }
 
 template <int MODEL>
-sg_status round_t(sg_graph *g, const Coins &co, int heavy_on, int32_t round, cudaStream_t st, cudaEvent_t after_fwd)
+sg_status round_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy_on, int32_t round, cudaStream_t st,
+                  cudaEvent_t after_fwd)
 {
-    sg_workspace &ws = g->ws;
     argmax_kernel<<<ws.am_blocks, AM_T, 0, st>>>(ws.s.p, (int)g->n, ws.ctl.p, ws.am_gain.p, ws.am_id.p,
                                                  ws.out_seeds.p, ws.out_gains.p, round, ws.du_cnt.p, co.W);
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
-    EngineArgs a = engine_args(g, co, heavy_on);
+    EngineArgs a = engine_args(g, ws, co, heavy_on);
     FwdArgs f;
     f.cov = ws.cov.p;
     f.nbits = ws.nbits.p;
@@ -2004,7 +2001,7 @@ sg_status round_t(sg_graph *g, const Coins &co, int heavy_on, int32_t round, cud
     SG_CUDA_TRY(cudaGetLastError());
     g_launches += 2;
     if (after_fwd) SG_CUDA_TRY(cudaEventRecord(after_fwd, st));
-    return launch_tiers<DIR_REV, MODEL, TASK_REVT>(g, a, st, nullptr);
+    return launch_tiers<DIR_REV, MODEL, TASK_REVT>(g, ws, a, st, nullptr);
 }
 
 }  // namespace
@@ -2013,19 +2010,18 @@ thread_local int g_launches = 0;
 int g_tier_limit[2] = {(1 << T1_LOGC) / 2, (1 << CO_LOGC) / 2};
 int g_landmarks = 8;
 
-sg_status run_heavy_index(sg_graph *g, const Coins &co, int model, cudaStream_t st)
+sg_status run_heavy_index(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st)
 {
     if (model == MODEL_WIC) {
-        SG_TRY((launch_index<DIR_FWD, MODEL_WIC>(g, co, st)));
-        return launch_index<DIR_REV, MODEL_WIC>(g, co, st);
+        SG_TRY((launch_index<DIR_FWD, MODEL_WIC>(g, ws, co, st)));
+        return launch_index<DIR_REV, MODEL_WIC>(g, ws, co, st);
     }
-    SG_TRY((launch_index<DIR_FWD, MODEL_UIC>(g, co, st)));
-    return launch_index<DIR_REV, MODEL_UIC>(g, co, st);
+    SG_TRY((launch_index<DIR_FWD, MODEL_UIC>(g, ws, co, st)));
+    return launch_index<DIR_REV, MODEL_UIC>(g, ws, co, st);
 }
 
-sg_status run_snapshot_lists(sg_graph *g, const Coins &co, cudaStream_t st)
+sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st)
 {
-    sg_workspace &ws = g->ws;
     const int nh = g->nh_in;
     const long long nq = (long long)nh * 64 * co.W;
     // counts
@@ -2053,18 +2049,18 @@ sg_status run_snapshot_lists(sg_graph *g, const Coins &co, cudaStream_t st)
     return SG_OK;
 }
 
-sg_status run_init_gains(sg_graph *g, const Coins &co, int model, int heavy_on, cudaStream_t st,
+sg_status run_init_gains(sg_graph *g, sg_workspace &ws, const Coins &co, int model, int heavy_on, cudaStream_t st,
                          const TierEvents *ev)
 {
-    return model == MODEL_WIC ? init_gains_t<MODEL_WIC>(g, co, heavy_on, st, ev)
-                              : init_gains_t<MODEL_UIC>(g, co, heavy_on, st, ev);
+    return model == MODEL_WIC ? init_gains_t<MODEL_WIC>(g, ws, co, heavy_on, st, ev)
+                              : init_gains_t<MODEL_UIC>(g, ws, co, heavy_on, st, ev);
 }
 
-sg_status run_round(sg_graph *g, const Coins &co, int model, int heavy_on, int32_t round, cudaStream_t st,
-                    cudaEvent_t after_fwd)
+sg_status run_round(sg_graph *g, sg_workspace &ws, const Coins &co, int model, int heavy_on, int32_t round,
+                    cudaStream_t st, cudaEvent_t after_fwd)
 {
-    return model == MODEL_WIC ? round_t<MODEL_WIC>(g, co, heavy_on, round, st, after_fwd)
-                              : round_t<MODEL_UIC>(g, co, heavy_on, round, st, after_fwd);
+    return model == MODEL_WIC ? round_t<MODEL_WIC>(g, ws, co, heavy_on, round, st, after_fwd)
+                              : round_t<MODEL_UIC>(g, ws, co, heavy_on, round, st, after_fwd);
 }
 
 sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st)

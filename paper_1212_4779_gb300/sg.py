@@ -27,7 +27,10 @@ _STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ETI
            6: "SG_EINTERNAL"}
 
 # exported entry points, as declared in include/sg.h
-EXPORTS = ("sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
+EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg_select_ws", "sg_select_batch",
+           "sg_batch_capture", "sg_batch_launch", "sg_batch_free", "sg_server_create", "sg_server_submit",
+           "sg_server_poll", "sg_server_counts", "sg_server_destroy",
+           "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
            "sg_set_snapshot_lists", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
            "sg_init_gains", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
 
@@ -61,6 +64,16 @@ class sg_stats(ctypes.Structure):
             v = getattr(self, k)
             out[k] = [list(row) for row in v] if k.startswith("work_") else v
         return out
+
+
+class sg_query(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("ws", ctypes.c_void_p), ("R", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("cascade", sg_cascade), ("seed", ctypes.c_uint64), ("out_seeds", ctypes.c_void_p),
+                ("out_gains", ctypes.c_void_p), ("status", ctypes.c_int)]
+
+
+class sg_server_cfg(ctypes.Structure):
+    _fields_ = [("max_running", ctypes.c_int32), ("memory_budget", ctypes.c_size_t), ("k_cap", ctypes.c_int32)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -101,9 +114,27 @@ def lib() -> ctypes.CDLL:
         L.sg_graph_csr.argtypes = [P, P, P, P]
         L.sg_free_graph.argtypes = [P]
         L.sg_free_graph.restype = None
+        L.sg_workspace_create.argtypes = [P, i32, i32, P, ctypes.POINTER(P)]
+        L.sg_workspace_bytes.argtypes = [P, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+        L.sg_workspace_free.argtypes = [P]
+        L.sg_workspace_free.restype = None
+        L.sg_select_ws.argtypes = [P, P, i32, i32, sg_cascade, u64, P, P, P, ctypes.POINTER(sg_stats)]
+        L.sg_select_batch.argtypes = [i32, ctypes.POINTER(sg_query), i32, P]
+        L.sg_batch_capture.argtypes = [i32, ctypes.POINTER(sg_query), i32, P, ctypes.POINTER(P)]
+        L.sg_batch_launch.argtypes = [P, P]
+        L.sg_batch_free.argtypes = [P]
+        L.sg_batch_free.restype = None
+        L.sg_server_create.argtypes = [ctypes.POINTER(sg_server_cfg), ctypes.POINTER(P)]
+        L.sg_server_submit.argtypes = [P, P, i32, i32, sg_cascade, u64, ctypes.POINTER(i64)]
+        L.sg_server_poll.argtypes = [P, i64, ctypes.POINTER(i32), P, P, ctypes.POINTER(ctypes.c_double)]
+        L.sg_server_counts.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.sg_server_destroy.argtypes = [P]
+        L.sg_server_destroy.restype = None
         L.sg_last_error.restype = ctypes.c_char_p
         L.sg_version.restype = ctypes.c_char_p
-        for name in ("sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
+        for name in ("sg_workspace_create", "sg_workspace_bytes", "sg_select_ws", "sg_select_batch",
+                     "sg_batch_capture", "sg_batch_launch", "sg_server_create", "sg_server_submit",
+                     "sg_server_poll", "sg_server_counts", "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
                      "sg_set_snapshot_lists", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
                      "sg_init_gains", "sg_live_masks", "sg_graph_csr"):
             getattr(L, name).restype = ctypes.c_int
@@ -302,6 +333,103 @@ def sg_graph_csr(h, row_ptr, col, stream=None):
 def sg_free_graph(h):
     if h:
         lib().sg_free_graph(h)
+
+
+def sg_workspace_create(h, R_max, k_max, stream=None):
+    w = ctypes.c_void_p()
+    _check(lib().sg_workspace_create(h, int(R_max), int(k_max), _stream_ptr(stream), ctypes.byref(w)))
+    return w
+
+
+def sg_workspace_bytes(h, R_max, k_max):
+    b = ctypes.c_size_t()
+    _check(lib().sg_workspace_bytes(h, int(R_max), int(k_max), ctypes.byref(b)))
+    return b.value
+
+
+def sg_workspace_free(w):
+    if w:
+        lib().sg_workspace_free(w)
+
+
+def sg_select_ws(h, w, R, k, model, p, seed, out_seeds, out_gains, stream=None, stats=False):
+    st = sg_stats() if stats else None
+    _check(lib().sg_select_ws(h, w, int(R), int(k), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                              _stream_ptr(stream), ctypes.c_void_p(_addr(out_seeds)[0]),
+                              ctypes.c_void_p(_addr(out_gains)[0]), ctypes.byref(st) if stats else None))
+    return st.as_dict() if stats else None
+
+
+def _queries(items):
+    """items: (graph handle, workspace or None, R, k, model, p, seed, seeds_out, gains_out)."""
+    arr = (sg_query * len(items))()
+    for i, (h, w, R, k, model, p, seed, so, go) in enumerate(items):
+        arr[i] = sg_query(h, w, int(R), int(k), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                          ctypes.c_void_p(_addr(so)[0]), ctypes.c_void_p(_addr(go)[0]), 0)
+    return arr
+
+
+def sg_select_batch(items, concurrency=8, stream=None):
+    """Run a batch of queries concurrently; returns the per-query statuses."""
+    arr = _queries(items)
+    rc = lib().sg_select_batch(len(items), arr, int(concurrency), _stream_ptr(stream))
+    _check(rc)
+    return [arr[i].status for i in range(len(items))]
+
+
+def sg_batch_capture(items, concurrency=8, stream=None):
+    arr = _queries(items)
+    b = ctypes.c_void_p()
+    _check(lib().sg_batch_capture(len(items), arr, int(concurrency), _stream_ptr(stream), ctypes.byref(b)))
+    return b
+
+
+def sg_batch_launch(b, stream=None):
+    _check(lib().sg_batch_launch(b, _stream_ptr(stream)))
+
+
+def sg_batch_free(b):
+    if b:
+        lib().sg_batch_free(b)
+
+
+def sg_server_create(max_running=8, memory_budget=0, k_cap=128):
+    _ensure_ready()
+    cfg = sg_server_cfg(int(max_running), int(memory_budget), int(k_cap))
+    sv = ctypes.c_void_p()
+    _check(lib().sg_server_create(ctypes.byref(cfg), ctypes.byref(sv)))
+    return sv
+
+
+def sg_server_submit(sv, h, R, k, model, p, seed):
+    rid = ctypes.c_int64()
+    _check(lib().sg_server_submit(sv, h, int(R), int(k), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                                  ctypes.byref(rid)))
+    return rid.value
+
+
+def sg_server_poll(sv, rid, k):
+    """(done, seeds, gains, latency_ms); seeds/gains None while pending."""
+    done = ctypes.c_int32()
+    lat = ctypes.c_double()
+    seeds = np.zeros(k, dtype=np.int32)
+    gains = np.zeros(k, dtype=np.int64)
+    _check(lib().sg_server_poll(sv, int(rid), ctypes.byref(done), ctypes.c_void_p(seeds.ctypes.data),
+                                ctypes.c_void_p(gains.ctypes.data), ctypes.byref(lat)))
+    if not done.value:
+        return False, None, None, None
+    return True, seeds, gains, lat.value
+
+
+def sg_server_counts(sv):
+    q, r, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sg_server_counts(sv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f)))
+    return q.value, r.value, f.value
+
+
+def sg_server_destroy(sv):
+    if sv:
+        lib().sg_server_destroy(sv)
 
 
 # --------------------------------------------------------------- convenience

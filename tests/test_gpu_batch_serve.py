@@ -1,0 +1,178 @@
+"""Batched and served execution give the same seeds and gains as each query
+run alone (sg_select), which the parity tests tie to the oracle; integers,
+so the tolerance is zero."""
+
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1212_4779_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1212_4779_gb300 import sg as _sg
+
+    return _sg
+
+
+@pytest.fixture(scope="module")
+def mixed(sg):
+    """Ten small queries over five graphs of the batched recipe family."""
+    recipes = inputs.batch_queries(5, first=0)
+    graphs, queries = [], []
+    for q in recipes:
+        q = dict(q, n=min(q["n"], 6000))
+        q["n_edges"] = int(q["n"] * q["mean_deg"] / 2)
+        n, s, d = inputs.batch_graph(q)
+        g = sg.Graph.from_coo(n, s, d)
+        graphs.append((g, n, s, d))
+        for j, R in enumerate((q["R"], 65)):
+            queries.append(dict(gi=len(graphs) - 1, model=q["model"], p=q["p"], R=R, k=min(q["k"], 30),
+                                seed=q["seed"] + 7 * j))
+    alone = []
+    for qq in queries:
+        g = graphs[qq["gi"]][0]
+        alone.append(g.select(qq["R"], qq["k"], qq["model"], qq["p"], qq["seed"]))
+    return graphs, queries, alone
+
+
+def _items(sg, graphs, queries, torch, workspaces):
+    items, outs = [], []
+    for i, qq in enumerate(queries):
+        so = torch.zeros(qq["k"], dtype=torch.int32, device="cuda")
+        go = torch.zeros(qq["k"], dtype=torch.int64, device="cuda")
+        outs.append((so, go))
+        items.append((graphs[qq["gi"]][0].handle, workspaces[i], qq["R"], qq["k"], qq["model"], qq["p"], qq["seed"],
+                      so, go))
+    return items, outs
+
+
+def test_alone_matches_oracle(sg, mixed):
+    graphs, queries, alone = mixed
+    for qq, res in list(zip(queries, alone))[:4]:
+        _, n, s, d = graphs[qq["gi"]]
+        ref = oracle.Graph(n, s, d, qq["model"], qq["p"]).select(qq["R"], qq["k"], qq["seed"], mode=oracle.DU)
+        assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+
+
+def test_batch_equals_alone(sg, mixed):
+    import torch
+
+    graphs, queries, alone = mixed
+    wss = [sg.sg_workspace_create(graphs[qq["gi"]][0].handle, qq["R"], qq["k"]) for qq in queries]
+    try:
+        for conc in (1, 3, 16):
+            items, outs = _items(sg, graphs, queries, torch, wss)
+            st = sg.sg_select_batch(items, concurrency=conc)
+            torch.cuda.synchronize()
+            assert all(x == sg.SG_OK for x in st)
+            for (so, go), res in zip(outs, alone):
+                assert np.array_equal(so.cpu().numpy(), res.seeds)
+                assert np.array_equal(go.cpu().numpy(), res.gains)
+    finally:
+        for w in wss:
+            sg.sg_workspace_free(w)
+
+
+def test_captured_batch_replays_identically(sg, mixed):
+    import torch
+
+    graphs, queries, alone = mixed
+    wss = [sg.sg_workspace_create(graphs[qq["gi"]][0].handle, qq["R"], qq["k"]) for qq in queries]
+    stream = torch.cuda.Stream()
+    items, outs = _items(sg, graphs, queries, torch, wss)
+    b = sg.sg_batch_capture(items, concurrency=4, stream=stream)
+    try:
+        for _ in range(2):
+            for so, go in outs:
+                so.fill_(-1)
+                go.fill_(-1)
+            torch.cuda.synchronize()
+            sg.sg_batch_launch(b, stream=stream)
+            stream.synchronize()
+            for (so, go), res in zip(outs, alone):
+                assert np.array_equal(so.cpu().numpy(), res.seeds)
+                assert np.array_equal(go.cpu().numpy(), res.gains)
+    finally:
+        sg.sg_batch_free(b)
+        for w in wss:
+            sg.sg_workspace_free(w)
+
+
+def test_batch_rejects_shared_workspace(sg, mixed):
+    import torch
+
+    graphs, queries, _ = mixed
+    q0 = [q for q in queries if q["gi"] == 0][:2]
+    items, _ = _items(sg, graphs, q0, torch, [None, None])  # both would use graph 0's own workspace
+    with pytest.raises(sg.SGError) as ei:
+        sg.sg_select_batch(items)
+    assert ei.value.status == sg.SG_EINVAL
+
+
+def test_server_results_equal_alone_under_overlap(sg, mixed):
+    """Requests arrive while others run (bursts); every result equals the
+    query run alone, and at least two requests were on the device at once."""
+    graphs, queries, alone = mixed
+    srv = sg.sg_server_create(max_running=4, k_cap=64)
+    try:
+        ids = []
+        peak = 0
+        for rep in range(3):
+            for i, qq in enumerate(queries):
+                rid = sg.sg_server_submit(srv, graphs[qq["gi"]][0].handle, qq["R"], qq["k"], qq["model"], qq["p"],
+                                          qq["seed"])
+                ids.append((rid, i))
+                peak = max(peak, sg.sg_server_counts(srv)[1])
+            time.sleep(0.002)
+        pending = list(ids)
+        deadline = time.time() + 300
+        while pending and time.time() < deadline:
+            peak = max(peak, sg.sg_server_counts(srv)[1])
+            rest = []
+            for rid, i in pending:
+                done, seeds, gains, lat = sg.sg_server_poll(srv, rid, queries[i]["k"])
+                if not done:
+                    rest.append((rid, i))
+                    continue
+                assert np.array_equal(seeds, alone[i].seeds) and np.array_equal(gains, alone[i].gains)
+                assert lat >= 0
+            pending = rest
+            time.sleep(0.001)
+        assert not pending
+        assert peak >= 2
+    finally:
+        sg.sg_server_destroy(srv)
+
+
+def test_server_admission_limits(sg, mixed):
+    graphs, queries, _ = mixed
+    g = graphs[0][0]
+    srv = sg.sg_server_create(max_running=2, memory_budget=1 << 20, k_cap=16)  # 1 MB: nothing fits
+    try:
+        with pytest.raises(sg.SGError):
+            sg.sg_server_submit(srv, g.handle, 64, 17, "uic", 0.05, 1)  # k above k_cap
+        rid = sg.sg_server_submit(srv, g.handle, 64, 5, "uic", 0.05, 1)
+        deadline = time.time() + 60
+        while time.time() < deadline:
+            try:
+                done, *_ = sg.sg_server_poll(srv, rid, 5)
+            except sg.SGError as e:
+                assert e.status == sg.SG_ENOMEM
+                break
+            time.sleep(0.01)
+        else:
+            pytest.fail("request never finished")
+    finally:
+        sg.sg_server_destroy(srv)
