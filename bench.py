@@ -122,15 +122,27 @@ def _dist():
 
 
 def _barrier_and_max(x, ws):
+    """Maximum of `x` over the ranks after a barrier (a CUDA tensor under
+    NCCL, a host tensor under gloo)."""
     if ws <= 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.barrier()
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(local_ms_total, units_per_step, steps, ws):
+    """Whole-job throughput of `ws` independent replicas, each running
+    `steps` steps of `units_per_step` units: the units of all ranks divided
+    by the slowest rank's time.  Returns (ms per step, units per second)."""
+    total_ms = _barrier_and_max(float(local_ms_total), ws)
+    ms_step = total_ms / steps
+    return ms_step, units_per_step * ws / (ms_step / 1e3)
 
 
 def cpu_baseline(wl, n, s, d, target_s=15.0):
@@ -179,9 +191,137 @@ def run_reference(args, wl):
 
 
 def wl_desc(wl):
-    return (f"R-MAT scale 20, 8388608 arcs, (0.57,0.19,0.19,0.05), weighted cascade, R={wl.R}, "
-            f"k={wl.k}, hash seed {wl.seed}" if wl.name == "rmat20"
-            else f"{wl.name} {wl.model} p={wl.p} R={wl.R} k={wl.k} seed={wl.seed}")
+    if wl.name.startswith("rmat"):
+        scale = int(wl.name[4:])
+        return (f"R-MAT scale {scale}, {8 << scale} arcs, (0.57,0.19,0.19,0.05), weighted cascade, R={wl.R}, "
+                f"k={wl.k}, hash seed {wl.seed}")
+    return f"{wl.name} {wl.model} p={wl.p} R={wl.R} k={wl.k} seed={wl.seed}"
+
+
+def _gen_graph(q):
+    return inputs.batch_graph(q)
+
+
+def _batch_graphs(qs, workers=None):
+    """The recipe graphs of `qs`, generated in a spawned process pool (before
+    any CUDA call, so no worker inherits a CUDA context)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_graph, qs, chunksize=4))
+
+
+def run_batched(args):
+    """Config 4: the 256 batched-recipe queries (Chung-Lu graphs, n
+    log-uniform in [1e3, 2e5], mixed cascades, R in {64, 128, 256}, k in
+    [10, 100]).  Times one query per launch in sequence, the same queries as
+    one batch over concurrent streams, and the batch captured once as a CUDA
+    graph and replayed with a single launch; checks that all three agree."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1212_4779_gb300 import sg
+
+    qs = inputs.batch_queries(args.queries)
+    coo = _batch_graphs(qs)
+    torch.cuda.set_device(0)
+    graphs = [sg.Graph.from_coo(*c) for c in coo]
+    del coo
+    dev = torch.device("cuda", 0)
+    outs = [(torch.zeros(q["k"], dtype=torch.int32, device=dev), torch.zeros(q["k"], dtype=torch.int64, device=dev))
+            for q in qs]
+    stream = torch.cuda.Stream()
+
+    def serial():
+        for q, g, (so, go) in zip(qs, graphs, outs):
+            sg.sg_select(g.handle, q["R"], q["k"], q["model"], q["p"], q["seed"], so, go, stream=stream)
+
+    serial()
+    stream.synchronize()
+    ref = [(so.cpu().numpy().copy(), go.cpu().numpy().copy()) for so, go in outs]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        serial()
+    stream.synchronize()
+    t_serial = (time.perf_counter() - t0) / args.steps
+
+    wss = [sg.sg_workspace_create(g.handle, q["R"], q["k"]) for q, g in zip(qs, graphs)]
+    items = [(g.handle, w, q["R"], q["k"], q["model"], q["p"], q["seed"], so, go)
+             for q, g, w, (so, go) in zip(qs, graphs, wss, outs)]
+    sg.sg_select_batch(items, concurrency=args.concurrency, stream=stream)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sg.sg_select_batch(items, concurrency=args.concurrency, stream=stream)
+    stream.synchronize()
+    t_batch = (time.perf_counter() - t0) / args.steps
+    ok_batch = all(np.array_equal(so.cpu().numpy(), a) and np.array_equal(go.cpu().numpy(), b)
+                   for (so, go), (a, b) in zip(outs, ref))
+
+    b = sg.sg_batch_capture(items, concurrency=args.concurrency, stream=stream)
+    sg.sg_batch_launch(b, stream=stream)
+    stream.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sg.sg_batch_launch(b, stream=stream)
+    ev1.record(stream)
+    ev1.synchronize()
+    t_graph = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    ok_graph = all(np.array_equal(so.cpu().numpy(), a) and np.array_equal(go.cpu().numpy(), b_)
+                   for (so, go), (a, b_) in zip(outs, ref))
+    sg.sg_batch_free(b)
+    for w in wss:
+        sg.sg_workspace_free(w)
+    nq = len(qs)
+    line = {"metric": "queries/s, batched StaticGreedy-DU (config 4)", "value": nq / t_graph, "unit": "queries/s",
+            "n_gpus": 1, "steps": args.steps, "higher_is_better": True, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"{nq} batched-recipe queries (Chung-Lu, n log-uniform 1e3..2e5)",
+                       "concurrency": args.concurrency},
+            "one_query_per_launch_qps": nq / t_serial, "batch_streams_qps": nq / t_batch,
+            "batch_graph_qps": nq / t_graph, "speedup_vs_serial": t_serial / t_graph,
+            "results_equal_serial": bool(ok_batch and ok_graph)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args):
+    """Config 5: Poisson arrivals against resident graphs -- a directed R-MAT
+    (scale 22 by default, WIC) plus the first 64 batched-recipe graphs;
+    per-request R in {100, 200}, k in [10, 100]; continuous batching through
+    the library's server vs one query per launch in arrival order."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1212_4779_gb300 import serve, sg
+
+    qs = inputs.batch_queries(64)
+    coo = _batch_graphs(qs)
+    big = inputs.rmat(args.served_scale, 16 << args.served_scale, (0.57, 0.19, 0.19, 0.05), 105)
+    torch.cuda.set_device(0)
+    graphs = [sg.Graph.from_coo(*big)] + [sg.Graph.from_coo(*c) for c in coo]
+    del coo, big
+    models = [("wic", 0.0)] + [(q["model"], q["p"]) for q in qs]
+    trace = serve.poisson_trace(args.requests, args.rate, 5000, models)
+    st_served, res_s = serve.run_served(graphs, trace, max_running=args.concurrency, k_cap=128)
+    st_serial, res_1 = serve.run_serial(graphs, trace)
+    same = all(np.array_equal(res_s[i][0], res_1[i][0]) and np.array_equal(res_s[i][1], res_1[i][1])
+               for i in range(len(trace)))
+    line = {"metric": "served queries/s and latency, StaticGreedy-DU (config 5)", "value": st_served["qps"],
+            "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"Poisson {args.rate}/s, {args.requests} requests, R-MAT scale {args.served_scale} "
+                                   f"(WIC) + 64 batched-recipe graphs, R in {{100,200}}, k in [10,100]",
+                       "max_running": args.concurrency,
+                       "requests_on_rmat": sum(1 for r in trace if r.graph == 0)},
+            "served": st_served, "one_query_per_launch": st_serial, "results_equal": bool(same)}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def main():
@@ -194,7 +334,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--queries", type=int, default=256, help="batched: number of queries")
+    ap.add_argument("--concurrency", type=int, default=16, help="batched/served: concurrent queries")
+    ap.add_argument("--requests", type=int, default=512, help="served: trace length")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
+    ap.add_argument("--served-scale", type=int, default=22, help="served: R-MAT scale of the large graph")
     args = ap.parse_args()
+    if args.workload == "batched" and args.impl == "ours":
+        return run_batched(args)
+    if args.workload == "served" and args.impl == "ours":
+        return run_served(args)
     wl = inputs.workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, wl)
@@ -251,10 +400,9 @@ def main():
         st_last = st
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = _barrier_and_max(float(np.sum(t_steps)), ws)
-    ms_step = total_ms / args.steps
     edges_step = float(np.mean(edges))
-    value = edges_step * ws / (ms_step / 1e3) / 1e9
+    ms_step, value = replica_throughput(np.sum(t_steps), edges_step, args.steps, ws)
+    value /= 1e9
 
     peaks, src = _peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)

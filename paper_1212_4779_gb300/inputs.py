@@ -192,6 +192,9 @@ _WORKLOAD_GRAPHS = {
     "cl15k": lambda: chung_lu_undirected(15000, 58000, 2.5, 7.7, 102),
     # directed R-MAT scale 20, 8,388,608 arcs, (0.57,0.19,0.19,0.05), seed 103
     "rmat20": lambda: rmat(20, 8388608, (0.57, 0.19, 0.19, 0.05), 103),
+    # the scale-20 recipe at scale 18 (2,097,152 arcs): a small case of the
+    # same kernels, for profiler captures
+    "rmat18": lambda: rmat(18, 2097152, (0.57, 0.19, 0.19, 0.05), 103),
     # directed R-MAT scale 22, 67,108,864 arcs, seed 105 (served graph)
     "rmat22": lambda: rmat(22, 67108864, (0.57, 0.19, 0.19, 0.05), 105),
 }
@@ -201,6 +204,7 @@ _WORKLOADS = {
     "cl15k_uic0.01": WorkloadGraph("cl15k", "uic", 0.01, 100, 50, 7),
     "cl15k_wic": WorkloadGraph("cl15k", "wic", 0.0, 100, 50, 7),
     "rmat20_wic": WorkloadGraph("rmat20", "wic", 0.0, 256, 50, 11),
+    "rmat18_wic": WorkloadGraph("rmat18", "wic", 0.0, 256, 50, 11),
 }
 
 
