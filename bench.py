@@ -42,10 +42,12 @@ from paper_1212_4779_gb300 import inputs  # noqa: E402
 METRIC = "GTEPS (snapshot-edges/s) of StaticGreedyDU k-seed selection"
 UNIT = "GTEPS"
 
-# Algorithmic bytes per expanded element (an arc of a light row or an index
-# entry of a heavy row, for one 64-bit task word): the 8-byte record read
-# plus the 8-byte state word of the neighbour.
+# Algorithmic bytes per expanded element (one arc, or one live-index entry,
+# for one 64-bit task word) plus the neighbour's 8-byte state word: an arc
+# record is 8 bytes (destination and threshold); a live-index entry (heavy
+# rows) or a cached arc is a 4-byte destination and an 8-byte live mask.
 BYTES_PER_ELEMENT = 16
+BYTES_PER_ELEMENT_INDEXED = 20
 LANES_PER_SM = 128  # INT32 lanes per SM per clock (4 SMSP x 32)
 
 
@@ -226,6 +228,7 @@ def run_batched(args):
     __graft_entry__.build()
     from paper_1212_4779_gb300 import sg
 
+    sg.sg_set_mask_cache(args.mask_cache)
     qs = inputs.batch_queries(args.queries)
     coo = _batch_graphs(qs)
     torch.cuda.set_device(0)
@@ -301,6 +304,7 @@ def run_served(args):
     __graft_entry__.build()
     from paper_1212_4779_gb300 import serve, sg
 
+    sg.sg_set_mask_cache(args.mask_cache)
     qs = inputs.batch_queries(64)
     coo = _batch_graphs(qs)
     big = inputs.rmat(args.served_scale, 16 << args.served_scale, (0.57, 0.19, 0.19, 0.05), 105)
@@ -339,6 +343,8 @@ def main():
     ap.add_argument("--requests", type=int, default=512, help="served: trace length")
     ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
     ap.add_argument("--served-scale", type=int, default=22, help="served: R-MAT scale of the large graph")
+    ap.add_argument("--mask-cache", type=int, default=0, choices=[0, 1],
+                    help="1: evaluate every arc's coins once per query into the live-mask cache")
     args = ap.parse_args()
     if args.workload == "batched" and args.impl == "ours":
         return run_batched(args)
@@ -363,6 +369,7 @@ def main():
     __graft_entry__.build()
     from paper_1212_4779_gb300 import sg
 
+    sg.sg_set_mask_cache(args.mask_cache)
     n, s, d = wl.graph()
     g = sg.Graph.from_coo(n, s, d)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -411,14 +418,15 @@ def main():
     # dense per-block arrays); algorithmic bytes = elements expanded x 16 B
     # (an 8-byte arc record or index entry plus the neighbour's 8-byte state)
     t3_ms = float(np.mean(t_t3))
-    t3_bytes = st_last["work_elems"][0][2] * BYTES_PER_ELEMENT
+    bpe = BYTES_PER_ELEMENT_INDEXED if (st_last["mask_cache"] or st_last["heavy_index"]) else BYTES_PER_ELEMENT
+    t3_bytes = st_last["work_elems"][0][2] * bpe
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = t3_bytes / (t3_ms / 1e3) / 1e9 if t3_ms > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": "coop_engine_kernel<dense> (initial gains, tier 3)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": None, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
                 "kernel_ms": t3_ms, "elements_per_launch": st_last["work_elems"][0][2],
-                "bytes_per_element": BYTES_PER_ELEMENT}
+                "bytes_per_element": bpe}
     t1_ms = float(np.mean(t_t1))
     alu_view = {"kernel": "warp_engine_kernel (initial gains, tier 1)", "kernel_ms": t1_ms,
                 "elements_per_launch": st_last["work_elems"][0][0],
@@ -438,7 +446,8 @@ def main():
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
         "config": {"workload": wl_desc(wl), "n": n, "m": int(g.m), "R": wl.R, "k": wl.k,
-                   "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
+                   "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{ws}",
+                   "mask_cache": bool(st_last["mask_cache"])},
         "snapshot_edges_per_step": edges_step,
         "phase_ms": {k: round(st_last[k], 3) for k in ("ms_index", "ms_landmarks", "ms_init_tier1", "ms_init_tier2",
                                                       "ms_init_tier3", "ms_init", "ms_fwd", "ms_rounds", "ms_total")},

@@ -82,7 +82,7 @@ typedef struct {
     int32_t status_flags;       /* nonzero: device-side check failed */
     int32_t kernel_launches;    /* kernels this call launched */
     int32_t heavy_index;        /* 1 if the heavy-row live index was used */
-    int32_t reserved;
+    int32_t mask_cache;         /* 1 if the live-mask cache was used */
     uint64_t work_keys[2][3];   /* [initial, reverse][tier 1..3]: nodes held in task tables */
     uint64_t work_elems[2][3];  /* [initial, reverse][tier 1..3]: arcs / index entries expanded */
     float ms_landmarks;         /* device time of the landmark reach sets */
@@ -120,8 +120,11 @@ sg_status sg_load_graph(int64_t n, int64_t m, const int64_t *row_ptr, const int3
 /* Degree at or above which a row gets a per-query live index in graphs
  * loaded after this call: for each such row and 64-snapshot word the
  * nonzero live masks of its arcs are computed once per query (from the
- * same hash) instead of on every expansion.  0 disables the index; the
- * default is 64.  Results do not depend on it.  Errors: SG_EINVAL if < 0. */
+ * same hash) instead of on every expansion, and the reverse pass reads the
+ * live in-arcs of such rows per snapshot.  0 disables the index; the
+ * default is 2 (every row with two or more arcs; the index is skipped when
+ * it would pass 8 GiB).  Results do not depend on it.
+ * Errors: SG_EINVAL if < 0. */
 sg_status sg_set_heavy_threshold(int32_t min_degree);
 
 /* Traversal-engine limits: a task whose visited set grows past tier1_keys
@@ -147,6 +150,17 @@ sg_status sg_set_landmarks(int32_t count);
  * snapshot's live in-arcs of a hub; 0 disables.  Results do not depend on
  * it.  Applies to later calls.  Errors: SG_EINVAL unless 0 or 1. */
 sg_status sg_set_snapshot_lists(int32_t enable);
+
+/* Live-mask cache: 1 makes each later query first evaluate every arc's coin
+ * for all R snapshots once (the hash of Section 3.1's snapshot definition,
+ * 64 snapshots per 64-bit word) into a per-workspace table of 2 x W x m
+ * words (CSR and CSC order), which the traversals then read instead of
+ * hashing in registers; 0 (the default) hashes in registers.  The table
+ * is a cache of the same function, so results do not depend on it.  It is
+ * skipped (in-register hashing) when it would pass 16 GiB.  Its bytes are
+ * included in sg_workspace_bytes while it is enabled.  Applies to later
+ * calls.  Errors: SG_EINVAL unless 0 or 1. */
+sg_status sg_set_mask_cache(int32_t enable);
 
 /* Same as sg_load_graph from an arc list src[i] -> dst[i], i < m.
  * src/dst are host memory when is_device_ptr is 0, device memory when 1. */

@@ -33,9 +33,10 @@ void clear_error() { g_err[0] = 0; }
 
 // ------------------------------------------------------------------ memory
 int g_snapshot_lists = 1;
+int g_mask_cache = 0;
 
 namespace {
-int g_heavy_min_deg = 64;
+int g_heavy_min_deg = 2;
 sg_alloc_fn g_alloc = nullptr;
 sg_release_fn g_release = nullptr;
 void *g_alloc_ctx = nullptr;
@@ -319,6 +320,7 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.anc_list, st);
     dbuf_free(ws.anc_cnt, st);
     dbuf_free(ws.lmk_rx, st);
+    dbuf_free(ws.lmk_ux, st);
     dbuf_free(ws.lmk_U, st);
     dbuf_free(ws.lmk_H, st);
     dbuf_free(ws.lmk_E, st);
@@ -337,6 +339,10 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     ws.snbr_cap = 0;
     ws.slists_on = 0;
     ws.hw_cap = 0;
+    dbuf_free(ws.lm_out, st);
+    dbuf_free(ws.lm_in, st);
+    ws.lm_cap = 0;
+    ws.lm_on = 0;
     dbuf_free(ws.slot_vis, st);
     dbuf_free(ws.slot_qa, st);
     dbuf_free(ws.slot_touched, st);
@@ -366,7 +372,37 @@ GraphView view_of(const sg_graph *g, const sg_workspace &ws, int heavy_on)
     v.hin = HeavyView{g->hid_in.p, g->hpref_in.p, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p,
                       ws.slists_on ? ws.soff.p : nullptr, ws.snbr.p, ws.svalid.p};
     v.heavy_on = heavy_on;
+    v.lm_out = ws.lm_on ? ws.lm_out.p : nullptr;
+    v.lm_in = ws.lm_on ? ws.lm_in.p : nullptr;
     return v;
+}
+
+// The live-mask cache takes 2 x W x m x 8 bytes (both arc orders); it is
+// built while that stays within 16 GiB.
+size_t mask_cache_bytes(const sg_graph *g, int32_t W)
+{
+    return (size_t)2 * (size_t)W * (size_t)g->m * 8;
+}
+
+static bool mask_cache_fits(const sg_graph *g, int32_t W)
+{
+    return g_mask_cache && g->m > 0 && mask_cache_bytes(g, W) <= ((size_t)16 << 30);
+}
+
+sg_status ensure_mask_cache(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st)
+{
+    ws.lm_on = 0;
+    if (!mask_cache_fits(g, W)) return SG_OK;
+    if (ws.lm_cap < W) {
+        dbuf_free(ws.lm_out, st);
+        dbuf_free(ws.lm_in, st);
+        ws.lm_cap = 0;
+        SG_TRY(dbuf_alloc(ws.lm_out, (size_t)W * (size_t)g->m, st));
+        SG_TRY(dbuf_alloc(ws.lm_in, (size_t)W * (size_t)g->m, st));
+        ws.lm_cap = W;
+    }
+    ws.lm_on = 1;
+    return SG_OK;
 }
 
 // The heavy-row index reserves (sum of heavy degrees) x W entries of 12 B
@@ -436,7 +472,7 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
     b += 4 * nw * 64;                                  // per-snapshot targets
     b += (8 + 8 + 4) * W64 + 4 * (size_t)W;            // offsets, counts
     b += 8 * nw + 4 * nw + 4 * (size_t)W;              // ancestors
-    b += 8 * nw * 8 + (W64 << 8) * (4 + 4 + 8 + 8);    // landmarks
+    b += 2 * 8 * nw * 8 + (W64 << 8) * (4 + 4 + 8 + 8);  // landmarks
     int qcap = 1;
     while ((size_t)qcap < n) qcap <<= 1;
     const size_t per_slot = n * 20 + (size_t)qcap * 4;
@@ -448,6 +484,7 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
         const size_t nq = (size_t)g->nh_in * W64 + 1;
         b += nq * 16 + ((size_t)1 << 20) * 4 + (size_t)(1.5 * 64.0 * W * (double)g->nh_in) * 4;
     }
+    if (mask_cache_fits(g, W)) b += mask_cache_bytes(g, W);
     return b;
 }
 
@@ -477,6 +514,7 @@ sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, 
         SG_TRY(dbuf_alloc(ws.anc_list, nw, st));
         SG_TRY(dbuf_alloc(ws.anc_cnt, (size_t)W, st));
         SG_TRY(dbuf_alloc(ws.lmk_rx, nw * 8, st));
+        SG_TRY(dbuf_alloc(ws.lmk_ux, nw * 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_U, ((size_t)64 * W) << 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_H, ((size_t)64 * W) << 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_E, ((size_t)64 * W) << 8, st));
@@ -640,6 +678,16 @@ sg_status sg_set_snapshot_lists(int32_t enable)
         return SG_EINVAL;
     }
     g_snapshot_lists = enable;
+    return SG_OK;
+}
+
+sg_status sg_set_mask_cache(int32_t enable)
+{
+    if (enable != 0 && enable != 1) {
+        set_error("mask cache switch must be 0 or 1");
+        return SG_EINVAL;
+    }
+    g_mask_cache = enable;
     return SG_OK;
 }
 
@@ -809,6 +857,7 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
     ws.slists_on = 0;
     if (heavy_on && g_snapshot_lists) SG_TRY(ensure_snapshot_lists(g, ws, co, c.p, model, st));
+    SG_TRY(ensure_mask_cache(g, ws, co.W, st));
     if (prepare_only) return SG_OK;
     // events: 0 start, 1 after index, 2 after init tier 1, 3 after init,
     // 4 end; per round: after forward update
@@ -846,6 +895,7 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) SG_TRY(run_heavy_index(g, ws, co, model, st));
     if (ws.slists_on) SG_TRY(run_snapshot_lists(g, ws, co, st));
+    if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_index, st));
     SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st, stats ? &tev : nullptr));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_init, st));
@@ -876,6 +926,7 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
         stats->status_flags = h.flags;
         stats->kernel_launches = g_launches - launches0;
         stats->heavy_index = heavy_on;
+        stats->mask_cache = ws.lm_on;
         memcpy(stats->work_keys, h.work_keys, sizeof(h.work_keys));
         memcpy(stats->work_elems, h.work_elems, sizeof(h.work_elems));
         cudaEventElapsedTime(&stats->ms_index, e_start, e_index);
@@ -1016,9 +1067,11 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
     ws.slists_on = 0;
+    SG_TRY(ensure_mask_cache(g, ws, co.W, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) SG_TRY(run_heavy_index(g, ws, co, model, st));
+    if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));
     if (init_edges) {

@@ -23,6 +23,9 @@
 //   tl    int32[W][64n]   newly covered nodes of the round, per snapshot,
 //                         minus those that reach the round's seed
 //   anc   uint64[W][n]    bit b: the node reaches the round's seed in snapshot 64w+b
+//   lm_out / lm_in uint64[W][m]  optional live-mask cache: the live bits of
+//                         every arc for each 64-snapshot word, in CSR and in
+//                         CSC order (built once per query from the hash)
 //   heavy live index, per direction: for heavy row h and word w the
 //     nonzero 64-snapshot live masks of its arcs, compacted in arc order:
 //     hcnt[h*W+w] entries at hnbr/hmask[hpref[h]*W + w*deg(h) ...]
@@ -127,6 +130,11 @@ struct GraphView {
     HeavyView hout;  // heavy CSR rows (forward traversals)
     HeavyView hin;   // heavy CSC rows (reverse traversals)
     int32_t heavy_on;
+    // live-mask cache (null when off): lm_out[w*m + e] = live bits of arc e
+    // (CSR position) in snapshots 64w..64w+63; lm_in[w*m + j] the same for
+    // the arc at CSC position j
+    const unsigned long long *lm_out;
+    const unsigned long long *lm_in;
 };
 
 // Counters kept on the device during one call (zeroed at the start).
@@ -170,7 +178,8 @@ struct sg_workspace {
     sgi::DBuf<unsigned long long> anc;   // [W][n] ancestors of the round's seed, per snapshot bit
     sgi::DBuf<int32_t> anc_list;         // [W][n] nodes with ancestor bits set
     sgi::DBuf<int32_t> anc_cnt;          // [W]
-    sgi::DBuf<unsigned long long> lmk_rx;    // [K][W][n] landmark reach bits
+    sgi::DBuf<unsigned long long> lmk_rx;    // [W][n][8] landmark reach bits (R(x_i) membership)
+    sgi::DBuf<unsigned long long> lmk_ux;    // [W][n][8] ... and which landmarks the node reaches
     sgi::DBuf<int32_t> lmk_U, lmk_H;         // [64W << K] union sizes / membership histogram
     sgi::DBuf<unsigned long long> lmk_E, lmk_HE;  // ... their out-degree sums
     sgi::DBuf<unsigned long long> slot_vis;  // tier-3 slots: [slot][n][2] visited / pending words
@@ -191,6 +200,10 @@ struct sg_workspace {
     sgi::DBuf<long long> scan_tmp;
     size_t soff_cap = 0, snbr_cap = 0;
     int32_t slists_on = 0;    // built for the current query
+    // live-mask cache, [W][m] per direction (optional)
+    sgi::DBuf<unsigned long long> lm_out, lm_in;
+    int32_t lm_cap = 0;       // words the cache was sized for
+    int32_t lm_on = 0;        // built for the current query
     int32_t kcap = 0;
     int32_t am_blocks = 0;
 };
@@ -235,10 +248,15 @@ extern int g_tier_limit[2];
 extern int g_landmarks;
 // per-snapshot live in-lists of heavy rows for the reverse update (0 or 1)
 extern int g_snapshot_lists;
+// nonzero: queries build and use the live-mask cache when it fits
+extern int g_mask_cache;
 
 // kernels (sg_kernels.cu)
 sg_status run_heavy_index(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
 sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
+sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
+sg_status ensure_mask_cache(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st);
+size_t mask_cache_bytes(const sg_graph *g, int32_t W);
 sg_status ensure_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model,
                                 cudaStream_t st);
 // events recorded around the initial-gain tier launches (any may be null)

@@ -167,6 +167,15 @@ __device__ __forceinline__ uint64_t elem(const GraphView &g, const Coins &co, lo
         y = __ldg(hv.snbr + base + j);
         return F;
     }
+    const unsigned long long *lm = DIR == DIR_FWD ? g.lm_out : g.lm_in;
+    if (!heavy && lm) {
+        // cached live bits of the arc at this CSR / CSC position
+        const long long q = base + j;
+        y = DIR == DIR_FWD ? __ldg(g.col + q) : __ldg(&g.cin[q].x);
+        const uint64_t mk = __ldg(lm + (long long)(rs >> 6) * g.m + q);
+        if (SLICE == SLICE_SNAP) return mk & F;
+        return ((mk >> (rs & 63u)) & 1ull) ? F : 0ull;
+    }
     if (heavy) {
         const long long q = base + j;
         y = __ldg(hv.hnbr + q);
@@ -214,12 +223,14 @@ struct EngineArgs {
     const long long *coff;  // [64W+1] chunk-task offsets
     int32_t *list1, *list2;
     const unsigned long long *anc;  // [W][n] ancestors of v*, per snapshot bit (this round)
-    // landmarks x_0..x_{K-1} (initial gains): bit b of lmk_rx[(i*W + w)*n + y]
-    // = y in R(G'_{64w+b}, x_i); lmk_U / lmk_E [(r << K) + I]: the size of the
+    // landmarks x_0..x_{K-1} (initial gains), 8 words per (w, y) side by side:
+    // bit b of lmk_rx[((w*n + y) << 3) + i] = y in R(G'_{64w+b}, x_i), bit b
+    // of lmk_ux[...] = y reaches x_i in G'_{64w+b}; lmk_U / lmk_E [(r << K) + I]: the size of the
     // union over i in I of R(G'_r, x_i), and the out-degree sum over it
     int lmk_k;
     int lmk_x[MAX_LMK];
     const unsigned long long *lmk_rx;
+    const unsigned long long *lmk_ux;
     const int32_t *lmk_U;
     const unsigned long long *lmk_E;
     long long ntasks;       // TASK_INIT: n * W
@@ -227,35 +238,40 @@ struct EngineArgs {
 };
 
 
-// Initial gains with landmarks x_i: a task that reaches x_i in snapshot r
-// gets all of R(G'_r, x_i) at once -- at the end it adds the size of the
-// union of the landmark sets it reached in each snapshot -- so bits of such
-// snapshots need not travel inside those sets.  lmk_filter returns the bits
-// of ml that still have to be recorded at y; bits reaching a landmark itself
-// are recorded in xbits[i].  Bits that arrived before the landmark did are
-// masked out at the end (lmk_effective).
-__device__ __forceinline__ const unsigned long long *lmk_bits(const EngineArgs &a, int i, int word)
+// Initial gains with landmarks x_i.  A task from v reaches x_i in snapshot
+// r exactly when v does (v in U(G'_r, x_i), one reverse walk per landmark),
+// and then R(G'_r, v) contains all of R(G'_r, x_i): the task starts with
+// xbits[i] = those snapshots, is credited at the end with the size of the
+// union of the reached landmarks' sets, and its bits of such snapshots need
+// not travel inside those sets (every node reached through a node of the
+// union is in the union).  lmk_filter returns the bits of ml that still
+// have to be recorded at y; xany = OR of xbits.  The seed's own bits inside
+// the union are masked out at the end (lmk_effective).
+__device__ __forceinline__ const unsigned long long *lmk_bits(const unsigned long long *base, const EngineArgs &a,
+                                                              int word, int y)
 {
-    return a.lmk_rx + ((size_t)i * a.co.W + word) * (size_t)a.g.n;
+    return base + (((size_t)word * (size_t)a.g.n + (size_t)y) << 3);
 }
 
 __device__ __forceinline__ uint64_t lmk_filter(const EngineArgs &a, int word, int y, uint64_t ml,
-                                               unsigned long long *xbits)
+                                               const unsigned long long *xbits, uint64_t xany)
 {
-#pragma unroll
-    for (int i = 0; i < MAX_LMK; ++i)
-        if (i < a.lmk_k && y == a.lmk_x[i]) {
-            atomicOr(&xbits[i], (unsigned long long)ml);
-            return 0;
-        }
+    if (!(ml & xany)) return ml;
+    const unsigned long long *p = lmk_bits(a.lmk_rx, a, word, y);
     uint64_t drop = 0;
 #pragma unroll
     for (int i = 0; i < MAX_LMK; ++i) {
         if (i >= a.lmk_k) break;
-        const uint64_t xb = *(volatile unsigned long long *)&xbits[i];
-        if (xb & ml) drop |= __ldg(lmk_bits(a, i, word) + y) & xb;
+        const uint64_t xb = xbits[i];
+        if (xb & ml) drop |= __ldg(p + i) & xb;
     }
     return ml & ~drop;
+}
+
+// Snapshots of word `word` in which node v reaches landmark i.
+__device__ __forceinline__ uint64_t lmk_reaches(const EngineArgs &a, int word, int v, int i)
+{
+    return __ldg(lmk_bits(a.lmk_ux, a, word, v) + i);
 }
 
 // State bits of a finished initial-gain task that count at u: those not
@@ -267,7 +283,7 @@ __device__ __forceinline__ uint64_t lmk_effective(const EngineArgs &a, int word,
 #pragma unroll
     for (int i = 0; i < MAX_LMK; ++i) {
         if (i >= a.lmk_k) break;
-        if (xb[i]) drop |= __ldg(lmk_bits(a, i, word) + u) & xb[i];
+        if (xb[i]) drop |= __ldg(lmk_bits(a.lmk_rx, a, word, u) + i) & xb[i];
     }
     return vis & ~drop;
 }
@@ -395,7 +411,8 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
             }
             return false;
         }
-        if (lane < MAX_LMK) T.xbits[lane] = 0;
+        if (lane < MAX_LMK)
+            T.xbits[lane] = lane < a.lmk_k ? lmk_reaches(a, word, x0, lane) & word_mask(word, co.R) : 0ull;
         if (lane == 0) {
             const uint64_t M0 = word_mask(word, co.R);
             const uint32_t h = slot_of<LOGC>(x0);
@@ -425,6 +442,9 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         }
     }
     __syncwarp();
+    uint64_t xany = 0;  // snapshots credited through some landmark (fixed for the task)
+    if (TASK == TASK_INIT)
+        for (int i = 0; i < a.lmk_k; ++i) xany |= T.xbits[i];
     unsigned long long tedges = 0;
     int qhead = 0;
     while (true) {
@@ -479,7 +499,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
                 // nodes reaching v* in this snapshot were settled by the ancestor pass
                 if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                     ml = 0;
-                if (TASK == TASK_INIT && ml && a.lmk_k > 0) ml = lmk_filter(a, word, y, ml, T.xbits);
+                if (TASK == TASK_INIT) ml = lmk_filter(a, word, y, ml, T.xbits, xany);
                 if (ml) {
                     const int h = table_slot<LOGC>(T, y, LIMIT);
                     if (h >= 0) {
@@ -679,6 +699,8 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                         const int32_t *tgt, int ntgt, const int *ncov, CtaShared &S)
 {
     constexpr int SLICE = TASK == TASK_REVT ? SLICE_TGT : SLICE_SNAP;
+    // landmark walks write one word of each node's 8-word landmark record
+    constexpr size_t VS = TASK == TASK_LMK ? (size_t)MAX_LMK : 1;
     const GraphView &g = a.g;
     const Coins &co = a.co;
     const int tid = threadIdx.x;
@@ -706,7 +728,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
         uint64_t M = M0;
         if (TASK == TASK_FWD || TASK == TASK_LMK) {
             M &= w.gm;
-            M &= ~atomicOr(&w.vis[x0], (unsigned long long)M);
+            M &= ~atomicOr(&w.vis[(size_t)x0 * VS], (unsigned long long)M);
             if (M) {
                 atomicOr(&w.pend[x0], (unsigned long long)M);
                 w.qa[0] = x0;
@@ -767,7 +789,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                     if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                         ml = 0;
                     if (ml) {
-                        const uint64_t old = atomicOr(&w.vis[y], (unsigned long long)ml);
+                        const uint64_t old = atomicOr(&w.vis[(size_t)y * VS], (unsigned long long)ml);
                         const uint64_t nw = ml & ~old;
                         if (nw) {
                             if (TASK == TASK_INIT) cnt += __popcll(nw);
@@ -1015,6 +1037,9 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
     const int lane = threadIdx.x & 31;
     unsigned long long tedges = 0;
     long long idle = 0;
+    uint64_t xany = 0;  // snapshots credited through some landmark (fixed for the task)
+    if (TASK == TASK_INIT)
+        for (int i = 0; i < a.lmk_k; ++i) xany |= c.xbits[i];
     while (true) {
         int nb = 0, qb = 0;
         if (lane == 0) {
@@ -1107,7 +1132,7 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                 uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y);
                 if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                     ml = 0;
-                if (TASK == TASK_INIT && ml && a.lmk_k > 0) ml = lmk_filter(a, word, y, ml, c.xbits);
+                if (TASK == TASK_INIT) ml = lmk_filter(a, word, y, ml, c.xbits, xany);
                 if (ml) {
                     const int idx = T.slot(y, limit, c);
                     if (idx >= 0) {
@@ -1185,13 +1210,14 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
             c.nkeys = 0;
             c.overflow = 0;
             c.err = 0;
-            for (int i = 0; i < MAX_LMK; ++i) c.xbits[i] = 0;
         }
         __syncthreads();
         if (TASK == TASK_INIT) {
             x0 = (int)(t / a.co.W);
             word = (int)(t - (long long)x0 * a.co.W);
             rs = (uint32_t)word * 64u;
+            if (tid < MAX_LMK)
+                c.xbits[tid] = tid < a.lmk_k ? lmk_reaches(a, word, x0, tid) & word_mask(word, a.co.R) : 0ull;
             if (tid == 0) coop_seed<TAB>(T, c, x0, word_mask(word, a.co.R), limit);
         } else {
             const int r = find_off(a.coff, 64 * a.co.W, t);
@@ -1466,14 +1492,16 @@ __global__ void __launch_bounds__(BT) fwd_post_kernel(EngineArgs a, FwdArgs f)
 
 
 // Landmark reach sets (initial gains).  landmark_walk_kernel: block
-// (word, group) walks from landmark i over the live arcs of the snapshots it
-// owns into that landmark's reach bits (zero on entry).
+// (word, group) walks from landmark i over the live arcs (DIR_FWD) or the
+// reversed live arcs (DIR_REV) of the snapshots it owns, into word i of
+// every node's landmark record (zero on entry): R(G'_r, x_i) into rx,
+// U(G'_r, x_i) into ux.
 struct LmkArgs {
-    unsigned long long *rx, *pendf, *E, *HE;
+    unsigned long long *rx, *ux, *pendf, *E, *HE;
     int32_t *fq_a, *fq_b, *U, *H;
 };
 
-template <int MODEL>
+template <int DIR, int MODEL>
 __global__ void __launch_bounds__(BT) landmark_walk_kernel(EngineArgs a, LmkArgs l, int i)
 {
     __shared__ CtaShared S;
@@ -1483,7 +1511,7 @@ __global__ void __launch_bounds__(BT) landmark_walk_kernel(EngineArgs a, LmkArgs
     constexpr int GB = 64 / FWD_GROUPS;
     const size_t qo = (size_t)blockIdx.x * (size_t)n;
     CtaState w;
-    w.vis = l.rx + ((size_t)i * a.co.W + word) * (size_t)n;
+    w.vis = (DIR == DIR_FWD ? l.rx : l.ux) + (((size_t)word * (size_t)n) << 3) + i;
     w.pend = l.pendf + (size_t)word * (size_t)n;
     w.qa = l.fq_a + qo;
     w.qb = l.fq_b + qo;
@@ -1492,7 +1520,23 @@ __global__ void __launch_bounds__(BT) landmark_walk_kernel(EngineArgs a, LmkArgs
     w.du_x = nullptr;
     w.ndu = nullptr;
     w.gm = (GB == 64 ? ~0ull : ((1ull << GB) - 1ull)) << (grp * GB);
-    cta_bfs<DIR_FWD, MODEL, TASK_LMK>(a, w, a.lmk_x[i], word_mask(word, a.co.R), word, (uint32_t)word * 64u, nullptr,
+    // In a snapshot where x_i and an earlier landmark x_j reach each other
+    // (one strongly connected component), R(x_i) = R(x_j) and U(x_i) =
+    // U(x_j): copy those bits of word j instead of walking them.
+    uint64_t M = word_mask(word, a.co.R) & w.gm;
+    const unsigned long long *ri = l.rx + (((size_t)word * (size_t)n + (size_t)a.lmk_x[i]) << 3);
+    const unsigned long long *ui = l.ux + (((size_t)word * (size_t)n + (size_t)a.lmk_x[i]) << 3);
+    for (int j = 0; j < i && M; ++j) {
+        const uint64_t same = M & ri[j] & ui[j];
+        if (!same) continue;
+        M &= ~same;
+        unsigned long long *base = (DIR == DIR_FWD ? l.rx : l.ux) + (((size_t)word * (size_t)n) << 3);
+        for (int y = threadIdx.x; y < n; y += BT) {
+            const uint64_t v = base[((size_t)y << 3) + j] & same;
+            if (v) atomicOr(&base[((size_t)y << 3) + i], (unsigned long long)v);
+        }
+    }
+    cta_bfs<DIR, MODEL, TASK_LMK>(a, w, a.lmk_x[i], M, word, (uint32_t)word * 64u, nullptr,
                                       0, nullptr, S);
 }
 
@@ -1510,8 +1554,9 @@ __global__ void __launch_bounds__(256) landmark_hist_kernel(EngineArgs a, LmkArg
         uint64_t rx[MAX_LMK];
         uint64_t any = 0;
 #pragma unroll
+        const unsigned long long *rec = l.rx + (((size_t)word * (size_t)n + (size_t)y) << 3);
         for (int i = 0; i < MAX_LMK; ++i) {
-            rx[i] = i < K ? l.rx[((size_t)i * W + word) * (size_t)n + y] : 0ull;
+            rx[i] = i < K ? rec[i] : 0ull;
             any |= rx[i];
         }
         if (!any) continue;
@@ -1841,6 +1886,37 @@ __global__ void live_masks_kernel(Coins co, long long m, const uint2 *fw, uint32
     }
 }
 
+// ========================================================= live-mask cache
+
+// lm_out[w*m + e] = live bits of arc e in the snapshots of word w.
+template <int MODEL>
+__global__ void __launch_bounds__(256) mask_cache_kernel(Coins co, long long m, const uint2 *fw,
+                                                         unsigned long long *lm_out)
+{
+    const long long total = m * co.W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int word = (int)(i / m);
+        const long long e = i - (long long)word * m;
+        const uint32_t tm1 = MODEL == MODEL_WIC ? __ldg(&fw[e].y) : co.uic_tm1;
+        lm_out[i] = live_bits(co, (uint32_t)e, (uint32_t)word * 64u, word_mask(word, co.R), tm1);
+    }
+}
+
+// lm_in[w*m + j] = lm_out[w*m + eid(j)] for CSC position j.
+__global__ void __launch_bounds__(256) mask_cache_csc_kernel(int W, long long m, const int2 *cin,
+                                                             const unsigned long long *lm_out,
+                                                             unsigned long long *lm_in)
+{
+    const long long total = m * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int word = (int)(i / m);
+        const long long j = i - (long long)word * m;
+        lm_in[i] = __ldg(lm_out + (long long)word * m + __ldg(&cin[j].y));
+    }
+}
+
 // ================================================================ launches
 
 EngineArgs engine_args(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy_on)
@@ -1860,6 +1936,7 @@ EngineArgs engine_args(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
     a.lmk_k = 0;
     for (int i = 0; i < MAX_LMK; ++i) a.lmk_x[i] = -1;
     a.lmk_rx = ws.lmk_rx.p;
+    a.lmk_ux = ws.lmk_ux.p;
     a.lmk_U = ws.lmk_U.p;
     a.lmk_E = ws.lmk_E.p;
     a.ntasks = 0;
@@ -1942,9 +2019,11 @@ sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
         a.lmk_k = K;
         for (int i = 0; i < K; ++i) a.lmk_x[i] = g->lmk_nodes[i];
         const size_t nw = (size_t)g->n * co.W;
-        SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_rx.p, 0, (size_t)K * nw * 8, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_rx.p, 0, nw * 8 * MAX_LMK, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_ux.p, 0, nw * 8 * MAX_LMK, st));
         LmkArgs l;
         l.rx = ws.lmk_rx.p;
+        l.ux = ws.lmk_ux.p;
         l.pendf = ws.pendf.p;
         l.fq_a = ws.fq_a.p;
         l.fq_b = ws.fq_b.p;
@@ -1953,7 +2032,9 @@ sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
         l.H = ws.lmk_H.p;
         l.HE = ws.lmk_HE.p;
         for (int i = 0; i < K; ++i) {
-            landmark_walk_kernel<MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, l, i);
+            landmark_walk_kernel<DIR_FWD, MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, l, i);
+            SG_CUDA_TRY(cudaGetLastError());
+            landmark_walk_kernel<DIR_REV, MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, l, i);
             SG_CUDA_TRY(cudaGetLastError());
         }
         const size_t nq = ((size_t)64 * co.W) << K;
@@ -1964,7 +2045,7 @@ sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
         SG_CUDA_TRY(cudaGetLastError());
         landmark_union_kernel<<<64 * co.W, 1 << MAX_LMK, 0, st>>>(K, l);
         SG_CUDA_TRY(cudaGetLastError());
-        g_launches += K + 2;
+        g_launches += 2 * K + 2;
     }
     return launch_tiers<DIR_FWD, MODEL, TASK_INIT>(g, ws, a, st, ev);
 }
@@ -2018,6 +2099,22 @@ sg_status run_heavy_index(sg_graph *g, sg_workspace &ws, const Coins &co, int mo
     }
     SG_TRY((launch_index<DIR_FWD, MODEL_UIC>(g, ws, co, st)));
     return launch_index<DIR_REV, MODEL_UIC>(g, ws, co, st);
+}
+
+sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st)
+{
+    const long long total = g->m * co.W;
+    if (total == 0) return SG_OK;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)g->num_sms * 16);
+    if (model == MODEL_WIC)
+        mask_cache_kernel<MODEL_WIC><<<blocks, 256, 0, st>>>(co, g->m, g->fw.p, ws.lm_out.p);
+    else
+        mask_cache_kernel<MODEL_UIC><<<blocks, 256, 0, st>>>(co, g->m, g->fw.p, ws.lm_out.p);
+    SG_CUDA_TRY(cudaGetLastError());
+    mask_cache_csc_kernel<<<blocks, 256, 0, st>>>(co.W, g->m, g->cin.p, ws.lm_out.p, ws.lm_in.p);
+    SG_CUDA_TRY(cudaGetLastError());
+    g_launches += 2;
+    return SG_OK;
 }
 
 sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st)

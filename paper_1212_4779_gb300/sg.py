@@ -31,7 +31,7 @@ EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg
            "sg_batch_capture", "sg_batch_launch", "sg_batch_free", "sg_server_create", "sg_server_submit",
            "sg_server_poll", "sg_server_counts", "sg_server_destroy",
            "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-           "sg_set_snapshot_lists", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+           "sg_set_snapshot_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
            "sg_init_gains", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
 
 
@@ -53,7 +53,7 @@ class sg_stats(ctypes.Structure):
                 ("ms_index", ctypes.c_float), ("ms_init", ctypes.c_float), ("ms_init_tier1", ctypes.c_float),
                 ("ms_rounds", ctypes.c_float), ("ms_fwd", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("status_flags", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("heavy_index", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("heavy_index", ctypes.c_int32), ("mask_cache", ctypes.c_int32),
                 ("work_keys", (ctypes.c_uint64 * 3) * 2), ("work_elems", (ctypes.c_uint64 * 3) * 2),
                 ("ms_landmarks", ctypes.c_float), ("ms_init_tier2", ctypes.c_float),
                 ("ms_init_tier3", ctypes.c_float), ("reserved2", ctypes.c_int32)]
@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
         L.sg_set_engine_limits.argtypes = [i32, i32]
         L.sg_set_landmarks.argtypes = [i32]
         L.sg_set_snapshot_lists.argtypes = [i32]
+        L.sg_set_mask_cache.argtypes = [i32]
         L.sg_argmax_noalloc.argtypes = [P, i64, P, P, P]
         L.sg_load_graph.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_load_graph_coo.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
@@ -135,7 +136,7 @@ def lib() -> ctypes.CDLL:
         for name in ("sg_workspace_create", "sg_workspace_bytes", "sg_select_ws", "sg_select_batch",
                      "sg_batch_capture", "sg_batch_launch", "sg_server_create", "sg_server_submit",
                      "sg_server_poll", "sg_server_counts", "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-                     "sg_set_snapshot_lists", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+                     "sg_set_snapshot_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
                      "sg_init_gains", "sg_live_masks", "sg_graph_csr"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -255,6 +256,12 @@ def sg_set_engine_limits(tier1_keys: int = 256, tier2_keys: int = 4096):
 def sg_set_snapshot_lists(enable: int = 1):
     """Per-snapshot live in-lists of heavy rows for the reverse pass (0: off)."""
     _check(lib().sg_set_snapshot_lists(int(enable)))
+
+
+def sg_set_mask_cache(enable: int = 0):
+    """Live-mask cache: evaluate every arc's coins once per query (1) or hash
+    in registers during the traversals (0, the default)."""
+    _check(lib().sg_set_mask_cache(int(enable)))
 
 
 def sg_argmax_noalloc(s, out_id, out_gain, stream=None):

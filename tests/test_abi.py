@@ -74,3 +74,18 @@ def test_invalid_arguments_are_rejected_without_gpu(libpath):
     assert L.sg_graph_info(None, None, None) == sg.SG_EINVAL
     assert L.sg_select(None, 10, 1, sg.sg_cascade(0, 0.1), 1, None, None, None, None) == sg.SG_EINVAL
     L.sg_free_graph(None)
+
+
+def test_setters_validate_without_gpu(libpath):
+    from paper_1212_4779_gb300 import sg
+
+    L = sg.lib()
+    assert L.sg_set_mask_cache(2) == sg.SG_EINVAL
+    assert L.sg_set_mask_cache(-1) == sg.SG_EINVAL
+    assert L.sg_set_snapshot_lists(3) == sg.SG_EINVAL
+    assert L.sg_set_landmarks(9) == sg.SG_EINVAL
+    assert L.sg_set_heavy_threshold(-1) == sg.SG_EINVAL
+    assert L.sg_set_mask_cache(0) == sg.SG_OK
+    assert L.sg_set_snapshot_lists(1) == sg.SG_OK
+    assert L.sg_set_landmarks(8) == sg.SG_OK
+    assert L.sg_set_heavy_threshold(2) == sg.SG_OK

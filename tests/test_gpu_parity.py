@@ -100,15 +100,19 @@ def test_init_gains_match_oracle(sg, name, R):
     assert ed == ed_want
 
 
-def test_big_tasks_take_the_upper_tiers_and_agree(sg):
+@pytest.mark.parametrize("lmk", [0, 8])
+def test_big_tasks_take_the_upper_tiers_and_agree(sg, limits, lmk):
     """High-probability cascade: most sources reach hundreds of nodes per
-    64-snapshot word, so the shared-memory warp tables overflow and tasks
-    move to the global-table tier."""
+    64-snapshot word, so without landmarks the shared-memory warp tables
+    overflow and tasks move to the upper tiers; with landmarks the sources
+    are credited with the giant component's reach and stay small."""
     n, s, d = inputs.chung_lu_undirected(3000, 12000, 2.5, 8.0, 31)
     g, o = _both(sg, n, s, d, "uic", 0.3)
+    sg.sg_set_landmarks(lmk)
     res = g.select(96, 8, "uic", 0.3, 4, stats=True)
     ref = o.select(96, 8, 4, mode=oracle.DU)
-    assert res.stats["init_tier2_tasks"] > 0
+    if lmk == 0:
+        assert res.stats["init_tier2_tasks"] > 0
     assert np.array_equal(res.seeds, ref["seeds"])
     assert np.array_equal(res.gains, ref["gains"])
     assert [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]] == list(map(int, ref["counters"]))
@@ -118,9 +122,43 @@ def test_big_tasks_take_the_upper_tiers_and_agree(sg):
 def limits(sg):
     yield sg.sg_set_engine_limits
     sg.sg_set_engine_limits(256, 4096)
-    sg.sg_set_heavy_threshold(64)
+    sg.sg_set_heavy_threshold(2)
     sg.sg_set_landmarks(8)
     sg.sg_set_snapshot_lists(1)
+    sg.sg_set_mask_cache(0)
+
+
+@pytest.mark.parametrize("heavy", [0, 2])
+@pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01", "er2k_uic0.1"])
+def test_mask_cache_gives_identical_results(sg, limits, name, heavy):
+    """The live-mask cache holds the same coins, evaluated once per query:
+    identical initial gains, seeds, gains and counters in every tier, with
+    and without the heavy-row index on top of it."""
+    wl = inputs.workload(name)
+    n, s, d = wl.graph()
+    sg.sg_set_heavy_threshold(heavy)
+    g, o = _both(sg, n, s, d, wl.model, wl.p)
+    sg.sg_set_mask_cache(1)
+    ref = o.select(wl.R, 10, wl.seed, mode=oracle.DU, want_init=True)
+    for t1, t2 in [(256, 4096), (2, 16)]:
+        limits(t1, t2)
+        s_gpu, ed = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
+        assert np.array_equal(s_gpu, ref["s_init"]) and ed == int(ref["counters"][0])
+        res = g.select(wl.R, 10, wl.model, wl.p, wl.seed, stats=True)
+        assert res.stats["mask_cache"] == 1
+        assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+        got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+        assert got == [int(x) for x in ref["counters"]]
+
+
+def test_mask_cache_bytes_are_reported(sg, limits):
+    wl = inputs.workload("cl15k_wic")
+    n, s, d = wl.graph()
+    g = sg.Graph.from_coo(n, s, d)
+    off = sg.sg_workspace_bytes(g.handle, 128, 10)
+    sg.sg_set_mask_cache(1)
+    on = sg.sg_workspace_bytes(g.handle, 128, 10)
+    assert on - off == 2 * 2 * g.m * 8
 
 
 @pytest.mark.parametrize("lists", [0, 1])
@@ -228,6 +266,30 @@ def test_giant_component_reaches_tier3_and_agrees(sg, limits):
         assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
         got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
         assert got == [int(x) for x in ref["counters"]]
+
+
+@pytest.mark.parametrize("t1,t2", [(256, 4096), (2, 16)])
+def test_landmark_credit_in_a_giant_component(sg, limits, t1, t2):
+    """UIC 0.05 on a Chung-Lu graph with a giant component (about 1,000
+    nodes per snapshot): sources that reach a landmark are credited with its
+    reach set from the start and stop at its boundary.  Results equal the
+    oracle with 0, 1 and 8 landmarks, and the landmarks remove most of the
+    traversal."""
+    n, s, d = inputs.chung_lu_undirected(4000, 30000, 2.5, 15.0, 77)
+    g, o = _both(sg, n, s, d, "uic", 0.05)
+    ref = o.select(128, 8, 99, mode=oracle.DU, want_init=True)
+    limits(t1, t2)
+    elems = {}
+    for lmk in (0, 1, 8):
+        sg.sg_set_landmarks(lmk)
+        s_gpu, ed = g.init_gains(128, "uic", 0.05, 99)
+        assert np.array_equal(s_gpu, ref["s_init"]) and ed == int(ref["counters"][0])
+        res = g.select(128, 8, "uic", 0.05, 99, stats=True)
+        assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+        got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+        assert got == [int(x) for x in ref["counters"]]
+        elems[lmk] = sum(res.stats["work_elems"][0])
+    assert elems[8] < 0.5 * elems[0], elems
 
 
 # ---------------------------------------------------------- full selection
@@ -352,6 +414,27 @@ def test_rmat20_gains_are_exact_marginals(sg, rmat20):
         assert f == int(gains[:i].sum()), i
         prev = f
     assert prev == int(gains.sum())
+
+
+def test_rmat20_mask_cache_equals_in_register_coins(sg, rmat20):
+    """Full size: the live-mask cache gives the same seeds, gains and
+    counters as in-register hashing (which the tests above tie to the
+    oracle), and the same initial gains on a sample checked against the
+    oracle."""
+    wl, g, o, res = rmat20
+    sg.sg_set_mask_cache(1)
+    try:
+        r2 = g.select(wl.R, wl.k, wl.model, wl.p, wl.seed, stats=True)
+        s_gpu, _ = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
+    finally:
+        sg.sg_set_mask_cache(0)
+    assert r2.stats["mask_cache"] == 1 and r2.stats["status_flags"] == 0
+    assert np.array_equal(r2.seeds, res.seeds) and np.array_equal(r2.gains, res.gains)
+    for key in ("init_edges", "fwd_edges", "rev_edges"):
+        assert r2.stats[key] == res.stats[key]
+    sample = np.unique(np.r_[np.random.default_rng(21).choice(g.n, 32, replace=False), res.seeds[:4]]).astype(np.int32)
+    want, _ = o.reach_sums(wl.R, wl.seed, sample)
+    assert np.array_equal(s_gpu[sample], want)
 
 
 def test_rmat20_greedy_choice_beats_sampled_candidates(sg, rmat20):
