@@ -342,6 +342,9 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.lm_out, st);
     dbuf_free(ws.lm_in, st);
     ws.lm_cap = 0;
+    dbuf_free(ws.rdesc, st);
+    ws.rd_cap = 0;
+    ws.rd_on = 0;
     ws.lm_on = 0;
     dbuf_free(ws.slot_vis, st);
     dbuf_free(ws.slot_qa, st);
@@ -374,6 +377,7 @@ GraphView view_of(const sg_graph *g, const sg_workspace &ws, int heavy_on)
     v.heavy_on = heavy_on;
     v.lm_out = ws.lm_on ? ws.lm_out.p : nullptr;
     v.lm_in = ws.lm_on ? ws.lm_in.p : nullptr;
+    v.rdesc = (heavy_on && ws.rd_on) ? ws.rdesc.p : nullptr;
     return v;
 }
 
@@ -416,6 +420,13 @@ bool heavy_index_enabled(const sg_graph *g, int32_t W)
 
 sg_status ensure_heavy_index(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st)
 {
+    ws.rd_on = 0;
+    if (ws.rd_cap < W) {
+        dbuf_free(ws.rdesc, st);
+        ws.rd_cap = 0;
+        SG_TRY(dbuf_alloc(ws.rdesc, (size_t)W * (size_t)g->n, st));
+        ws.rd_cap = W;
+    }
     if (ws.hw_cap >= W) return SG_OK;
     dbuf_free(ws.hcnt_out, st);
     dbuf_free(ws.hnbr_out, st);
@@ -481,6 +492,7 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
     b += (size_t)g->num_sms * 2 * 12 + (size_t)k * 12 + 4096;
     if (heavy_index_enabled(g, W)) {
         b += (size_t)(g->hsum_out + g->hsum_in) * W * 12 + (size_t)(g->nh_out + g->nh_in) * W * 4;
+        b += (size_t)g->n * W * 16;  // forward row descriptors
         const size_t nq = (size_t)g->nh_in * W64 + 1;
         b += nq * 16 + ((size_t)1 << 20) * 4 + (size_t)(1.5 * 64.0 * W * (double)g->nh_in) * 4;
     }
@@ -893,7 +905,11 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     SG_CUDA_TRY(cudaMemsetAsync(ws.anc.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.anc_cnt.p, 0, (size_t)co.W * 4, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
-    if (heavy_on) SG_TRY(run_heavy_index(g, ws, co, model, st));
+    if (heavy_on) {
+        SG_TRY(run_heavy_index(g, ws, co, model, st));
+        SG_TRY(run_row_desc(g, ws, co, st));
+        ws.rd_on = 1;
+    }
     if (ws.slists_on) SG_TRY(run_snapshot_lists(g, ws, co, st));
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_index, st));
@@ -1070,7 +1086,11 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     SG_TRY(ensure_mask_cache(g, ws, co.W, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
-    if (heavy_on) SG_TRY(run_heavy_index(g, ws, co, model, st));
+    if (heavy_on) {
+        SG_TRY(run_heavy_index(g, ws, co, model, st));
+        SG_TRY(run_row_desc(g, ws, co, st));
+        ws.rd_on = 1;
+    }
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));

@@ -135,6 +135,10 @@ struct GraphView {
     // the arc at CSC position j
     const unsigned long long *lm_out;
     const unsigned long long *lm_in;
+    // forward row descriptors (null when the heavy-row index is off):
+    // rdesc[w*n + x] = {segment base (lo, hi), elements to expand for word w,
+    // out-degree | (indexed << 31)}
+    const int4 *rdesc;
 };
 
 // Counters kept on the device during one call (zeroed at the start).
@@ -200,6 +204,9 @@ struct sg_workspace {
     sgi::DBuf<long long> scan_tmp;
     size_t soff_cap = 0, snbr_cap = 0;
     int32_t slists_on = 0;    // built for the current query
+    sgi::DBuf<int4> rdesc;    // [W][n] forward row descriptors (with the heavy-row index)
+    int32_t rd_cap = 0;
+    int32_t rd_on = 0;
     // live-mask cache, [W][m] per direction (optional)
     sgi::DBuf<unsigned long long> lm_out, lm_in;
     int32_t lm_cap = 0;       // words the cache was sized for
@@ -255,6 +262,7 @@ extern int g_mask_cache;
 sg_status run_heavy_index(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
 sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
 sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
+sg_status run_row_desc(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
 sg_status ensure_mask_cache(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st);
 size_t mask_cache_bytes(const sg_graph *g, int32_t W);
 sg_status ensure_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model,

@@ -125,6 +125,17 @@ template <int DIR, int MODEL, int SLICE = SLICE_SNAP>
 __device__ __forceinline__ Row row_ref(const GraphView &g, const Coins &co, int x, int word, uint32_t rs = 0)
 {
     Row r;
+    if (DIR == DIR_FWD && g.rdesc) {
+        // one 16-byte load instead of the row offsets, index ordinal and
+        // segment prefix one after another
+        const int4 d = __ldg(g.rdesc + (size_t)word * (size_t)g.n + x);
+        r.base = (long long)(((unsigned long long)(unsigned)d.y << 32) | (unsigned)d.x);
+        r.vdeg = d.z;
+        r.deg = d.w & 0x7fffffff;
+        r.heavy = (int)((unsigned)d.w >> 31);
+        r.rtm1 = co.uic_tm1;
+        return r;
+    }
     int beg, end;
     if (DIR == DIR_FWD) {
         beg = __ldg(g.rp + x);
@@ -1886,6 +1897,29 @@ __global__ void live_masks_kernel(Coins co, long long m, const uint2 *fw, uint32
     }
 }
 
+// ================================================== forward row descriptors
+
+__global__ void __launch_bounds__(256) row_desc_kernel(GraphView g, int W, int4 *out)
+{
+    const long long total = (long long)W * g.n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int word = (int)(i / g.n);
+        const int x = (int)(i - (long long)word * g.n);
+        const int beg = __ldg(g.rp + x), deg = __ldg(g.rp + x + 1) - beg;
+        const int h = __ldg(g.hout.hid + x);
+        long long base = beg;
+        int vdeg = deg, heavy = 0;
+        if (h >= 0) {
+            base = __ldg(g.hout.hpref + h) * W + (long long)word * deg;
+            vdeg = __ldg(g.hout.hcnt + (long long)h * W + word);
+            heavy = 1;
+        }
+        out[i] = make_int4((int)(unsigned)(unsigned long long)base, (int)(unsigned)((unsigned long long)base >> 32),
+                           vdeg, deg | (heavy << 31));
+    }
+}
+
 // ========================================================= live-mask cache
 
 // lm_out[w*m + e] = live bits of arc e in the snapshots of word w.
@@ -2114,6 +2148,18 @@ sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int mod
     mask_cache_csc_kernel<<<blocks, 256, 0, st>>>(co.W, g->m, g->cin.p, ws.lm_out.p, ws.lm_in.p);
     SG_CUDA_TRY(cudaGetLastError());
     g_launches += 2;
+    return SG_OK;
+}
+
+sg_status run_row_desc(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st)
+{
+    const long long total = g->n * co.W;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)g->num_sms * 16);
+    GraphView v = view_of(g, ws, 1);
+    v.rdesc = nullptr;
+    row_desc_kernel<<<blocks, 256, 0, st>>>(v, co.W, ws.rdesc.p);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
     return SG_OK;
 }
 
