@@ -463,11 +463,14 @@ sg_status ensure_wic(sg_graph *g, cudaStream_t st)
     return SG_OK;
 }
 
-// Tier-3 slot memory: 4 KB per node, between 64 MB and 4 GiB.
+// Tier-3 slot memory: 8 KB per node, between 64 MB and 16 GiB.
 size_t tier3_budget(int64_t n)
 {
-    const size_t b = (size_t)n * 4096;
-    return std::min<size_t>((size_t)4 << 30, std::max<size_t>((size_t)64 << 20, b));
+    // about 24 bytes per node per slot: 8 KB per node gives every graph up
+    // to 1.6 M nodes its two slots per SM (tier-3 tasks are latency-bound,
+    // so the number of resident blocks sets their throughput)
+    const size_t b = (size_t)n * 8192;
+    return std::min<size_t>((size_t)16 << 30, std::max<size_t>((size_t)64 << 20, b));
 }
 
 // Device bytes a workspace for (W, k) takes, as ensure_workspace /
@@ -535,7 +538,7 @@ sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, 
 
         SG_CUDA_TRY(cudaMemsetAsync(ws.nbits.p, 0, ws.nbits.bytes, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.pendf.p, 0, ws.pendf.bytes, st));
-        // tier-3 slots: dense per-slot arrays (vis, pend, ring queue, touched), <= ~4 GiB in total
+        // tier-3 slots: dense per-slot arrays (vis, pend, ring queue, touched), <= ~16 GiB in total
         int qcap = 1;
         while (qcap < n) qcap <<= 1;
         const size_t per_slot = (size_t)n * (2 * sizeof(unsigned long long) + sizeof(int32_t)) + (size_t)qcap * 4;
