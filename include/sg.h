@@ -162,6 +162,22 @@ sg_status sg_set_snapshot_lists(int32_t enable);
  * calls.  Errors: SG_EINVAL unless 0 or 1. */
 sg_status sg_set_mask_cache(int32_t enable);
 
+/* Seed-set spread on fresh snapshots (Section 3.1's snapshot estimate of
+ * the influence spread; Section 6 rates seed sets by Monte Carlo
+ * simulation): *out_total = sum over the R snapshots of hash seed `seed`
+ * of |R(G'_r, S)|, the nodes reachable from S = S[0..s_count) including
+ * S; the spread estimate is *out_total / R.  Repeated seeds count once;
+ * s_count = 0 gives 0.  *out_edges (may be NULL) gets the snapshot-edge
+ * count, the out-degree sum over the reached (node, snapshot) pairs.
+ * A multi-source bit-sliced traversal, one 64-snapshot word per block, with
+ * the coins hashed in registers (no per-query cache is used).  S: host or
+ * device int32[s_count]; out_total: host or device int64; out_edges: host.
+ * Synchronises `stream` before returning; uses up to ~4 GiB of scratch.
+ * Errors: SG_EINVAL for a NULL graph/output, s_count < 0, a seed outside
+ * [0, n), R outside [1, 2^24) or an invalid cascade; SG_ENOMEM; SG_ECUDA. */
+sg_status sg_spread(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, const int32_t *S, int32_t s_count,
+                    void *stream, int64_t *out_total, uint64_t *out_edges);
+
 /* Same as sg_load_graph from an arc list src[i] -> dst[i], i < m.
  * src/dst are host memory when is_device_ptr is 0, device memory when 1. */
 sg_status sg_load_graph_coo(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,

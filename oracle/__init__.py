@@ -65,7 +65,7 @@ def _load():
         lib.or_init_gains.restype = cint
         lib.or_init_gains.argtypes = [i64, P, P, P, i32, i32, u64, cint, P, P]
         lib.or_spread.restype = i64
-        lib.or_spread.argtypes = [i64, P, P, P, i32, u64, i32, P, cint]
+        lib.or_spread.argtypes = [i64, P, P, P, i32, u64, i32, P, cint, P]
         lib.or_reach_sums.restype = cint
         lib.or_reach_sums.argtypes = [i64, P, P, P, i32, u64, i32, P, cint, P, P]
         lib.or_live_masks.restype = cint
@@ -155,14 +155,16 @@ class Graph:
                "init_gains")
         return s, int(ed.value)
 
-    def spread(self, R, seed, S, nthreads=None):
-        """f(S) = sum_r |R(G'_r, S)|."""
+    def spread(self, R, seed, S, nthreads=None, want_edges=False):
+        """f(S) = sum_r |R(G'_r, S)| (and, with want_edges, the snapshot-edge
+        count sum_r sum over R(G'_r, S) of out-degrees)."""
         S = np.ascontiguousarray(S, dtype=np.int32)
+        ed = ctypes.c_uint64(0)
         v = _load().or_spread(self.n, _ptr(self.rp), _ptr(self.col), _ptr(self.thr), R,
-                              ctypes.c_uint64(seed), S.size, _ptr(S), _threads(nthreads))
+                              ctypes.c_uint64(seed), S.size, _ptr(S), _threads(nthreads), ctypes.byref(ed))
         if v < 0:
             raise OracleError(f"spread: oracle status {v}")
-        return int(v)
+        return (int(v), int(ed.value)) if want_edges else int(v)
 
     def reach_sums(self, R, seed, vs, nthreads=None):
         """(sum_r |R(G'_r, v)| for v in vs, their init snapshot-edge count)."""

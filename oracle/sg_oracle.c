@@ -504,14 +504,17 @@ static int64_t reach_fly(int64_t n, const int64_t *rp, const int32_t *col, const
 }
 
 /* f(S) = sum_r |R(G'_r, S)| (Section 3.1: the snapshot estimate of I(S),
- * times R), with on-demand coins; snapshots in parallel. */
+ * times R), with on-demand coins; snapshots in parallel.  *edges (if not
+ * NULL) gets the snapshot-edge count sum_r sum_{u in R(G'_r, S)} outdeg(u). */
 int64_t or_spread(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
-                  int32_t R, uint64_t seed, int32_t nS, const int32_t *Sset, int nthreads)
+                  int32_t R, uint64_t seed, int32_t nS, const int32_t *Sset, int nthreads,
+                  uint64_t *edges)
 {
     int64_t total = 0;
+    uint64_t ed = 0;
     int failed = 0;
 #ifdef _OPENMP
-#pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : total)
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : total, ed)
 #endif
     {
         uint8_t *mark = (uint8_t *)calloc((size_t)n, 1);
@@ -523,10 +526,11 @@ int64_t or_spread(int64_t n, const int64_t *rp, const int32_t *col, const uint64
 #pragma omp for schedule(dynamic, 1)
 #endif
             for (int32_t r = 0; r < R; r++)
-                total += reach_fly(n, rp, col, thr, seed, (uint32_t)r, nS, Sset, mark, queue, NULL);
+                total += reach_fly(n, rp, col, thr, seed, (uint32_t)r, nS, Sset, mark, queue, &ed);
         }
         free(mark); free(queue);
     }
+    if (edges) *edges = ed;
     return failed ? (int64_t)OR_ENOMEM : total;
 }
 

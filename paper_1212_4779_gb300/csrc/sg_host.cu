@@ -1067,6 +1067,53 @@ void sg_workspace_free(sg_workspace *ws)
     delete ws;
 }
 
+sg_status sg_spread(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, const int32_t *S, int32_t s_count,
+                    void *stream, int64_t *out_total, uint64_t *out_edges)
+{
+    clear_error();
+    if (!g || !out_total || s_count < 0 || (s_count > 0 && !S)) {
+        set_error("sg_spread: NULL graph or output, or a negative or missing seed list");
+        return SG_EINVAL;
+    }
+    SG_TRY(check_query(g, R, 1));
+    Coins co;
+    SG_TRY(make_coins(c, seed, R, &co));
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
+    // the seed list, checked on the host (host or device input)
+    std::vector<int32_t> hs((size_t)s_count);
+    if (s_count > 0) SG_CUDA_TRY(cudaMemcpy(hs.data(), S, (size_t)s_count * 4, cudaMemcpyDefault));
+    for (int32_t v : hs)
+        if (v < 0 || v >= g->n) {
+            set_error("sg_spread: seed %d is not a node (n = %lld)", v, (long long)g->n);
+            return SG_EINVAL;
+        }
+    DBuf<int32_t> dS;
+    DBuf<long long> dc;
+    sg_status rc = SG_OK;
+    if ((rc = dbuf_alloc(dS, (size_t)std::max(1, s_count), st)) != SG_OK) return rc;
+    if ((rc = dbuf_alloc(dc, 2, st)) != SG_OK) {
+        dbuf_free(dS, st);
+        return rc;
+    }
+    if (s_count > 0 && cudaMemcpyAsync(dS.p, hs.data(), (size_t)s_count * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = SG_ECUDA;
+    if (rc == SG_OK && cudaMemsetAsync(dc.p, 0, 16, st) != cudaSuccess) rc = SG_ECUDA;
+    if (rc == SG_OK && s_count > 0)
+        rc = run_spread(g, co, model, dS.p, s_count, dc.p, reinterpret_cast<unsigned long long *>(dc.p + 1), st);
+    long long hc[2] = {0, 0};
+    if (rc == SG_OK && cudaMemcpyAsync(hc, dc.p, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SG_ECUDA;
+    if (rc == SG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SG_ECUDA;
+    dbuf_free(dS, st);
+    dbuf_free(dc, st);
+    if (rc == SG_ECUDA && !g_err[0]) set_error("sg_spread: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc != SG_OK) return rc;
+    SG_CUDA_TRY(cudaMemcpy(out_total, &hc[0], 8, cudaMemcpyDefault));
+    if (out_edges) *out_edges = (uint64_t)hc[1];
+    return SG_OK;
+}
+
 sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, void *stream, int64_t *out_s,
                         uint64_t *init_edges)
 {

@@ -263,6 +263,8 @@ sg_status run_heavy_index(sg_graph *g, sg_workspace &ws, const Coins &co, int mo
 sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
 sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
 sg_status run_row_desc(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
+sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S, int32_t ns, long long *d_total,
+                     unsigned long long *d_edges, cudaStream_t st);
 sg_status ensure_mask_cache(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st);
 size_t mask_cache_bytes(const sg_graph *g, int32_t W);
 sg_status ensure_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model,

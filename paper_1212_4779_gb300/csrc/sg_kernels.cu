@@ -46,7 +46,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr long long SEED_MARK = -(1LL << 62);
 
 enum { DIR_FWD = 0, DIR_REV = 1 };
-enum { TASK_INIT = 0, TASK_REVT = 1, TASK_FWD = 2, TASK_ANC = 3, TASK_LMK = 4 };
+enum { TASK_INIT = 0, TASK_REVT = 1, TASK_FWD = 2, TASK_ANC = 3, TASK_LMK = 4, TASK_SPREAD = 5 };
 enum { SLICE_SNAP = 0, SLICE_TGT = 1 };
 
 constexpr int T1_LOGC = 9;   // tier-1 table: 512 slots per warp (shared memory)
@@ -694,6 +694,8 @@ struct CtaState {
     int32_t *du_x;              // TASK_FWD / TASK_LMK: the word's list of nodes gaining bits
     int32_t *ndu;               // ... and its length (global, shared by the word's blocks)
     unsigned long long gm;      // snapshot bits this block owns (several blocks may share a word)
+    long long *cnt_out;               // TASK_SPREAD: reached (node, snapshot) pairs are added here
+    unsigned long long *edges_out;    // TASK_SPREAD: snapshot-edge count
 };
 
 // One traversal by the whole block over dense arrays, level-synchronous.
@@ -703,6 +705,9 @@ struct CtaState {
 // reverse walk from v* over the snapshots where v* newly covers nodes; vis
 // (the word's ancestor bits) is kept, and every ancestor u loses
 // sum over its bits r of |N_r| (= ncov[r]) from its gain.
+// TASK_SPREAD: multi-source walk from tgt[0..ntgt) with bits M0 over a
+// zeroed vis; the reached (node, snapshot) pairs and their out-degrees are
+// added to cnt_out / edges_out.
 // Seeds: INIT, FWD, ANC: x0 with bits M0 (FWD: minus what is covered);
 // REVT: the targets tgt[0..ntgt) with one bit each.
 template <int DIR, int MODEL, int TASK>
@@ -734,6 +739,16 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
         if (tid == 0) {
             S.qlen = ntgt;
             S.ntouch = ntgt;
+        }
+    } else if (TASK == TASK_SPREAD) {
+        for (int j = tid; j < ntgt; j += BT) {
+            const int x = tgt[j];
+            const uint64_t M = M0 & ~atomicOr(&w.vis[x], (unsigned long long)M0);  // repeated sources count once
+            if (M) {
+                atomicOr(&w.pend[x], (unsigned long long)M);
+                w.qa[atomicAdd(&S.qlen, 1)] = x;
+                cnt += __popcll(M);
+            }
         }
     } else if (tid == 0) {
         uint64_t M = M0;
@@ -777,7 +792,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                 S.base[tid] = rr.base;
                 S.heavy[tid] = rr.heavy;
                 S.tm1[tid] = rr.rtm1;
-                if (TASK == TASK_INIT || TASK == TASK_FWD)
+                if (TASK == TASK_INIT || TASK == TASK_FWD || TASK == TASK_SPREAD)
                     edges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
             }
             int total;
@@ -803,8 +818,8 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                         const uint64_t old = atomicOr(&w.vis[(size_t)y * VS], (unsigned long long)ml);
                         const uint64_t nw = ml & ~old;
                         if (nw) {
-                            if (TASK == TASK_INIT) cnt += __popcll(nw);
-                            if (TASK != TASK_FWD && TASK != TASK_LMK && old == 0)
+                            if (TASK == TASK_INIT || TASK == TASK_SPREAD) cnt += __popcll(nw);
+                            if (TASK != TASK_FWD && TASK != TASK_LMK && TASK != TASK_SPREAD && old == 0)
                                 w.touched[atomicAdd(&S.ntouch, 1)] = y;
                             if ((TASK == TASK_FWD || TASK == TASK_LMK) && w.du_x) {
                                 const uint64_t ob = atomicOr(&w.nbits[y], (unsigned long long)nw);
@@ -854,11 +869,14 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
         }
     }
     const unsigned long long e_tot = block_sum(edges, S.red_ull);
-    if (TASK == TASK_INIT) {
+    if (TASK == TASK_INIT || TASK == TASK_SPREAD) {
         const long long c_tot = block_sum(cnt, S.red_ll);
-        if (tid == 0) atomicAdd((unsigned long long *)&a.s[x0], (unsigned long long)c_tot);
+        if (tid == 0 && c_tot)
+            atomicAdd((unsigned long long *)(TASK == TASK_INIT ? &a.s[x0] : w.cnt_out), (unsigned long long)c_tot);
     }
-    if (tid == 0 && e_tot) {
+    if (TASK == TASK_SPREAD) {
+        if (tid == 0 && e_tot) atomicAdd(w.edges_out, e_tot);
+    } else if (tid == 0 && e_tot) {
         unsigned long long *dst = TASK == TASK_INIT ? &a.ctl->init_edges
                                   : (TASK == TASK_FWD ? &a.ctl->fwd_edges : &a.ctl->rev_edges);
         atomicAdd(dst, e_tot);
@@ -1551,6 +1569,40 @@ __global__ void __launch_bounds__(BT) landmark_walk_kernel(EngineArgs a, LmkArgs
                                       0, nullptr, S);
 }
 
+// Seed-set spread on the snapshots of words w0 + blockIdx.x: one block per
+// 64-snapshot word, all 64 bits, multi-source from S.
+struct SpreadArgs {
+    unsigned long long *vis, *pend;  // [words][n], zero on entry
+    int32_t *qa, *qb;                // [words][n]
+    const int32_t *S;
+    int ns;
+    int w0;
+    long long *total;
+    unsigned long long *edges;
+};
+
+template <int MODEL>
+__global__ void __launch_bounds__(BT) spread_kernel(EngineArgs a, SpreadArgs sp)
+{
+    __shared__ CtaShared S;
+    const size_t n = (size_t)a.g.n;
+    const int word = sp.w0 + blockIdx.x;
+    CtaState w;
+    w.vis = sp.vis + blockIdx.x * n;
+    w.pend = sp.pend + blockIdx.x * n;
+    w.qa = sp.qa + blockIdx.x * n;
+    w.qb = sp.qb + blockIdx.x * n;
+    w.touched = nullptr;
+    w.nbits = nullptr;
+    w.du_x = nullptr;
+    w.ndu = nullptr;
+    w.gm = ~0ull;
+    w.cnt_out = sp.total;
+    w.edges_out = sp.edges;
+    cta_bfs<DIR_FWD, MODEL, TASK_SPREAD>(a, w, -1, word_mask(word, a.co.R), word, (uint32_t)word * 64u, sp.S, sp.ns,
+                                         nullptr, S);
+}
+
 // Histogram, per snapshot r, of the landmark-membership mask
 // m_r(y) = {i : y in R(G'_r, x_i)} over the nodes with m_r(y) nonempty
 // (count and out-degree sum), in H / HE [(r << K) + m].
@@ -2161,6 +2213,56 @@ sg_status run_row_desc(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStrea
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
     return SG_OK;
+}
+
+sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S, int32_t ns, long long *d_total,
+                     unsigned long long *d_edges, cudaStream_t st)
+{
+    const size_t n = (size_t)g->n;
+    // words per launch: dense vis/pend (8 B each) and two level queues (4 B
+    // each) per node and word, within 4 GiB
+    const size_t per_word = n * 24;
+    const int wc = (int)std::max<size_t>(1, std::min<size_t>((size_t)co.W, ((size_t)4 << 30) / per_word));
+    DBuf<unsigned long long> vis, pend;
+    DBuf<int32_t> qa, qb;
+    sg_status rc = SG_OK;
+    if ((rc = dbuf_alloc(vis, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(pend, (size_t)wc * n, st)) != SG_OK ||
+        (rc = dbuf_alloc(qa, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(qb, (size_t)wc * n, st)) != SG_OK) {
+        dbuf_free(vis, st);
+        dbuf_free(pend, st);
+        dbuf_free(qa, st);
+        dbuf_free(qb, st);
+        return rc;
+    }
+    EngineArgs a{};
+    a.g = view_of(g, g->ws, 0);
+    a.g.lm_out = nullptr;  // caches belong to another query's snapshots
+    a.g.lm_in = nullptr;
+    a.g.rdesc = nullptr;
+    a.co = co;
+    a.lmk_k = 0;
+    for (int w0 = 0; w0 < co.W && rc == SG_OK; w0 += wc) {
+        const int words = std::min(wc, co.W - w0);
+        if (cudaMemsetAsync(vis.p, 0, (size_t)words * n * 8, st) != cudaSuccess ||
+            cudaMemsetAsync(pend.p, 0, (size_t)words * n * 8, st) != cudaSuccess) {
+            set_error("sg_spread: memset failed");
+            rc = SG_ECUDA;
+            break;
+        }
+        SpreadArgs sp{vis.p, pend.p, qa.p, qb.p, d_S, ns, w0, d_total, d_edges};
+        if (model == MODEL_WIC) spread_kernel<MODEL_WIC><<<words, BT, 0, st>>>(a, sp);
+        else spread_kernel<MODEL_UIC><<<words, BT, 0, st>>>(a, sp);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("sg_spread: launch failed");
+            rc = SG_ECUDA;
+        }
+        ++g_launches;
+    }
+    dbuf_free(vis, st);
+    dbuf_free(pend, st);
+    dbuf_free(qa, st);
+    dbuf_free(qb, st);
+    return rc;
 }
 
 sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st)

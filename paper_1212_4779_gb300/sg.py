@@ -32,7 +32,7 @@ EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg
            "sg_server_poll", "sg_server_counts", "sg_server_destroy",
            "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
            "sg_set_snapshot_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
-           "sg_init_gains", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
+           "sg_init_gains", "sg_spread", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
 
 
 class SGError(RuntimeError):
@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
         L.sg_set_landmarks.argtypes = [i32]
         L.sg_set_snapshot_lists.argtypes = [i32]
         L.sg_set_mask_cache.argtypes = [i32]
+        L.sg_spread.argtypes = [P, i32, sg_cascade, u64, P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(u64)]
         L.sg_argmax_noalloc.argtypes = [P, i64, P, P, P]
         L.sg_load_graph.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_load_graph_coo.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
@@ -137,7 +138,7 @@ def lib() -> ctypes.CDLL:
                      "sg_batch_capture", "sg_batch_launch", "sg_server_create", "sg_server_submit",
                      "sg_server_poll", "sg_server_counts", "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
                      "sg_set_snapshot_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
-                     "sg_init_gains", "sg_live_masks", "sg_graph_csr"):
+                     "sg_init_gains", "sg_spread", "sg_live_masks", "sg_graph_csr"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -327,6 +328,20 @@ def sg_init_gains(h, R, model, p, seed, out_s, stream=None, want_edges=False):
     return ed.value if want_edges else None
 
 
+def sg_spread(h, R, model, p, seed, S, stream=None):
+    """(sum_r |R(G'_r, S)|, snapshot-edge count) over R snapshots of hash
+    seed ``seed``; S is any int sequence, numpy or torch (host or device)."""
+    if not hasattr(S, "data_ptr"):
+        S = np.ascontiguousarray(np.asarray(S, dtype=np.int32))
+    total = ctypes.c_int64(0)
+    edges = ctypes.c_uint64(0)
+    n_s = int(S.numel() if hasattr(S, "numel") else S.size)
+    _check(lib().sg_spread(h, int(R), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                           ctypes.c_void_p(_addr(S)[0] if n_s else 0), n_s, _stream_ptr(stream),
+                           ctypes.byref(total), ctypes.byref(edges)))
+    return total.value, edges.value
+
+
 def sg_live_masks(h, R, model, p, seed, out_masks, stream=None):
     _check(lib().sg_live_masks(h, int(R), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
                                _stream_ptr(stream), ctypes.c_void_p(_addr(out_masks)[0])))
@@ -483,6 +498,10 @@ class Graph:
         s = np.zeros(self.n, dtype=np.int64)
         edges = sg_init_gains(self._h, R, model, p, seed, s, stream, want_edges=True)
         return s, edges
+
+    def spread(self, R, model, p, seed, S, stream=None):
+        """(sum_r |R(G'_r, S)|, snapshot-edge count) on R fresh snapshots."""
+        return sg_spread(self._h, R, model, p, seed, S, stream)
 
     def live_masks(self, R, model="uic", p=0.0, seed=0, stream=None):
         W = (R + 63) // 64

@@ -178,6 +178,25 @@ def test_p1_out_star(oracle_mod, mode):
     assert list(out["gains"]) == [5 * 20, 0, 0, 0]
 
 
+def test_spread_closed_forms(oracle_mod):
+    """p = 1: the spread of a seed set is R times the nodes it reaches, and
+    its snapshot-edge count R times their out-degree sum (path: a suffix;
+    out-star: everything from the centre, the leaf alone otherwise)."""
+    n, s, d = inputs.path_graph(12)
+    g = oracle.Graph(n, s, d, "uic", 1.0)
+    for S, reach in (([0], 12), ([5], 7), ([9, 3], 9), ([11], 1)):
+        tot, ed = g.spread(6, 2, S, want_edges=True)
+        assert tot == 6 * reach and ed == 6 * (reach - 1)
+    n, s, d = inputs.out_star(20, centre=7)
+    g = oracle.Graph(n, s, d, "uic", 1.0)
+    assert g.spread(3, 1, [7], want_edges=True) == (3 * 20, 3 * 19)
+    assert g.spread(3, 1, [4], want_edges=True) == (3, 0)
+    assert g.spread(3, 1, [4, 7, 9], want_edges=True) == (3 * 20, 3 * 19)
+    # p = 0: the seeds alone, and the out-degrees of the seeds are scanned
+    g = oracle.Graph(n, s, d, "uic", 0.0)
+    assert g.spread(5, 1, [7, 2], want_edges=True) == (10, 5 * 19)
+
+
 def _subtree_sizes(n, parent_of):
     size = [1] * n
     for v in range(n - 1, 0, -1):  # parent < child
