@@ -29,7 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 UIC, WIC = 0, 1
-LITERAL, COVER, DU = 0, 1, 2
+LITERAL, COVER, DU, CELF = 0, 1, 2, 3
 OR_OK, OR_EINVAL, OR_ENOMEM, OR_EINVARIANT = 0, -1, -2, -3
 
 
@@ -129,7 +129,7 @@ class Graph:
         lib = _load()
         seeds = np.zeros(k, dtype=np.int32)
         gains = np.zeros(k, dtype=np.int64)
-        cnt = np.zeros(3, dtype=np.uint64)
+        cnt = np.zeros(4, dtype=np.uint64)
         s_init = np.zeros(self.n, dtype=np.int64) if want_init else None
         s_hist = np.zeros((k, self.n), dtype=np.int64) if want_hist else None
         rc = lib.or_select(mode, self.n, _ptr(self.rp), _ptr(self.col), _ptr(self.thr), R, k,
@@ -137,7 +137,7 @@ class Graph:
                            _ptr(s_init) if want_init else None, _ptr(s_hist) if want_hist else None,
                            _ptr(cnt))
         _check(rc, "select")
-        out = dict(seeds=seeds, gains=gains, counters=cnt)
+        out = dict(seeds=seeds, gains=gains, counters=cnt[:3], evals=int(cnt[3]))
         if want_init:
             out["s_init"] = s_init
         if want_hist:

@@ -25,7 +25,9 @@
  *       OR_LITERAL  Algorithm 1 as stated (recompute |R(G'_r, S u {v})|);
  *       OR_COVER    Algorithm 1 with the marginal gain counted directly as
  *                   |R(G'_r, v) \ R(G'_r, S)|;
- *       OR_DU       Algorithm 2 (dynamic update of Section 4).
+ *       OR_DU       Algorithm 2 (dynamic update of Section 4);
+ *       OR_CELF     lazy forward evaluation (CELF, Section 2) on the same
+ *                   snapshots: StaticGreedyCELF of Section 6.
  *
  * Parity pins and readings of the paper (counted from vertex itself,
  * lowest-id tie break, DU set = newly covered nodes) are stated at each
@@ -51,7 +53,7 @@
 #define OR_EINVARIANT -3
 
 enum { OR_UIC = 0, OR_WIC = 1 };
-enum { OR_LITERAL = 0, OR_COVER = 1, OR_DU = 2 };
+enum { OR_LITERAL = 0, OR_COVER = 1, OR_DU = 2, OR_CELF = 3 };
 
 /* ------------------------------------------------------------------ hash */
 
@@ -319,6 +321,73 @@ static int32_t argmax_not_seed(int64_t n, const int64_t *s, const uint8_t *is_se
     return best;
 }
 
+/* ------------------------------------------------- CELF priority queue */
+
+/* Binary max-heap of (bound, id, stamp) ordered by bound descending, then
+ * id ascending. */
+typedef struct {
+    int64_t *b;
+    int32_t *v, *stamp;
+    int64_t size;
+} or_heap;
+
+static int heap_before(const or_heap *h, int64_t x, int64_t y)
+{
+    return h->b[x] > h->b[y] || (h->b[x] == h->b[y] && h->v[x] < h->v[y]);
+}
+
+static void heap_swap(or_heap *h, int64_t x, int64_t y)
+{
+    int64_t tb = h->b[x]; h->b[x] = h->b[y]; h->b[y] = tb;
+    int32_t tv = h->v[x]; h->v[x] = h->v[y]; h->v[y] = tv;
+    int32_t ts = h->stamp[x]; h->stamp[x] = h->stamp[y]; h->stamp[y] = ts;
+}
+
+static int heap_init(or_heap *h, int64_t cap)
+{
+    h->b = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    h->v = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    h->stamp = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    h->size = 0;
+    return (h->b && h->v && h->stamp) ? 0 : -1;
+}
+
+static void heap_free(or_heap *h)
+{
+    free(h->b); free(h->v); free(h->stamp);
+    h->b = NULL; h->v = NULL; h->stamp = NULL;
+}
+
+static void heap_push(or_heap *h, int64_t b, int32_t v, int32_t stamp)
+{
+    int64_t i = h->size++;
+    h->b[i] = b; h->v[i] = v; h->stamp[i] = stamp;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!heap_before(h, i, p)) break;
+        heap_swap(h, i, p);
+        i = p;
+    }
+}
+
+static void heap_pop(or_heap *h, int64_t *b, int32_t *v, int32_t *stamp)
+{
+    *b = h->b[0]; *v = h->v[0]; *stamp = h->stamp[0];
+    h->size--;
+    if (h->size > 0) {
+        h->b[0] = h->b[h->size]; h->v[0] = h->v[h->size]; h->stamp[0] = h->stamp[h->size];
+        int64_t i = 0;
+        for (;;) {
+            int64_t l = 2 * i + 1, r = l + 1, m = i;
+            if (l < h->size && heap_before(h, l, m)) m = l;
+            if (r < h->size && heap_before(h, r, m)) m = r;
+            if (m == i) break;
+            heap_swap(h, i, m);
+            i = m;
+        }
+    }
+}
+
 /* ------------------------------------------------------------- selection */
 
 /* Greedy seed selection on static snapshots.
@@ -337,11 +406,21 @@ static int32_t argmax_not_seed(int64_t n, const int64_t *s, const uint8_t *is_se
  *     reverse BFS must never visit a node covered before this round (such
  *     a node would reach w, so w would already be covered); a visit returns
  *     OR_EINVARIANT.
- * Outputs seeds[k], gains[k].  Optional: s_init[n] (initial gains, DU and
- * COVER only), s_hist[k*n] (the gain vector after each DU round, seeds'
- * entries included), counters[3] = {init, forward, reverse} snapshot-edge
+ *   mode OR_CELF: s starts at the initial gains, which are exact upper
+ *     bounds of every later marginal gain (submodularity, Section 3.1).
+ *     The candidates sit in a priority queue ordered by (bound descending,
+ *     id ascending).  Round i pops the head; if its bound was computed in
+ *     round i it is the round's seed (every other candidate's gain is at
+ *     most its bound, and an equal bound comes with a larger id), else its
+ *     marginal gain sum_r |R(G'_r, v) \ Cov_r| is computed as in OR_COVER
+ *     (one evaluation) and it goes back with that bound.  Round 0 uses the
+ *     initial gains as computed in round 0.
+ * Outputs seeds[k], gains[k].  Optional: s_init[n] (initial gains, DU,
+ * COVER and CELF), s_hist[k*n] (the gain vector after each DU round, seeds'
+ * entries included), counters[4] = {init, forward, reverse} snapshot-edge
  * counts of the DU route (forward: sum over expanded (u,r) of outdeg(u);
- * reverse: sum over visited (u,w,r) of indeg(u)). */
+ * reverse: sum over visited (u,w,r) of indeg(u)) and, for OR_CELF, the
+ * number of marginal-gain evaluations after the initial gains. */
 int or_select(int mode, int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
               int32_t R, int32_t k, uint64_t seed, int nthreads, int32_t *seeds, int64_t *gains,
               int64_t *s_init, int64_t *s_hist, uint64_t *counters)
@@ -363,10 +442,16 @@ int or_select(int mode, int64_t n, const int64_t *rp, const int32_t *col, const 
     uint64_t c_init = 0, c_fwd = 0, c_rev = 0;
     int64_t f_S = 0; /* f(S) of the current seed set */
 
-    if (mode == OR_DU || mode == OR_COVER) {
+    if (mode == OR_DU || mode == OR_COVER || mode == OR_CELF) {
         rc = init_gains(S, rp, nthreads, s, &c_init);
         if (rc != OR_OK) goto done;
         if (s_init) memcpy(s_init, s, sizeof(int64_t) * (size_t)n);
+    }
+    uint64_t c_eval = 0;
+    or_heap H = {0};
+    if (mode == OR_CELF) {
+        if (heap_init(&H, n) != 0) { rc = OR_ENOMEM; goto done; }
+        for (int64_t v = 0; v < n; v++) heap_push(&H, s[v], (int32_t)v, 0);
     }
 
     for (int32_t i = 0; i < k; i++) {
@@ -393,7 +478,21 @@ int or_select(int mode, int64_t n, const int64_t *rp, const int32_t *col, const 
                 s[v] = acc;
             }
         }
-        int32_t vs = argmax_not_seed(n, s, is_seed);
+        int32_t vs;
+        if (mode == OR_CELF) {
+            for (;;) {
+                int64_t b; int32_t v, stamp;
+                heap_pop(&H, &b, &v, &stamp);
+                if (stamp == i) { s[v] = b; vs = v; break; }
+                int64_t acc = 0;
+                for (int32_t r = 0; r < R; r++)
+                    acc += reach_count(S, r, rp, 1, &v, cov + (size_t)r * (size_t)n, &w, NULL);
+                c_eval++;
+                heap_push(&H, acc, v, i);
+            }
+        } else {
+            vs = argmax_not_seed(n, s, is_seed);
+        }
         seeds[i] = vs;
         gains[i] = (mode == OR_LITERAL) ? s[vs] - f_S : s[vs];
         f_S += gains[i];
@@ -449,8 +548,9 @@ int or_select(int mode, int64_t n, const int64_t *rp, const int32_t *col, const 
         }
         if (s_hist && mode == OR_DU) memcpy(s_hist + (size_t)i * (size_t)n, s, sizeof(int64_t) * (size_t)n);
     }
-    if (counters) { counters[0] = c_init; counters[1] = c_fwd; counters[2] = c_rev; }
+    if (counters) { counters[0] = c_init; counters[1] = c_fwd; counters[2] = c_rev; counters[3] = c_eval; }
 done:
+    heap_free(&H);
     ws_free(&w);
     free(s); free(is_seed); free(cov); free(indeg);
     snaps_free(S);

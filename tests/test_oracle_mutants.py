@@ -35,6 +35,10 @@ MUTANTS = {
     "keep_duplicates": ("if (i == 0 || key[i] != key[i - 1]) key[m++] = key[i];", "key[m++] = key[i];"),
     "gain_literal_no_base": ("gains[i] = (mode == OR_LITERAL) ? s[vs] - f_S : s[vs];", "gains[i] = s[vs];"),
     "fwd_counter_indeg": ("c_fwd += (uint64_t)(rp[u + 1] - rp[u]);", "c_fwd += (uint64_t)indeg[u];"),
+    "celf_accepts_stale_bound": ("if (stamp == i) { s[v] = b; vs = v; break; }",
+                                 "if (stamp <= i) { s[v] = b; vs = v; break; }"),
+    "celf_ties_to_highest_id": ("return h->b[x] > h->b[y] || (h->b[x] == h->b[y] && h->v[x] < h->v[y]);",
+                                "return h->b[x] > h->b[y] || (h->b[x] == h->b[y] && h->v[x] > h->v[y]);"),
 }
 
 

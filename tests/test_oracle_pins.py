@@ -143,7 +143,7 @@ def test_canonicalisation_drops_loops_and_repeats(oracle_mod):
 # ------------------------------------------------------------- closed forms
 
 
-MODES = [oracle.LITERAL, oracle.COVER, oracle.DU]
+MODES = [oracle.LITERAL, oracle.COVER, oracle.DU, oracle.CELF]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -195,6 +195,28 @@ def test_spread_closed_forms(oracle_mod):
     # p = 0: the seeds alone, and the out-degrees of the seeds are scanned
     g = oracle.Graph(n, s, d, "uic", 0.0)
     assert g.spread(5, 1, [7, 2], want_edges=True) == (10, 5 * 19)
+
+
+def test_celf_evaluation_count_on_path(oracle_mod):
+    """p = 1 path, lazy evaluation with the (bound desc, id asc) queue:
+    round 0 takes node 0 straight from the initial gains (it covers
+    everything).  In round 1 every other node's bound R(n - i) exceeds the
+    true gain 0, so all n - 1 are evaluated before the lowest id (bound 0,
+    fresh) is taken; in each later round the head is the lowest remaining
+    id with a stale bound 0, evaluated once and taken: (n - 1) + (k - 2)
+    evaluations."""
+    n, s, d = inputs.path_graph(12)
+    g = oracle.Graph(n, s, d, "uic", 1.0)
+    out = g.select(R=3, k=4, seed=5, mode=oracle.CELF)
+    assert out["evals"] == 11 + 2
+    assert list(out["seeds"]) == [0, 1, 2, 3] and list(out["gains"]) == [36, 0, 0, 0]
+    # an out-star: the centre first, then the 8 leaves (bound R each) are
+    # all evaluated in round 1, one head evaluation in each later round
+    n, s, d = inputs.out_star(9, centre=4)
+    g = oracle.Graph(n, s, d, "uic", 1.0)
+    out = g.select(R=2, k=4, seed=1, mode=oracle.CELF)
+    assert list(out["seeds"]) == [4, 0, 1, 2] and list(out["gains"]) == [18, 0, 0, 0]
+    assert out["evals"] == 8 + 2
 
 
 def _subtree_sizes(n, parent_of):
@@ -307,6 +329,9 @@ def test_du_matches_recompute_and_invariants(medium_graphs, model):
     cv = g.select(R=R, k=k, seed=seed, mode=oracle.COVER)
     assert list(du["seeds"]) == list(cv["seeds"])
     assert list(du["gains"]) == list(cv["gains"])
+    ce = g.select(R=R, k=k, seed=seed, mode=oracle.CELF)
+    assert list(du["seeds"]) == list(ce["seeds"]) and list(du["gains"]) == list(ce["gains"])
+    assert 0 < ce["evals"] < (k - 1) * g.n  # lazy: far fewer than recomputing every candidate
     gains = du["gains"]
     assert np.all(np.diff(gains) <= 0), "greedy gains of a submodular f are non-increasing"
     assert len(set(du["seeds"].tolist())) == k
