@@ -393,6 +393,47 @@ def run_spread_bench(args):
     return 0
 
 
+def run_celf_bench(args):
+    """StaticGreedyCELF against StaticGreedyDU (Section 6 times both) on the
+    R-MAT scale-20 weighted-cascade query (R = 256, k = 50, hash seed 11):
+    the same seeds and gains, selected with lazy evaluation.  One step = one
+    sg_select_celf call (host-driven: one GPU walk per evaluation)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1212_4779_gb300 import sg
+
+    wl = inputs.workload(args.celf_workload)
+    n, s, d = wl.graph()
+    torch.cuda.set_device(0)
+    g = sg.Graph.from_coo(n, s, d)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        g.select_celf(wl.R, wl.k, wl.model, wl.p, wl.seed, stream=stream)
+        g.select(wl.R, wl.k, wl.model, wl.p, wl.seed, stream=stream)
+    torch.cuda.synchronize()
+    t_celf, t_du, evals, same = [], [], 0, True
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res, evals = g.select_celf(wl.R, wl.k, wl.model, wl.p, wl.seed, stream=stream)
+        torch.cuda.synchronize()
+        t_celf.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        du = g.select(wl.R, wl.k, wl.model, wl.p, wl.seed, stream=stream)
+        torch.cuda.synchronize()
+        t_du.append(time.perf_counter() - t0)
+        same = same and bool(np.array_equal(res.seeds, du.seeds) and np.array_equal(res.gains, du.gains))
+    line = {"metric": "k-seed select time, StaticGreedyCELF vs StaticGreedyDU", "value": float(np.mean(t_celf)) * 1e3,
+            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": "int64", "data": "synthetic", "config": {"workload": wl_desc(wl)},
+            "du_ms": float(np.mean(t_du)) * 1e3, "celf_over_du": float(np.mean(t_celf) / np.mean(t_du)),
+            "celf_evaluations": evals, "results_equal": same}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,6 +450,7 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
     ap.add_argument("--served-scale", type=int, default=22, help="served: R-MAT scale of the large graph")
     ap.add_argument("--spread-R", type=int, default=20000, help="spread: snapshots of the evaluation")
+    ap.add_argument("--celf-workload", default="rmat20_wic", help="celf: the query compared with the dynamic update")
     ap.add_argument("--mask-cache", type=int, default=0, choices=[0, 1],
                     help="1: evaluate every arc's coins once per query into the live-mask cache")
     args = ap.parse_args()
@@ -418,6 +460,8 @@ def main():
         return run_served(args)
     if args.workload == "spread" and args.impl == "ours":
         return run_spread_bench(args)
+    if args.workload == "celf" and args.impl == "ours":
+        return run_celf_bench(args)
     wl = inputs.workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, wl)

@@ -162,6 +162,22 @@ sg_status sg_set_snapshot_lists(int32_t enable);
  * calls.  Errors: SG_EINVAL unless 0 or 1. */
 sg_status sg_set_mask_cache(int32_t enable);
 
+/* StaticGreedyCELF (Section 6): the same seeds and gains as sg_select,
+ * found with lazy forward evaluation (CELF, Section 2) over the static
+ * snapshots instead of the dynamic update.  After the initial gains (the
+ * same kernels as sg_select) the candidates wait in a host priority queue
+ * ordered by (bound descending, id ascending); a head whose bound is from
+ * the current round is the seed, otherwise its marginal gain
+ * sum_r |R(G'_r, v) minus the covered nodes| is computed on the GPU and it
+ * is queued again.  *out_evals (may be NULL) receives the number of such
+ * evaluations (the initial gains not counted).  Outputs as sg_select (host
+ * or device); stats (may be NULL): init and forward snapshot-edge counts
+ * (reverse 0), ms_init, ms_rounds, ms_total.  Synchronises `stream` once per
+ * evaluation and per round (not capturable).  Uses the graph's default
+ * workspace, like sg_select.  Errors: as sg_select. */
+sg_status sg_select_celf(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                         int32_t *out_seeds, int64_t *out_gains, int64_t *out_evals, sg_stats *stats);
+
 /* Seed-set spread on fresh snapshots (Section 3.1's snapshot estimate of
  * the influence spread; Section 6 rates seed sets by Monte Carlo
  * simulation): *out_total = sum over the R snapshots of hash seed `seed`

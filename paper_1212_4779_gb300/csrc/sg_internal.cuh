@@ -265,6 +265,14 @@ sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int mod
 sg_status run_row_desc(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
 sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S, int32_t ns, long long *d_total,
                      unsigned long long *d_edges, cudaStream_t st);
+// Walk from d_S over all W words (FWD_GROUPS blocks per word) on the query's
+// coins (heavy-row index and caches of ws when heavy_on): vis [W][n] holds
+// the nodes to leave out and gains the reached bits; pend [W][n] zero;
+// qa/qb [W * 8][n]; new (node, snapshot) pairs / out-degrees added to
+// d_total / d_edges.
+sg_status run_walk(sg_graph *g, const sg_workspace &ws, const Coins &co, int model, int heavy_on,
+                   const int32_t *d_S, int32_t ns, unsigned long long *vis, unsigned long long *pend, int32_t *qa,
+                   int32_t *qb, long long *d_total, unsigned long long *d_edges, cudaStream_t st);
 sg_status ensure_mask_cache(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st);
 size_t mask_cache_bytes(const sg_graph *g, int32_t W);
 sg_status ensure_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model,

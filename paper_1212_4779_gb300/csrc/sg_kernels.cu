@@ -1569,14 +1569,19 @@ __global__ void __launch_bounds__(BT) landmark_walk_kernel(EngineArgs a, LmkArgs
                                       0, nullptr, S);
 }
 
-// Seed-set spread on the snapshots of words w0 + blockIdx.x: one block per
-// 64-snapshot word, all 64 bits, multi-source from S.
+// Multi-source walk over the snapshots of words w0 .. w0 + gridDim.x /
+// groups - 1: block b walks word w0 + b / groups, owning 64 / groups of its
+// snapshot bits (the word's blocks share vis and pend, bit-disjoint), from
+// every node of S.  vis holds the nodes to leave out (zero, or a copy of
+// the coverage) and gains the reached bits; the newly reached (node,
+// snapshot) pairs and their out-degree sum are added to total / edges.
 struct SpreadArgs {
-    unsigned long long *vis, *pend;  // [words][n], zero on entry
-    int32_t *qa, *qb;                // [words][n]
+    unsigned long long *vis, *pend;  // [words][n]; pend zero on entry
+    int32_t *qa, *qb;                // [words * groups][n]
     const int32_t *S;
     int ns;
     int w0;
+    int groups;                      // 1, 2, 4 or 8
     long long *total;
     unsigned long long *edges;
 };
@@ -1586,21 +1591,23 @@ __global__ void __launch_bounds__(BT) spread_kernel(EngineArgs a, SpreadArgs sp)
 {
     __shared__ CtaShared S;
     const size_t n = (size_t)a.g.n;
-    const int word = sp.w0 + blockIdx.x;
+    const int wi = blockIdx.x / sp.groups, grp = blockIdx.x - wi * sp.groups;
+    const int word = sp.w0 + wi;
+    const int gb = 64 / sp.groups;
     CtaState w;
-    w.vis = sp.vis + blockIdx.x * n;
-    w.pend = sp.pend + blockIdx.x * n;
+    w.vis = sp.vis + (size_t)wi * n;
+    w.pend = sp.pend + (size_t)wi * n;
     w.qa = sp.qa + blockIdx.x * n;
     w.qb = sp.qb + blockIdx.x * n;
     w.touched = nullptr;
     w.nbits = nullptr;
     w.du_x = nullptr;
     w.ndu = nullptr;
-    w.gm = ~0ull;
+    w.gm = gb == 64 ? ~0ull : (((1ull << gb) - 1ull) << (grp * gb));
     w.cnt_out = sp.total;
     w.edges_out = sp.edges;
-    cta_bfs<DIR_FWD, MODEL, TASK_SPREAD>(a, w, -1, word_mask(word, a.co.R), word, (uint32_t)word * 64u, sp.S, sp.ns,
-                                         nullptr, S);
+    cta_bfs<DIR_FWD, MODEL, TASK_SPREAD>(a, w, -1, word_mask(word, a.co.R) & w.gm, word, (uint32_t)word * 64u, sp.S,
+                                         sp.ns, nullptr, S);
 }
 
 // Histogram, per snapshot r, of the landmark-membership mask
@@ -2249,7 +2256,7 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
             rc = SG_ECUDA;
             break;
         }
-        SpreadArgs sp{vis.p, pend.p, qa.p, qb.p, d_S, ns, w0, d_total, d_edges};
+        SpreadArgs sp{vis.p, pend.p, qa.p, qb.p, d_S, ns, w0, 1, d_total, d_edges};
         if (model == MODEL_WIC) spread_kernel<MODEL_WIC><<<words, BT, 0, st>>>(a, sp);
         else spread_kernel<MODEL_UIC><<<words, BT, 0, st>>>(a, sp);
         if (cudaGetLastError() != cudaSuccess) {
@@ -2263,6 +2270,22 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
     dbuf_free(qa, st);
     dbuf_free(qb, st);
     return rc;
+}
+
+sg_status run_walk(sg_graph *g, const sg_workspace &ws, const Coins &co, int model, int heavy_on,
+                   const int32_t *d_S, int32_t ns, unsigned long long *vis, unsigned long long *pend, int32_t *qa,
+                   int32_t *qb, long long *d_total, unsigned long long *d_edges, cudaStream_t st)
+{
+    EngineArgs a{};
+    a.g = view_of(g, ws, heavy_on);
+    a.co = co;
+    a.lmk_k = 0;
+    SpreadArgs sp{vis, pend, qa, qb, d_S, ns, 0, FWD_GROUPS, d_total, d_edges};
+    if (model == MODEL_WIC) spread_kernel<MODEL_WIC><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, sp);
+    else spread_kernel<MODEL_UIC><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, sp);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
+    return SG_OK;
 }
 
 sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st)

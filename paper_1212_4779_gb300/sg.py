@@ -32,7 +32,7 @@ EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg
            "sg_server_poll", "sg_server_counts", "sg_server_destroy",
            "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
            "sg_set_snapshot_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
-           "sg_init_gains", "sg_spread", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
+           "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
 
 
 class SGError(RuntimeError):
@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
         L.sg_set_snapshot_lists.argtypes = [i32]
         L.sg_set_mask_cache.argtypes = [i32]
         L.sg_spread.argtypes = [P, i32, sg_cascade, u64, P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(u64)]
+        L.sg_select_celf.argtypes = [P, i32, i32, sg_cascade, u64, P, P, P, ctypes.POINTER(i64), P]
         L.sg_argmax_noalloc.argtypes = [P, i64, P, P, P]
         L.sg_load_graph.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_load_graph_coo.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
@@ -138,7 +139,7 @@ def lib() -> ctypes.CDLL:
                      "sg_batch_capture", "sg_batch_launch", "sg_server_create", "sg_server_submit",
                      "sg_server_poll", "sg_server_counts", "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
                      "sg_set_snapshot_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
-                     "sg_init_gains", "sg_spread", "sg_live_masks", "sg_graph_csr"):
+                     "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -328,6 +329,18 @@ def sg_init_gains(h, R, model, p, seed, out_s, stream=None, want_edges=False):
     return ed.value if want_edges else None
 
 
+def sg_select_celf(h, R, k, model, p, seed, out_seeds, out_gains, stream=None, stats=False):
+    """StaticGreedyCELF: same outputs as sg_select; returns (evaluations,
+    stats dict or None)."""
+    st = sg_stats() if stats else None
+    ev = ctypes.c_int64(0)
+    _check(lib().sg_select_celf(h, int(R), int(k), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                                _stream_ptr(stream), ctypes.c_void_p(_addr(out_seeds)[0]),
+                                ctypes.c_void_p(_addr(out_gains)[0]), ctypes.byref(ev),
+                                ctypes.byref(st) if stats else None))
+    return ev.value, (st.as_dict() if stats else None)
+
+
 def sg_spread(h, R, model, p, seed, S, stream=None):
     """(sum_r |R(G'_r, S)|, snapshot-edge count) over R snapshots of hash
     seed ``seed``; S is any int sequence, numpy or torch (host or device)."""
@@ -498,6 +511,13 @@ class Graph:
         s = np.zeros(self.n, dtype=np.int64)
         edges = sg_init_gains(self._h, R, model, p, seed, s, stream, want_edges=True)
         return s, edges
+
+    def select_celf(self, R, k, model="uic", p=0.0, seed=0, stream=None, stats=False):
+        """StaticGreedyCELF; returns (Selection, evaluations)."""
+        seeds = np.zeros(k, dtype=np.int32)
+        gains = np.zeros(k, dtype=np.int64)
+        ev, st = sg_select_celf(self._h, R, k, model, p, seed, seeds, gains, stream, stats)
+        return Selection(seeds, gains, st), ev
 
     def spread(self, R, model, p, seed, S, stream=None):
         """(sum_r |R(G'_r, S)|, snapshot-edge count) on R fresh snapshots."""
