@@ -116,6 +116,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _recorded_traffic(kernel_src="paper_1212_4779_gb300/csrc/sg_kernels.cu",
+                      summary="profiles/coop_engine_tier3_init_rmat20_traffic.md"):
+    """DRAM bytes per launch of the tier-3 initial-gain kernel from the
+    committed ncu summary, or None when the kernel source has changed since
+    that capture (its sha256 prefix is recorded in the summary)."""
+    import hashlib
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        text = open(os.path.join(here, summary)).read()
+        digest = hashlib.sha256(open(os.path.join(here, kernel_src), "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    rec = dict(line.split(": ", 1) for line in text.splitlines() if line.startswith(("kernel_source", "traffic_bytes")))
+    if not rec.get("kernel_source", "").endswith(digest):
+        return None
+    try:
+        return int(rec["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -536,7 +558,9 @@ def main():
     achieved = t3_bytes / (t3_ms / 1e3) / 1e9 if t3_ms > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": "coop_engine_kernel<dense> (initial gains, tier 3)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
+                "traffic": _recorded_traffic() if wl.name == "rmat20" else None,
+                "traffic_source": "profiles/coop_engine_tier3_init_rmat20_traffic.md (full-size ncu capture)",
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
                 "kernel_ms": t3_ms, "elements_per_launch": st_last["work_elems"][0][2],
                 "bytes_per_element": bpe}
     t1_ms = float(np.mean(t_t1))

@@ -195,6 +195,7 @@ _WORKLOAD_GRAPHS = {
     # the scale-20 recipe at scale 18 (2,097,152 arcs): a small case of the
     # same kernels, for profiler captures
     "rmat18": lambda: rmat(18, 2097152, (0.57, 0.19, 0.19, 0.05), 103),
+    "rmat19": lambda: rmat(19, 4194304, (0.57, 0.19, 0.19, 0.05), 103),
     # directed R-MAT scale 22, 67,108,864 arcs, seed 105 (served graph)
     "rmat22": lambda: rmat(22, 67108864, (0.57, 0.19, 0.19, 0.05), 105),
 }
@@ -205,6 +206,7 @@ _WORKLOADS = {
     "cl15k_wic": WorkloadGraph("cl15k", "wic", 0.0, 100, 50, 7),
     "rmat20_wic": WorkloadGraph("rmat20", "wic", 0.0, 256, 50, 11),
     "rmat18_wic": WorkloadGraph("rmat18", "wic", 0.0, 256, 50, 11),
+    "rmat19_wic": WorkloadGraph("rmat19", "wic", 0.0, 256, 50, 11),
 }
 
 
