@@ -34,6 +34,7 @@ void clear_error() { g_err[0] = 0; }
 // ------------------------------------------------------------------ memory
 int g_snapshot_lists = 1;
 int g_mask_cache = 0;
+int g_fwd_lists = 1;
 
 namespace {
 int g_heavy_min_deg = 2;
@@ -253,6 +254,17 @@ sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> 
     }
     g->nh_out = (int32_t)ho.hrow.size();
     g->nh_in = (int32_t)hi.hrow.size();
+    {
+        // expected live out-arcs per snapshot over the indexed rows under
+        // the weighted cascade (sizes the forward per-snapshot lists)
+        double acc = 0.0;
+        for (int32_t x : ho.hrow)
+            for (int32_t e = rp[(size_t)x]; e < rp[(size_t)x + 1]; ++e) {
+                const int32_t y = col[(size_t)e];
+                acc += 1.0 / (double)(crp[(size_t)y + 1] - crp[(size_t)y]);
+            }
+        g->hlive_out_wic = acc;
+    }
     g->hsum_out = ho.hpref.back();
     g->hsum_in = hi.hpref.back();
     if ((rc = upload(g->rp, rp.data(), (size_t)n + 1, st)) != SG_OK ||
@@ -345,6 +357,13 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.rdesc, st);
     ws.rd_cap = 0;
     ws.rd_on = 0;
+    dbuf_free(ws.fsoff, st);
+    dbuf_free(ws.fscan, st);
+    dbuf_free(ws.fsnbr, st);
+    dbuf_free(ws.fsvalid, st);
+    ws.fsoff_cap = 0;
+    ws.fsnbr_cap = 0;
+    ws.fl_on = 0;
     ws.lm_on = 0;
     dbuf_free(ws.slot_vis, st);
     dbuf_free(ws.slot_qa, st);
@@ -378,6 +397,10 @@ GraphView view_of(const sg_graph *g, const sg_workspace &ws, int heavy_on)
     v.lm_out = ws.lm_on ? ws.lm_out.p : nullptr;
     v.lm_in = ws.lm_on ? ws.lm_in.p : nullptr;
     v.rdesc = (heavy_on && ws.rd_on) ? ws.rdesc.p : nullptr;
+    const bool fl = heavy_on && ws.fl_on;
+    v.fsoff = fl ? ws.fsoff.p : nullptr;
+    v.fsnbr = fl ? ws.fsnbr.p : nullptr;
+    v.fsvalid = fl ? ws.fsvalid.p : nullptr;
     return v;
 }
 
@@ -496,6 +519,13 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
     if (heavy_index_enabled(g, W)) {
         b += (size_t)(g->hsum_out + g->hsum_in) * W * 12 + (size_t)(g->nh_out + g->nh_in) * W * 4;
         b += (size_t)g->n * W * 16;  // forward row descriptors
+        {
+            // forward per-snapshot lists (upper bound: WIC expectation or all arcs)
+            const size_t nq = (size_t)g->n * 64 * W + 1;
+            const double want = 1.5 * 64.0 * W * std::max(g->hlive_out_wic, 0.1 * (double)g->hsum_out) + (1u << 20);
+            const double fb = want * 4.0 + (double)(2 * nq + nq / 1024 + 16) * 8.0;
+            if (g_fwd_lists && fb <= 8.0 * (double)(1ull << 30)) b += (size_t)fb;
+        }
         const size_t nq = (size_t)g->nh_in * W64 + 1;
         b += nq * 16 + ((size_t)1 << 20) * 4 + (size_t)(1.5 * 64.0 * W * (double)g->nh_in) * 4;
     }
@@ -600,6 +630,41 @@ sg_status ensure_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, 
     return SG_OK;
 }
 
+// Forward per-snapshot live lists of the indexed out-rows, node-indexed
+// (offsets for n * 64W (node, snapshot) pairs).  The list buffer holds 1.5x
+// the expected live (arc, snapshot) pairs plus slack; a query that exceeds
+// it marks the lists invalid and expands through the index instead.
+// Skipped when offsets, counts and lists would pass 8 GiB.
+sg_status ensure_fwd_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model,
+                           cudaStream_t st)
+{
+    ws.fl_on = 0;
+    if (!g_fwd_lists || g->nh_out == 0) return SG_OK;
+    const double R = 64.0 * co.W;
+    const double expect = model == MODEL_WIC ? R * g->hlive_out_wic : R * p_uic * (double)g->hsum_out;
+    const size_t want = (size_t)(expect * 1.5) + (1u << 20);
+    const size_t nq = (size_t)g->n * 64 * co.W + 1;
+    const size_t scan = nq + nq / 1024 + 16;
+    if ((double)want * 4.0 + (double)(nq + scan) * 8.0 > 8.0 * (double)(1ull << 30)) return SG_OK;
+    if (ws.fsoff_cap < nq) {
+        dbuf_free(ws.fsoff, st);
+        dbuf_free(ws.fscan, st);
+        ws.fsoff_cap = 0;
+        SG_TRY(dbuf_alloc(ws.fsoff, nq, st));
+        SG_TRY(dbuf_alloc(ws.fscan, scan, st));
+        ws.fsoff_cap = nq;
+    }
+    if (ws.fsnbr_cap < want) {
+        dbuf_free(ws.fsnbr, st);
+        ws.fsnbr_cap = 0;
+        SG_TRY(dbuf_alloc(ws.fsnbr, want, st));
+        ws.fsnbr_cap = want;
+    }
+    if (!ws.fsvalid.p) SG_TRY(dbuf_alloc(ws.fsvalid, 1, st));
+    ws.fl_on = 1;
+    return SG_OK;
+}
+
 sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out)
 {
     if (R < 1 || R >= (1 << 24)) {
@@ -693,6 +758,16 @@ sg_status sg_set_snapshot_lists(int32_t enable)
         return SG_EINVAL;
     }
     g_snapshot_lists = enable;
+    return SG_OK;
+}
+
+sg_status sg_set_forward_lists(int32_t enable)
+{
+    if (enable != 0 && enable != 1) {
+        set_error("forward lists switch must be 0 or 1");
+        return SG_EINVAL;
+    }
+    g_fwd_lists = enable;
     return SG_OK;
 }
 
@@ -872,6 +947,8 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
     ws.slists_on = 0;
     if (heavy_on && g_snapshot_lists) SG_TRY(ensure_snapshot_lists(g, ws, co, c.p, model, st));
+    ws.fl_on = 0;
+    if (heavy_on) SG_TRY(ensure_fwd_lists(g, ws, co, c.p, model, st));
     SG_TRY(ensure_mask_cache(g, ws, co.W, st));
     if (prepare_only) return SG_OK;
     // events: 0 start, 1 after index, 2 after init tier 1, 3 after init,
@@ -913,6 +990,7 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
         SG_TRY(run_row_desc(g, ws, co, st));
         ws.rd_on = 1;
     }
+    if (ws.fl_on) SG_TRY(run_fwd_lists(g, ws, co, st));
     if (ws.slists_on) SG_TRY(run_snapshot_lists(g, ws, co, st));
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_index, st));
@@ -1133,6 +1211,8 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
     ws.slists_on = 0;
+    ws.fl_on = 0;
+    if (heavy_on) SG_TRY(ensure_fwd_lists(g, ws, co, c.p, model, st));
     SG_TRY(ensure_mask_cache(g, ws, co.W, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
@@ -1141,6 +1221,7 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
         SG_TRY(run_row_desc(g, ws, co, st));
         ws.rd_on = 1;
     }
+    if (ws.fl_on) SG_TRY(run_fwd_lists(g, ws, co, st));
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));

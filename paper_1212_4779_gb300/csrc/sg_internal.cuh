@@ -139,6 +139,12 @@ struct GraphView {
     // rdesc[w*n + x] = {segment base (lo, hi), elements to expand for word w,
     // out-degree | (indexed << 31)}
     const int4 *rdesc;
+    // forward per-snapshot live lists (null when off): the live out-arcs of
+    // node x in snapshot r are fsnbr[fsoff[x*64W + r] .. fsoff[x*64W + r + 1])
+    // for every indexed row x; *fsvalid = 1 once built completely
+    const long long *fsoff;
+    const int32_t *fsnbr;
+    const int32_t *fsvalid;
 };
 
 // Counters kept on the device during one call (zeroed at the start).
@@ -205,6 +211,11 @@ struct sg_workspace {
     size_t soff_cap = 0, snbr_cap = 0;
     int32_t slists_on = 0;    // built for the current query
     sgi::DBuf<int4> rdesc;    // [W][n] forward row descriptors (with the heavy-row index)
+    // forward per-snapshot live lists of indexed rows, node-indexed
+    sgi::DBuf<long long> fsoff, fscan;
+    sgi::DBuf<int32_t> fsnbr, fsvalid;
+    size_t fsoff_cap = 0, fsnbr_cap = 0;
+    int32_t fl_on = 0;        // built for the current query
     int32_t rd_cap = 0;
     int32_t rd_on = 0;
     // live-mask cache, [W][m] per direction (optional)
@@ -230,6 +241,7 @@ struct sg_graph {
     int32_t heavy_min_deg = 0;
     int32_t nh_out = 0, nh_in = 0;
     long long hsum_out = 0, hsum_in = 0;   // sum of heavy-row degrees
+    double hlive_out_wic = 0;              // sum over heavy out-rows' arcs of 1 / indeg(destination)
     sgi::DBuf<int32_t> hid_out, hrow_out, hid_in, hrow_in;
     sgi::DBuf<long long> hpref_out, hpref_in;
     sgi::DBuf<int32_t> hcpref_out, hcpref_in;  // prefix of ceil(deg / index-build block) per heavy row
@@ -257,12 +269,16 @@ extern int g_landmarks;
 extern int g_snapshot_lists;
 // nonzero: queries build and use the live-mask cache when it fits
 extern int g_mask_cache;
+// nonzero: queries build and use forward per-snapshot live lists when they fit
+extern int g_fwd_lists;
 
 // kernels (sg_kernels.cu)
 sg_status run_heavy_index(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
 sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
 sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
 sg_status run_row_desc(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
+sg_status run_fwd_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
+sg_status ensure_fwd_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model, cudaStream_t st);
 sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S, int32_t ns, long long *d_total,
                      unsigned long long *d_edges, cudaStream_t st);
 // Walk from d_S over all W words (FWD_GROUPS blocks per word) on the query's

@@ -53,6 +53,10 @@ constexpr int T1_LOGC = 9;   // tier-1 table: 512 slots per warp (shared memory)
 constexpr int WE_THREADS = 128;
 constexpr int HB_ARCS = 1024;  // heavy-index build: arcs per work item
 constexpr int MAX_LMK = 8;     // landmarks for the initial gains
+// An initial-gain task expands a node whose state has at most this many
+// snapshot bits through the per-snapshot live lists, one bit at a time
+// (the other bits go back to pending); denser states scan the word's index.
+constexpr int SPARSE_BITS = 4;
 
 // ------------------------------------------------------------------ coins
 // High 32 bits of splitmix64(base ^ (r << 40)) (Steele, Lea, Flood 2014,
@@ -178,6 +182,11 @@ __device__ __forceinline__ uint64_t elem(const GraphView &g, const Coins &co, lo
         y = __ldg(hv.snbr + base + j);
         return F;
     }
+    if (DIR == DIR_FWD && SLICE == SLICE_SNAP && heavy == 3) {
+        // one snapshot's live out-arcs; F is that snapshot's bit
+        y = __ldg(g.fsnbr + base + j);
+        return F;
+    }
     const unsigned long long *lm = DIR == DIR_FWD ? g.lm_out : g.lm_in;
     if (!heavy && lm) {
         // cached live bits of the arc at this CSR / CSC position
@@ -199,6 +208,28 @@ __device__ __forceinline__ uint64_t elem(const GraphView &g, const Coins &co, lo
     if (SLICE == SLICE_SNAP) return live_bits(co, eid, rs, F, tm1);
     if (co.none_live) return 0ull;
     return coin_hi32(co.seed ^ (uint64_t)eid, rs) <= tm1 ? F : 0ull;
+}
+
+// Initial gains: a node x with state F of at most SPARSE_BITS bits and an
+// indexed row takes its lowest bit through that snapshot's live list; the
+// caller puts the other bits back to pending.  Returns the remaining bits
+// (F is then the single bit, rr the list), or F unchanged otherwise with
+// rest 0 and rr untouched.
+template <int DIR, int SLICE>
+__device__ __forceinline__ uint64_t sparse_pick(const GraphView &g, const Coins &co, int x, int word, uint64_t &F,
+                                                Row &rr)
+{
+    if (DIR != DIR_FWD || SLICE != SLICE_SNAP || !g.fsoff || !F || __popcll(F) > SPARSE_BITS) return 0;
+    const int b = __ffsll((long long)F) - 1;
+    const long long q = (long long)x * (64 * co.W) + 64 * word + b;
+    const long long o0 = __ldg(g.fsoff + q), o1 = __ldg(g.fsoff + q + 1);
+    if (rr.heavy != 1) return 0;  // rows without an index have no lists
+    const uint64_t rest = F & (F - 1);
+    F = 1ull << b;
+    rr.base = o0;
+    rr.vdeg = (int)(o1 - o0);
+    rr.heavy = 3;
+    return rest;
 }
 
 template <class T>
@@ -456,6 +487,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
     uint64_t xany = 0;  // snapshots credited through some landmark (fixed for the task)
     if (TASK == TASK_INIT)
         for (int i = 0; i < a.lmk_k; ++i) xany |= T.xbits[i];
+    const bool flists = TASK == TASK_INIT && g.fsoff && __ldg(g.fsvalid);
     unsigned long long tedges = 0;
     int qhead = 0;
     while (true) {
@@ -472,7 +504,14 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
             const int x = T.key[h];
             F = T.pend[h];
             T.pend[h] = 0;
-            const Row rr = row_ref<DIR, MODEL, SLICE>(g, co, x, word, rs);
+            Row rr = row_ref<DIR, MODEL, SLICE>(g, co, x, word, rs);
+            if (TASK == TASK_INIT && flists) {
+                const uint64_t rest = sparse_pick<DIR, SLICE>(g, co, x, word, F, rr);
+                if (rest) {  // the other bits are expanded when x is popped again
+                    T.pend[h] = rest;
+                    T.queue[atomicAdd(&T.ctr[0], 1) & (C - 1)] = (unsigned short)h;
+                }
+            }
             base = rr.base;
             vdeg = rr.vdeg;
             heavy = rr.heavy;
@@ -1069,6 +1108,7 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
     uint64_t xany = 0;  // snapshots credited through some landmark (fixed for the task)
     if (TASK == TASK_INIT)
         for (int i = 0; i < a.lmk_k; ++i) xany |= c.xbits[i];
+    const bool flists = TASK == TASK_INIT && g.fsoff && __ldg(g.fsvalid);
     while (true) {
         int nb = 0, qb = 0;
         if (lane == 0) {
@@ -1125,7 +1165,14 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
             const int idx = T.take(qb + lane, c);
             if (idx >= 0) {
                 F = atomicExch(&T.pendr(idx), 0ull);
-                const Row rr = row_ref<DIR, MODEL, SLICE>(g, co, T.node(idx), word, rs);
+                Row rr = row_ref<DIR, MODEL, SLICE>(g, co, T.node(idx), word, rs);
+                if (TASK == TASK_INIT && flists) {
+                    const uint64_t rest = sparse_pick<DIR, SLICE>(g, co, T.node(idx), word, F, rr);
+                    // the other bits go back to pending; re-queue unless an
+                    // arrival already did
+                    if (rest && atomicOr(&T.pendr(idx), (unsigned long long)rest) == 0ull)
+                        T.put(atomicAdd(&c.tail, 1), idx);
+                }
                 base = rr.base;
                 vdeg = F ? rr.vdeg : 0;
                 heavy = rr.heavy;
@@ -1855,12 +1902,16 @@ __global__ void __launch_bounds__(256) heavy_index_kernel(GraphView g, Coins co,
 // From the per-word index of heavy in-rows: count the live in-arcs of every
 // (heavy row, snapshot), scan, and fill.  mode 0 counts into scnt, mode 1
 // fills snbr using scnt as cursors (reset to zero in between).
+// by_node 0: lists indexed by heavy-row ordinal h (q = h*64W + r), nq =
+// nh*64W; by_node 1: indexed by the row's node (q = x*64W + r), nq = n*64W.
+// rp holds the row offsets of the index's direction (for the degree).
 __global__ void __launch_bounds__(256) snapshot_lists_kernel(Coins co, int nh, const int32_t *hcnt,
                                                              const int32_t *hnbr, const unsigned long long *hmask,
                                                              const long long *hpref, const int32_t *crp,
                                                              const int32_t *hrow, long long *scnt,
                                                              const long long *soff, int32_t *snbr,
-                                                             long long cap, int32_t *svalid, int mode)
+                                                             long long cap, int32_t *svalid, int mode,
+                                                             int by_node, long long nq)
 {
     const int lane = threadIdx.x & 31;
     const long long nseg = (long long)nh * co.W;
@@ -1879,7 +1930,7 @@ __global__ void __launch_bounds__(256) snapshot_lists_kernel(Coins co, int nh, c
             while (M) {
                 const int b = __ffsll((long long)M) - 1;
                 M &= M - 1;
-                const long long q = (long long)h * R64 + 64 * w + b;
+                const long long q = (long long)(by_node ? x : h) * R64 + 64 * w + b;
                 if (mode == 0) {
                     atomicAdd((unsigned long long *)&scnt[q], 1ull);
                 } else {
@@ -1889,7 +1940,7 @@ __global__ void __launch_bounds__(256) snapshot_lists_kernel(Coins co, int nh, c
             }
         }
     }
-    if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) *svalid = soff[(long long)nh * R64] <= cap ? 1 : 0;
+    if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) *svalid = soff[nq] <= cap ? 1 : 0;
 }
 
 // Exclusive scan of int64 counts (in place into `out`), three phases.
@@ -2288,6 +2339,31 @@ sg_status run_walk(sg_graph *g, const sg_workspace &ws, const Coins &co, int mod
     return SG_OK;
 }
 
+sg_status run_fwd_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st)
+{
+    const int nh = g->nh_out;
+    const long long nq = g->n * 64LL * co.W;
+    const long long n1 = nq + 1;
+    const long long nb = (n1 + SC_T - 1) / SC_T;
+    long long *cnt = ws.fscan.p, *sums = ws.fscan.p + n1;
+    const int grid = g->num_sms * 8;
+    SG_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)n1 * 8, st));
+    snapshot_lists_kernel<<<grid, 256, 0, st>>>(co, nh, ws.hcnt_out.p, ws.hnbr_out.p, ws.hmask_out.p, g->hpref_out.p,
+                                                g->rp.p, g->hrow_out.p, cnt, nullptr, nullptr, 0, nullptr, 0, 1, nq);
+    SG_CUDA_TRY(cudaGetLastError());
+    scan_blocks_kernel<<<(unsigned)nb, SC_T, 0, st>>>(cnt, ws.fsoff.p, n1, sums);
+    scan_sums_kernel<<<1, SC_T, 0, st>>>(sums, nb, sums + nb);
+    scan_add_kernel<<<(unsigned)nb, SC_T, 0, st>>>(ws.fsoff.p, n1, sums);
+    SG_CUDA_TRY(cudaGetLastError());
+    SG_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)nq * 8, st));
+    snapshot_lists_kernel<<<grid, 256, 0, st>>>(co, nh, ws.hcnt_out.p, ws.hnbr_out.p, ws.hmask_out.p, g->hpref_out.p,
+                                                g->rp.p, g->hrow_out.p, cnt, ws.fsoff.p, ws.fsnbr.p,
+                                                (long long)ws.fsnbr_cap, ws.fsvalid.p, 1, 1, nq);
+    SG_CUDA_TRY(cudaGetLastError());
+    g_launches += 5;
+    return SG_OK;
+}
+
 sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st)
 {
     const int nh = g->nh_in;
@@ -2297,7 +2373,7 @@ sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cud
     const int grid = g->num_sms * 8;
     snapshot_lists_kernel<<<grid, 256, 0, st>>>(co, nh, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p, g->hpref_in.p,
                                                 g->crp.p, g->hrow_in.p, ws.scan_tmp.p, nullptr, nullptr, 0, nullptr,
-                                                0);
+                                                0, 0, nq);
     SG_CUDA_TRY(cudaGetLastError());
     // offsets: soff[0..nq] = exclusive scan of counts (nq+1 entries, last = total)
     const long long n1 = nq + 1;
@@ -2311,7 +2387,7 @@ sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cud
     SG_CUDA_TRY(cudaMemsetAsync(ws.scan_tmp.p, 0, (size_t)nq * 8, st));
     snapshot_lists_kernel<<<grid, 256, 0, st>>>(co, nh, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p, g->hpref_in.p,
                                                 g->crp.p, g->hrow_in.p, ws.scan_tmp.p, ws.soff.p, ws.snbr.p,
-                                                (long long)ws.snbr_cap, ws.svalid.p, 1);
+                                                (long long)ws.snbr_cap, ws.svalid.p, 1, 0, nq);
     SG_CUDA_TRY(cudaGetLastError());
     g_launches += 5;
     return SG_OK;

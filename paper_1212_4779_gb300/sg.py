@@ -31,7 +31,7 @@ EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg
            "sg_batch_capture", "sg_batch_launch", "sg_batch_free", "sg_server_create", "sg_server_submit",
            "sg_server_poll", "sg_server_counts", "sg_server_destroy",
            "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-           "sg_set_snapshot_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+           "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
            "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
 
 
@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
         L.sg_set_landmarks.argtypes = [i32]
         L.sg_set_snapshot_lists.argtypes = [i32]
         L.sg_set_mask_cache.argtypes = [i32]
+        L.sg_set_forward_lists.argtypes = [i32]
         L.sg_spread.argtypes = [P, i32, sg_cascade, u64, P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(u64)]
         L.sg_select_celf.argtypes = [P, i32, i32, sg_cascade, u64, P, P, P, ctypes.POINTER(i64), P]
         L.sg_argmax_noalloc.argtypes = [P, i64, P, P, P]
@@ -138,7 +139,7 @@ def lib() -> ctypes.CDLL:
         for name in ("sg_workspace_create", "sg_workspace_bytes", "sg_select_ws", "sg_select_batch",
                      "sg_batch_capture", "sg_batch_launch", "sg_server_create", "sg_server_submit",
                      "sg_server_poll", "sg_server_counts", "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-                     "sg_set_snapshot_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+                     "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
                      "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -258,6 +259,11 @@ def sg_set_engine_limits(tier1_keys: int = 256, tier2_keys: int = 4096):
 def sg_set_snapshot_lists(enable: int = 1):
     """Per-snapshot live in-lists of heavy rows for the reverse pass (0: off)."""
     _check(lib().sg_set_snapshot_lists(int(enable)))
+
+
+def sg_set_forward_lists(enable: int = 1):
+    """Forward per-snapshot live lists for sparse initial-gain expansions (0: off)."""
+    _check(lib().sg_set_forward_lists(int(enable)))
 
 
 def sg_set_mask_cache(enable: int = 0):

@@ -81,6 +81,8 @@ def test_setters_validate_without_gpu(libpath):
 
     L = sg.lib()
     assert L.sg_set_mask_cache(2) == sg.SG_EINVAL
+    assert L.sg_set_forward_lists(2) == sg.SG_EINVAL
+    assert L.sg_set_forward_lists(1) == sg.SG_OK
     assert L.sg_set_mask_cache(-1) == sg.SG_EINVAL
     assert L.sg_set_snapshot_lists(3) == sg.SG_EINVAL
     assert L.sg_set_landmarks(9) == sg.SG_EINVAL

@@ -126,6 +126,30 @@ def limits(sg):
     sg.sg_set_landmarks(8)
     sg.sg_set_snapshot_lists(1)
     sg.sg_set_mask_cache(0)
+    sg.sg_set_forward_lists(1)
+
+
+@pytest.mark.parametrize("fl", [0, 1])
+@pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01", "er2k_uic0.1"])
+def test_forward_lists_give_identical_results(sg, limits, name, fl):
+    """Sparse expansions through the forward per-snapshot lists (one bit at
+    a time, the rest re-queued) give the oracle's initial gains, seeds,
+    gains and counters in every tier, with the lists on and off."""
+    wl = inputs.workload(name)
+    n, s, d = wl.graph()
+    g, o = _both(sg, n, s, d, wl.model, wl.p)
+    sg.sg_set_forward_lists(fl)
+    ref = o.select(wl.R, 10, wl.seed, mode=oracle.DU, want_init=True)
+    for t1, t2 in [(256, 4096), (2, 16)]:
+        limits(t1, t2)
+        for lmk in (0, 8):
+            sg.sg_set_landmarks(lmk)
+            s_gpu, ed = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
+            assert np.array_equal(s_gpu, ref["s_init"]) and ed == int(ref["counters"][0])
+            res = g.select(wl.R, 10, wl.model, wl.p, wl.seed, stats=True)
+            assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+            got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+            assert got == [int(x) for x in ref["counters"]]
 
 
 @pytest.mark.parametrize("heavy", [0, 2])
