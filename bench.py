@@ -43,11 +43,13 @@ METRIC = "GTEPS (snapshot-edges/s) of StaticGreedyDU k-seed selection"
 UNIT = "GTEPS"
 
 # Algorithmic bytes per expanded element (one arc, or one live-index entry,
-# for one 64-bit task word) plus the neighbour's 8-byte state word: an arc
-# record is 8 bytes (destination and threshold); a live-index entry (heavy
-# rows) or a cached arc is a 4-byte destination and an 8-byte live mask.
+# for one 64-bit task word, or one per-snapshot list entry) plus the
+# neighbour's 8-byte state word: an arc record is 8 bytes (destination and
+# threshold); a live-index entry (heavy rows) or a cached arc is a 4-byte
+# destination and an 8-byte live mask; a list entry is a 4-byte destination.
 BYTES_PER_ELEMENT = 16
 BYTES_PER_ELEMENT_INDEXED = 20
+BYTES_PER_LIST_ELEMENT = 12
 LANES_PER_SM = 128  # INT32 lanes per SM per clock (4 SMSP x 32)
 
 
@@ -553,7 +555,8 @@ def main():
     # (an 8-byte arc record or index entry plus the neighbour's 8-byte state)
     t3_ms = float(np.mean(t_t3))
     bpe = BYTES_PER_ELEMENT_INDEXED if (st_last["mask_cache"] or st_last["heavy_index"]) else BYTES_PER_ELEMENT
-    t3_bytes = st_last["work_elems"][0][2] * bpe
+    t3_list = st_last["list_elems"][2]
+    t3_bytes = (st_last["work_elems"][0][2] - t3_list) * bpe + t3_list * BYTES_PER_LIST_ELEMENT
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = t3_bytes / (t3_ms / 1e3) / 1e9 if t3_ms > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": "coop_engine_kernel<dense> (initial gains, tier 3)",
@@ -562,7 +565,8 @@ def main():
                 "traffic_source": "profiles/coop_engine_tier3_init_rmat20_traffic.md (full-size ncu capture)",
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
                 "kernel_ms": t3_ms, "elements_per_launch": st_last["work_elems"][0][2],
-                "bytes_per_element": bpe}
+                "list_elements_per_launch": t3_list, "bytes_per_element": bpe,
+                "bytes_per_list_element": BYTES_PER_LIST_ELEMENT, "algorithmic_bytes_per_launch": t3_bytes}
     t1_ms = float(np.mean(t_t1))
     alu_view = {"kernel": "warp_engine_kernel (initial gains, tier 1)", "kernel_ms": t1_ms,
                 "elements_per_launch": st_last["work_elems"][0][0],

@@ -89,6 +89,7 @@ typedef struct {
     float ms_init_tier2;        /* device time of the initial-gain tier-2 launch */
     float ms_init_tier3;        /* device time of the initial-gain tier-3 launch */
     int32_t reserved2;
+    uint64_t list_elems[3];     /* initial gains, tier 1..3: of work_elems, per-snapshot live-list entries */
 } sg_stats;
 
 /* Opaque graph handle; owns its device memory until sg_free_graph. */

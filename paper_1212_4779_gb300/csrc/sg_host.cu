@@ -1026,6 +1026,7 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
         stats->mask_cache = ws.lm_on;
         memcpy(stats->work_keys, h.work_keys, sizeof(h.work_keys));
         memcpy(stats->work_elems, h.work_elems, sizeof(h.work_elems));
+        memcpy(stats->list_elems, h.list_elems, sizeof(h.list_elems));
         cudaEventElapsedTime(&stats->ms_index, e_start, e_index);
         cudaEventElapsedTime(&stats->ms_init, e_start, e_init);
         cudaEventElapsedTime(&stats->ms_landmarks, e_index, tev.start);

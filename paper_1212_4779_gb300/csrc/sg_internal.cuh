@@ -158,6 +158,7 @@ struct Ctl {
     unsigned long long rev_tasks;         // target-sliced reverse tasks, all rounds
     unsigned long long work_keys[2][3];   // [init, reverse][tier]: nodes held in task tables
     unsigned long long work_elems[2][3];  // [init, reverse][tier]: arcs / index entries expanded
+    unsigned long long list_elems[3];     // initial gains, per tier: of those, per-snapshot list entries
     unsigned long long t1_next;   // dynamic task counter, tier 1
     unsigned long long l1_count;  // tasks handed from tier 1 to tier 2
     unsigned long long l1_next;

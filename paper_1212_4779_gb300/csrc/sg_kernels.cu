@@ -424,7 +424,8 @@ __device__ __forceinline__ int table_slot(const WTab &T, int y, int limit)
 // the task was applied; the table is clean again either way).
 template <int LOGC, int DIR, int MODEL, int TASK>
 __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, long long t, int lane,
-                                          unsigned long long &edges_acc, unsigned long long &wk)
+                                          unsigned long long &edges_acc, unsigned long long &wk,
+                                          unsigned long long &lel)
 {
     constexpr int C = 1 << LOGC;
     const int LIMIT = a.limit;  // in [1, C/2]
@@ -511,6 +512,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
                     T.pend[h] = rest;
                     T.queue[atomicAdd(&T.ctr[0], 1) & (C - 1)] = (unsigned short)h;
                 }
+                if (rr.heavy == 3) lel += (unsigned long long)rr.vdeg;
             }
             base = rr.base;
             vdeg = rr.vdeg;
@@ -643,7 +645,7 @@ __global__ void __launch_bounds__(WE_THREADS) warp_engine_kernel(EngineArgs a, i
     __syncwarp();
     Ctl *ctl = a.ctl;
     const long long ntasks = TASK == TASK_INIT ? a.ntasks : *(volatile long long *)&ctl->du_total;
-    unsigned long long edges = 0, wk = 0;
+    unsigned long long edges = 0, wk = 0, lel = 0;
     while (true) {
         long long base = 0;
         if (lane == 0) base = (long long)atomicAdd(&ctl->t1_next, (unsigned long long)chunk);
@@ -651,12 +653,16 @@ __global__ void __launch_bounds__(WE_THREADS) warp_engine_kernel(EngineArgs a, i
         if (base >= ntasks) break;
         const long long tend = min(base + (long long)chunk, ntasks);
         for (long long t = base; t < tend; ++t) {
-            const bool ovf = warp_task<LOGC, DIR, MODEL, TASK>(a, T, t, lane, edges, wk);
+            const bool ovf = warp_task<LOGC, DIR, MODEL, TASK>(a, T, t, lane, edges, wk, lel);
             if (ovf && lane == 0) a.list1[atomicAdd(&ctl->l1_count, 1ull)] = (int32_t)t;
         }
     }
     edges = warp_sum(edges);
     if (lane == 0 && edges) atomicAdd(TASK == TASK_INIT ? &ctl->init_edges : &ctl->rev_edges, edges);
+    if (TASK == TASK_INIT) {
+        lel = warp_sum(lel);
+        if (lane == 0 && lel) atomicAdd(&ctl->list_elems[0], lel);
+    }
     if (lane < 2 && wk)
         atomicAdd(lane == 0 ? &ctl->work_keys[TASK == TASK_INIT ? 0 : 1][0] : &ctl->work_elems[TASK == TASK_INIT ? 0 : 1][0],
                   wk);
@@ -814,6 +820,8 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
     }
     unsigned long long edges = 0;
     int32_t *cur = w.qa, *nxt = w.qb;
+    const bool flists = DIR == DIR_FWD && (TASK == TASK_FWD || TASK == TASK_LMK || TASK == TASK_SPREAD) && g.fsoff &&
+                        __ldg(g.fsvalid);
     __syncthreads();
     while (true) {
         const int L = S.qlen;
@@ -823,9 +831,16 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
             int vd = 0;
             if (i < L) {
                 const int x = cur[i];
-                const uint64_t F = w.gm == ~0ull ? atomicExch(&w.pend[x], 0ull)
-                                                 : (atomicAnd(&w.pend[x], ~w.gm) & w.gm);
-                const Row rr = row_ref<DIR, MODEL, SLICE>(g, co, x, word, rs);
+                uint64_t F = w.gm == ~0ull ? atomicExch(&w.pend[x], 0ull)
+                                           : (atomicAnd(&w.pend[x], ~w.gm) & w.gm);
+                Row rr = row_ref<DIR, MODEL, SLICE>(g, co, x, word, rs);
+                if (flists) {
+                    // sparse state: one snapshot's live out-arcs now, the
+                    // other bits at the next level (reachability only)
+                    const uint64_t rest = sparse_pick<DIR, SLICE>(g, co, x, word, F, rr);
+                    if (rest && (atomicOr(&w.pend[x], (unsigned long long)rest) & w.gm) == 0ull)
+                        nxt[atomicAdd(&S.qnext, 1)] = x;
+                }
                 vd = F ? rr.vdeg : 0;
                 S.F[tid] = F;
                 S.base[tid] = rr.base;
@@ -1097,7 +1112,8 @@ __device__ __forceinline__ void coop_seed(CoopTab<TAB> &T, CoopCtl &c, int y, ui
 // claimed.
 template <int TAB, int DIR, int MODEL, int TASK>
 __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, CoopTab<TAB> &T, CoopCtl &c, int word,
-                                                          uint32_t rs, int limit, unsigned long long &elems)
+                                                          uint32_t rs, int limit, unsigned long long &elems,
+                                                          unsigned long long &lel)
 {
     constexpr int SLICE = TASK == TASK_REVT ? SLICE_TGT : SLICE_SNAP;
     const GraphView &g = a.g;
@@ -1172,6 +1188,7 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                     // arrival already did
                     if (rest && atomicOr(&T.pendr(idx), (unsigned long long)rest) == 0ull)
                         T.put(atomicAdd(&c.tail, 1), idx);
+                    if (rr.heavy == 3 && F) lel += (unsigned long long)rr.vdeg;
                 }
                 base = rr.base;
                 vdeg = F ? rr.vdeg : 0;
@@ -1269,7 +1286,7 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
     const long long count = (long long)*(volatile unsigned long long *)(TAB == TAB_HASH ? &ctl->l1_count : &ctl->l2_count);
     unsigned long long *next = TAB == TAB_HASH ? &ctl->l1_next : &ctl->l2_next;
     const int32_t *list = TAB == TAB_HASH ? a.list1 : a.list2;
-    unsigned long long edges = 0, wk_keys = 0, wk_elems = 0;
+    unsigned long long edges = 0, wk_keys = 0, wk_elems = 0, lel = 0;
     __syncthreads();
     while (true) {
         if (tid == 0) sh_t = (long long)atomicAdd(next, 1ull);
@@ -1305,7 +1322,7 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
             if (tid < cnt) coop_seed<TAB>(T, c, a.tl[b0 + tid], 1ull << tid, limit);
         }
         __syncthreads();
-        unsigned long long tedges = coop_expand<TAB, DIR, MODEL, TASK>(a, T, c, word, rs, limit, wk_elems);
+        unsigned long long tedges = coop_expand<TAB, DIR, MODEL, TASK>(a, T, c, word, rs, limit, wk_elems, lel);
         __syncthreads();
         const int ovf = c.overflow | c.err;
         const int nt = c.nkeys;
@@ -1358,6 +1375,10 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
     }
     edges = warp_sum(edges);
     wk_elems = warp_sum(wk_elems);
+    if (TASK == TASK_INIT) {
+        lel = warp_sum(lel);
+        if (lane == 0 && lel) atomicAdd(&ctl->list_elems[TAB == TAB_HASH ? 1 : 2], lel);
+    }
     if (lane == 0) red_ull[wid] = edges;
     if (lane == 0) red_ll[wid] = (long long)wk_elems;
     __syncthreads();

@@ -56,13 +56,14 @@ class sg_stats(ctypes.Structure):
                 ("heavy_index", ctypes.c_int32), ("mask_cache", ctypes.c_int32),
                 ("work_keys", (ctypes.c_uint64 * 3) * 2), ("work_elems", (ctypes.c_uint64 * 3) * 2),
                 ("ms_landmarks", ctypes.c_float), ("ms_init_tier2", ctypes.c_float),
-                ("ms_init_tier3", ctypes.c_float), ("reserved2", ctypes.c_int32)]
+                ("ms_init_tier3", ctypes.c_float), ("reserved2", ctypes.c_int32),
+                ("list_elems", ctypes.c_uint64 * 3)]
 
     def as_dict(self):
         out = {}
         for k, _ in self._fields_:
             v = getattr(self, k)
-            out[k] = [list(row) for row in v] if k.startswith("work_") else v
+            out[k] = [list(row) for row in v] if k.startswith("work_") else (list(v) if k == "list_elems" else v)
         return out
 
 
