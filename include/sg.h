@@ -47,7 +47,16 @@ typedef enum {
     SG_EINTERNAL = 6  /* a device-side consistency check failed */
 } sg_status;
 
-typedef enum { SG_UIC = 0, SG_WIC = 1 } sg_model;
+/* SG_UIC: every arc live with probability p, one coin per arc.
+ * SG_WIC: arc u->v live with probability 1 / indeg(v).
+ * SG_UIC_UNDIRECTED: the undirected variant -- a symmetric graph (every
+ *   arc's reverse present) with one coin per undirected edge: both arcs use
+ *   the coin of the lower of their two canonical arc ids, so each snapshot
+ *   is undirected and reach sets are connected components.  sg_select,
+ *   sg_init_gains, sg_spread, sg_live_masks, batches and the server accept
+ *   it (sg_select runs it by per-snapshot union-find); sg_select_celf does
+ *   not.  A graph that is not symmetric gives SG_EINVAL. */
+typedef enum { SG_UIC = 0, SG_WIC = 1, SG_UIC_UNDIRECTED = 2 } sg_model;
 
 /* Cascade model: UIC uses p in [0, 1] for every arc; WIC ignores p and uses
  * 1/indeg(v) for every arc u -> v (Section 3.4.1 and Section 5.1). */

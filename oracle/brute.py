@@ -35,9 +35,23 @@ def canonical_arcs(src, dst):
     return sorted({(int(u), int(v)) for u, v in zip(src, dst) if int(u) != int(v)})
 
 
+def coin_ids(arcs, model):
+    """The id each arc's coin hashes: its own index, or for the undirected
+    variant ("uic_undirected") the smaller index of the arc and its reverse."""
+    if model != "uic_undirected":
+        return list(range(len(arcs)))
+    index = {a: i for i, a in enumerate(arcs)}
+    out = []
+    for i, (u, v) in enumerate(arcs):
+        if (v, u) not in index:
+            raise ValueError("uic_undirected needs a symmetric graph")
+        out.append(min(i, index[(v, u)]))
+    return out
+
+
 def thresholds(n, arcs, model, p=0.0):
     """thr(e) in [0, 2^32]: floor(p 2^32) (UIC) or floor(2^32 / indeg(v)) (WIC)."""
-    if model == "uic":
+    if model in ("uic", "uic_undirected"):
         t = math.floor(Fraction(p) * (1 << 32))
         return [t] * len(arcs)
     indeg = [0] * n
@@ -71,10 +85,11 @@ class Brute:
         self.n = n
         self.arcs = canonical_arcs(src, dst)
         self.thr = thresholds(n, self.arcs, model, p)
+        cid = coin_ids(self.arcs, model)
         self.R = R
         self.reach = []
         for r in range(R):
-            live = [a for e, a in enumerate(self.arcs) if coin(seed, r, e, self.thr[e])]
+            live = [a for e, a in enumerate(self.arcs) if coin(seed, r, cid[e], self.thr[e])]
             self.reach.append(closure(n, live))
 
     def f(self, S) -> int:
@@ -113,18 +128,17 @@ def exact_spread(n, src, dst, model, p, S):
     arcs = canonical_arcs(src, dst)
     thr = thresholds(n, arcs, model, p)
     q = [Fraction(t, 1 << 32) for t in thr]
-    m = len(arcs)
+    cid = coin_ids(arcs, model)
+    coins = sorted(set(cid))           # one independent coin per id (an edge, when coupled)
+    slot = {c: i for i, c in enumerate(coins)}
+    m = len(coins)
     mean = Fraction(0)
     second = Fraction(0)
     for world in range(1 << m):
         prob = Fraction(1)
-        live = []
-        for e in range(m):
-            if world >> e & 1:
-                prob *= q[e]
-                live.append(arcs[e])
-            else:
-                prob *= 1 - q[e]
+        for i, c in enumerate(coins):
+            prob *= q[c] if world >> i & 1 else 1 - q[c]
+        live = [a for e, a in enumerate(arcs) if world >> slot[cid[e]] & 1]
         if prob == 0:
             continue
         reach = closure(n, live)

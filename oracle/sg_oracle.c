@@ -169,8 +169,34 @@ static void snaps_free(or_snaps *S)
     free(S);
 }
 
+/* Coupling of a symmetric canonical graph (the undirected variant): cid[e]
+ * = the lower of arc e's id and its reverse arc's id, found by binary
+ * search in the reverse arc's row.  Returns OR_EINVAL if some arc has no
+ * reverse. */
+int or_coupled_ids(int64_t n, const int64_t *rp, const int32_t *col, int64_t *cid)
+{
+    for (int64_t u = 0; u < n; u++)
+        for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
+            int32_t v = col[e];
+            int64_t lo = rp[v], hi = rp[v + 1];
+            while (lo < hi) {
+                int64_t mid = (lo + hi) / 2;
+                if (col[mid] < u) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= rp[v + 1] || col[lo] != u) return OR_EINVAL;
+            cid[e] = e < lo ? e : lo;
+        }
+    return OR_OK;
+}
+
+/* The id hashed for arc e's coin: e itself, or cid[e] when a coupling is
+ * given (the undirected variant: both arcs of an edge use the lower arc id,
+ * so one coin decides the edge in each snapshot, as Section 3.4.1 treats an
+ * undirected snapshot). */
+static uint64_t coin_of(const int64_t *cid, int64_t e) { return cid ? (uint64_t)cid[e] : (uint64_t)e; }
+
 static or_snaps *snaps_build(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
-                             int32_t r0, int32_t R, uint64_t seed, int nthreads)
+                             int32_t r0, int32_t R, uint64_t seed, int nthreads, const int64_t *cid)
 {
     or_snaps *S = (or_snaps *)calloc(1, sizeof(or_snaps));
     if (!S) return NULL;
@@ -193,7 +219,7 @@ static or_snaps *snaps_build(int64_t n, const int64_t *rp, const int32_t *col, c
         int64_t kept = 0;
         for (int64_t u = 0; u < n; u++)
             for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
-                keep[e] = (uint8_t)or_live(seed, (uint32_t)(r0 + r), (uint64_t)e, thr[e]);
+                keep[e] = (uint8_t)or_live(seed, (uint32_t)(r0 + r), coin_of(cid, e), thr[e]);
                 if (keep[e]) { orp[u + 1]++; irp[col[e] + 1]++; kept++; }
             }
         for (int64_t v = 0; v < n; v++) { orp[v + 1] += orp[v]; irp[v + 1] += irp[v]; }
@@ -423,10 +449,10 @@ static void heap_pop(or_heap *h, int64_t *b, int32_t *v, int32_t *stamp)
  * number of marginal-gain evaluations after the initial gains. */
 int or_select(int mode, int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
               int32_t R, int32_t k, uint64_t seed, int nthreads, int32_t *seeds, int64_t *gains,
-              int64_t *s_init, int64_t *s_hist, uint64_t *counters)
+              int64_t *s_init, int64_t *s_hist, uint64_t *counters, const int64_t *cid)
 {
     if (n < 1 || R < 1 || k < 1 || k > n) return OR_EINVAL;
-    or_snaps *S = snaps_build(n, rp, col, thr, 0, R, seed, nthreads);
+    or_snaps *S = snaps_build(n, rp, col, thr, 0, R, seed, nthreads, cid);
     if (!S) return OR_ENOMEM;
     int rc = OR_OK;
     int64_t *s = (int64_t *)calloc((size_t)n, sizeof(int64_t));
@@ -563,10 +589,10 @@ done:
  * initial gains. */
 int or_init_gains(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
                   int32_t r0, int32_t r1, uint64_t seed, int nthreads, int64_t *s,
-                  uint64_t *init_edges)
+                  uint64_t *init_edges, const int64_t *cid)
 {
     if (n < 1 || r0 < 0 || r1 <= r0) return OR_EINVAL;
-    or_snaps *S = snaps_build(n, rp, col, thr, r0, r1 - r0, seed, nthreads);
+    or_snaps *S = snaps_build(n, rp, col, thr, r0, r1 - r0, seed, nthreads, cid);
     if (!S) return OR_ENOMEM;
     int rc = init_gains(S, rp, nthreads, s, init_edges);
     snaps_free(S);
@@ -582,7 +608,7 @@ int or_init_gains(int64_t n, const int64_t *rp, const int32_t *col, const uint64
  * mark/queue: n-entry scratch, mark zeroed by the caller. */
 static int64_t reach_fly(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
                          uint64_t seed, uint32_t r, int32_t nsrc, const int32_t *src,
-                         uint8_t *mark, int32_t *queue, uint64_t *edges)
+                         uint8_t *mark, int32_t *queue, uint64_t *edges, const int64_t *cid)
 {
     int64_t head = 0, tail = 0;
     for (int32_t i = 0; i < nsrc; i++)
@@ -593,7 +619,7 @@ static int64_t reach_fly(int64_t n, const int64_t *rp, const int32_t *col, const
         for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
             int32_t x = col[e];
             if (mark[x]) continue;
-            if (!or_live(seed, r, (uint64_t)e, thr[e])) continue;
+            if (!or_live(seed, r, coin_of(cid, e), thr[e])) continue;
             mark[x] = 1;
             queue[tail++] = x;
         }
@@ -608,7 +634,7 @@ static int64_t reach_fly(int64_t n, const int64_t *rp, const int32_t *col, const
  * NULL) gets the snapshot-edge count sum_r sum_{u in R(G'_r, S)} outdeg(u). */
 int64_t or_spread(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
                   int32_t R, uint64_t seed, int32_t nS, const int32_t *Sset, int nthreads,
-                  uint64_t *edges)
+                  uint64_t *edges, const int64_t *cid)
 {
     int64_t total = 0;
     uint64_t ed = 0;
@@ -626,7 +652,7 @@ int64_t or_spread(int64_t n, const int64_t *rp, const int32_t *col, const uint64
 #pragma omp for schedule(dynamic, 1)
 #endif
             for (int32_t r = 0; r < R; r++)
-                total += reach_fly(n, rp, col, thr, seed, (uint32_t)r, nS, Sset, mark, queue, &ed);
+                total += reach_fly(n, rp, col, thr, seed, (uint32_t)r, nS, Sset, mark, queue, &ed, cid);
         }
         free(mark); free(queue);
     }
@@ -639,7 +665,7 @@ int64_t or_spread(int64_t n, const int64_t *rp, const int32_t *col, const uint64
  * of those sources. */
 int or_reach_sums(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
                   int32_t R, uint64_t seed, int32_t nv, const int32_t *v, int nthreads,
-                  int64_t *out, uint64_t *edges)
+                  int64_t *out, uint64_t *edges, const int64_t *cid)
 {
     uint64_t ed = 0;
     int failed = 0;
@@ -658,7 +684,7 @@ int or_reach_sums(int64_t n, const int64_t *rp, const int32_t *col, const uint64
             for (int32_t i = 0; i < nv; i++) {
                 int64_t acc = 0;
                 for (int32_t r = 0; r < R; r++)
-                    acc += reach_fly(n, rp, col, thr, seed, (uint32_t)r, 1, v + i, mark, queue, &ed);
+                    acc += reach_fly(n, rp, col, thr, seed, (uint32_t)r, 1, v + i, mark, queue, &ed, cid);
                 out[i] = acc;
             }
         }
@@ -670,7 +696,8 @@ int or_reach_sums(int64_t n, const int64_t *rp, const int32_t *col, const uint64
 
 /* Coins as 64-snapshot words: bit b of masks[e*W + w] is the coin of arc e
  * in snapshot 64w+b, for snapshots < R (higher bits of the last word 0). */
-int or_live_masks(int64_t m, const uint64_t *thr, int32_t R, uint64_t seed, uint64_t *masks)
+int or_live_masks(int64_t m, const uint64_t *thr, int32_t R, uint64_t seed, uint64_t *masks,
+                  const int64_t *cid)
 {
     int32_t W = (R + 63) / 64;
     for (int64_t e = 0; e < m; e++)
@@ -678,7 +705,7 @@ int or_live_masks(int64_t m, const uint64_t *thr, int32_t R, uint64_t seed, uint
             uint64_t word = 0;
             for (int32_t b = 0; b < 64; b++) {
                 int32_t r = 64 * w + b;
-                if (r < R && or_live(seed, (uint32_t)r, (uint64_t)e, thr[e])) word |= 1ULL << b;
+                if (r < R && or_live(seed, (uint32_t)r, coin_of(cid, e), thr[e])) word |= 1ULL << b;
             }
             masks[e * W + w] = word;
         }

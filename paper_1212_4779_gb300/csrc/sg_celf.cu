@@ -65,6 +65,9 @@ sg_status celf_impl(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
     ws.slists_on = 0;
+    // every per-query cache is rebuilt for this query's coins
+    ws.fl_on = 0;
+    if (heavy_on) SG_TRY(ensure_fwd_lists(g, ws, co, c.p, model, st));
     SG_TRY(ensure_mask_cache(g, ws, co.W, st));
 
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -87,6 +90,7 @@ sg_status celf_impl(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
         SG_TRY(run_row_desc(g, ws, co, st));
         ws.rd_on = 1;
     }
+    if (ws.fl_on) SG_TRY(run_fwd_lists(g, ws, co, st));
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st, nullptr));
     if (stats) SG_CUDA_TRY(cudaEventRecord(ev[1], st));
@@ -183,6 +187,10 @@ extern "C" sg_status sg_select_celf(sg_graph *g, int32_t R, int32_t k, sg_cascad
     SG_TRY(check_query(g, R, k));
     if (!out_seeds || !out_gains) {
         set_error("sg_select_celf: output pointers must be non-NULL");
+        return SG_EINVAL;
+    }
+    if (c.model == SG_UIC_UNDIRECTED) {
+        set_error("sg_select_celf: the undirected cascade is served by sg_select (component bookkeeping)");
         return SG_EINVAL;
     }
     DeviceGuard dg(g->device);

@@ -167,6 +167,8 @@ void free_graph_buffers(sg_graph *g, cudaStream_t st)
     dbuf_free(g->hrow_in, st);
     dbuf_free(g->hpref_in, st);
     dbuf_free(g->hcpref_in, st);
+    dbuf_free(g->cc_esrc, st);
+    dbuf_free(g->cc_pmin, st);
 }
 
 // Heavy rows of one direction (row offsets rp): degree >= min_deg.
@@ -357,6 +359,13 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.rdesc, st);
     ws.rd_cap = 0;
     ws.rd_on = 0;
+    dbuf_free(ws.cc_lab, st);
+    dbuf_free(ws.cc_size, st);
+    dbuf_free(ws.cc_deg, st);
+    dbuf_free(ws.cc_cov, st);
+    dbuf_free(ws.cc_root, st);
+    ws.cc_cap = 0;
+    ws.cc_rcap = 0;
     dbuf_free(ws.fsoff, st);
     dbuf_free(ws.fscan, st);
     dbuf_free(ws.fsnbr, st);
@@ -677,7 +686,7 @@ sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out)
     co.W = (R + 63) / 64;
     co.none_live = 0;
     co.uic_tm1 = 0xffffffffu;
-    if (c.model == SG_UIC) {
+    if (c.model == SG_UIC || c.model == SG_UIC_UNDIRECTED) {
         if (!(c.p >= 0.0 && c.p <= 1.0)) {
             set_error("UIC probability must lie in [0, 1]");
             return SG_EINVAL;
@@ -926,6 +935,66 @@ void sg_free_graph(sg_graph *g)
 
 namespace sgi {
 
+// The undirected variant (one coin per edge): Algorithm 2 by component
+// bookkeeping (sg_cc.cu).  Same outputs, counters and statuses as the
+// general path.  The first query on a graph checks its symmetry (one
+// host synchronisation); prepare_only sizes the workspace.
+sg_status cc_select_impl(sg_graph *g, sg_workspace &ws, const Coins &co, int32_t k, cudaStream_t st,
+                         int32_t *out_seeds, int64_t *out_gains, sg_stats *stats, bool prepare_only)
+{
+    SG_TRY(cc_prepare_graph(g, st));
+    const int launches0 = g_launches;
+    SG_TRY(ensure_workspace(g, ws, co.W, k, st));
+    SG_TRY(cc_ensure(g, ws, co.R, st));
+    if (prepare_only) return SG_OK;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard()
+        {
+            for (int i = 0; i < 3; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+    if (stats) {
+        for (auto &e : ev) SG_CUDA_TRY(cudaEventCreate(&e));
+        SG_CUDA_TRY(cudaEventRecord(ev[0], st));
+    }
+    SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
+    SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
+    SG_TRY(cc_clear_cover(g, ws, co, st));
+    SG_TRY(cc_init_gains(g, ws, co, st));
+    if (stats) SG_CUDA_TRY(cudaEventRecord(ev[1], st));
+    for (int32_t i = 0; i < k; ++i) {
+        SG_TRY(run_argmax(g, ws, co, i, st));
+        SG_TRY(cc_round(g, ws, co, st));
+    }
+    SG_CUDA_TRY(cudaMemcpyAsync(out_seeds, ws.out_seeds.p, (size_t)k * 4, cudaMemcpyDefault, st));
+    SG_CUDA_TRY(cudaMemcpyAsync(out_gains, ws.out_gains.p, (size_t)k * 8, cudaMemcpyDefault, st));
+    if (stats) {
+        SG_CUDA_TRY(cudaEventRecord(ev[2], st));
+        Ctl h;
+        SG_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+        memset(stats, 0, sizeof(*stats));
+        stats->init_edges = h.init_edges;
+        stats->fwd_edges = h.fwd_edges;
+        stats->rev_edges = h.rev_edges;
+        stats->status_flags = h.flags;
+        stats->kernel_launches = g_launches - launches0;
+        cudaEventElapsedTime(&stats->ms_init, ev[0], ev[1]);
+        cudaEventElapsedTime(&stats->ms_rounds, ev[1], ev[2]);
+        cudaEventElapsedTime(&stats->ms_total, ev[0], ev[2]);
+        if (h.flags) {
+            set_error("device-side check failed (flags 0x%x)", h.flags);
+            return SG_EINTERNAL;
+        }
+    } else if (is_pageable(out_seeds) || is_pageable(out_gains)) {
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return SG_OK;
+}
+
 // Algorithm 2 end to end on graph g with workspace ws.  prepare_only: size
 // the workspace for the query (allocations happen here) and launch nothing.
 sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
@@ -940,6 +1009,8 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     SG_TRY(make_coins(c, seed, R, &co));
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (c.model == SG_UIC_UNDIRECTED)
+        return cc_select_impl(g, ws, co, k, st, out_seeds, out_gains, stats, prepare_only);
     const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
     const int launches0 = g_launches;
     SG_TRY(ensure_workspace(g, ws, co.W, k, st));
@@ -1179,8 +1250,19 @@ sg_status sg_spread(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, const i
     if (s_count > 0 && cudaMemcpyAsync(dS.p, hs.data(), (size_t)s_count * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = SG_ECUDA;
     if (rc == SG_OK && cudaMemsetAsync(dc.p, 0, 16, st) != cudaSuccess) rc = SG_ECUDA;
-    if (rc == SG_OK && s_count > 0)
-        rc = run_spread(g, co, model, dS.p, s_count, dc.p, reinterpret_cast<unsigned long long *>(dc.p + 1), st);
+    if (rc == SG_OK && s_count > 0) {
+        if (c.model == SG_UIC_UNDIRECTED) {
+            rc = cc_prepare_graph(g, st);
+            if (rc == SG_OK) rc = ensure_workspace(g, g->ws, co.W, 1, st);
+            if (rc == SG_OK) rc = cc_ensure(g, g->ws, co.R, st);
+            if (rc == SG_OK)
+                rc = cc_spread(g, g->ws, co, dS.p, s_count, dc.p, reinterpret_cast<unsigned long long *>(dc.p + 1),
+                               st);
+        } else {
+            rc = run_spread(g, co, model, dS.p, s_count, dc.p, reinterpret_cast<unsigned long long *>(dc.p + 1),
+                            st);
+        }
+    }
     long long hc[2] = {0, 0};
     if (rc == SG_OK && cudaMemcpyAsync(hc, dc.p, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = SG_ECUDA;
     if (rc == SG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = SG_ECUDA;
@@ -1209,6 +1291,23 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
     sg_workspace &ws = g->ws;
     SG_TRY(ensure_workspace(g, ws, co.W, 1, st));
+    if (c.model == SG_UIC_UNDIRECTED) {
+        SG_TRY(cc_prepare_graph(g, st));
+        SG_TRY(cc_ensure(g, ws, co.R, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
+        SG_TRY(cc_init_gains(g, ws, co, st));
+        SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));
+        Ctl h;
+        SG_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+        if (init_edges) *init_edges = h.init_edges;
+        if (h.flags) {
+            set_error("device-side check failed (flags 0x%x)", h.flags);
+            return SG_EINTERNAL;
+        }
+        return SG_OK;
+    }
     const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
     ws.slists_on = 0;
@@ -1255,15 +1354,20 @@ sg_status sg_live_masks(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
     const size_t count = (size_t)g->m * (size_t)co.W;
     if (count == 0) return SG_OK;
+    const int32_t *cid = nullptr;
+    if (c.model == SG_UIC_UNDIRECTED) {
+        SG_TRY(cc_prepare_graph(g, st));
+        cid = g->cc_pmin.p;
+    }
     if (!is_pageable(out_masks)) {
         cudaPointerAttributes at;
         SG_CUDA_TRY(cudaPointerGetAttributes(&at, out_masks));
         if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
-            return run_live_masks(g, co, model, out_masks, st);
+            return run_live_masks(g, co, model, out_masks, st, cid);
     }
     DBuf<uint64_t> tmp;
     SG_TRY(dbuf_alloc(tmp, count, st));
-    sg_status rc = run_live_masks(g, co, model, tmp.p, st);
+    sg_status rc = run_live_masks(g, co, model, tmp.p, st, cid);
     if (rc == SG_OK && cudaMemcpyAsync(out_masks, tmp.p, count * 8, cudaMemcpyDefault, st) != cudaSuccess) {
         set_error("sg_live_masks: copy-out failed");
         rc = SG_ECUDA;

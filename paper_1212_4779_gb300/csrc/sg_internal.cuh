@@ -222,6 +222,13 @@ struct sg_workspace {
     // live-mask cache, [W][m] per direction (optional)
     sgi::DBuf<unsigned long long> lm_out, lm_in;
     int32_t lm_cap = 0;       // words the cache was sized for
+    // undirected variant: per-snapshot component labels, sizes, degree sums,
+    // covered flags [R][n]; the round's roots and new sizes [2R]
+    sgi::DBuf<int32_t> cc_lab, cc_size, cc_root;
+    sgi::DBuf<long long> cc_deg;
+    sgi::DBuf<uint8_t> cc_cov;
+    size_t cc_cap = 0;
+    int32_t cc_rcap = 0;
     int32_t lm_on = 0;        // built for the current query
     int32_t kcap = 0;
     int32_t am_blocks = 0;
@@ -243,6 +250,10 @@ struct sg_graph {
     int32_t nh_out = 0, nh_in = 0;
     long long hsum_out = 0, hsum_in = 0;   // sum of heavy-row degrees
     double hlive_out_wic = 0;              // sum over heavy out-rows' arcs of 1 / indeg(destination)
+    // undirected variant: -1 not checked, 0 not symmetric, 1 symmetric; the
+    // source of every arc and min(arc id, reverse arc id)
+    int32_t cc_sym = -1;
+    sgi::DBuf<int32_t> cc_esrc, cc_pmin;
     sgi::DBuf<int32_t> hid_out, hrow_out, hid_in, hrow_in;
     sgi::DBuf<long long> hpref_out, hpref_in;
     sgi::DBuf<int32_t> hcpref_out, hcpref_in;  // prefix of ceil(deg / index-build block) per heavy row
@@ -277,6 +288,16 @@ extern int g_fwd_lists;
 sg_status run_heavy_index(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
 sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
 sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st);
+sg_status run_argmax(sg_graph *g, sg_workspace &ws, const Coins &co, int32_t round, cudaStream_t st);
+// undirected variant (sg_cc.cu)
+sg_status cc_prepare_graph(sg_graph *g, cudaStream_t st);
+size_t cc_workspace_bytes(const sg_graph *g, int32_t R);
+sg_status cc_ensure(sg_graph *g, sg_workspace &ws, int32_t R, cudaStream_t st);
+sg_status cc_init_gains(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
+sg_status cc_round(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
+sg_status cc_clear_cover(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
+sg_status cc_spread(sg_graph *g, sg_workspace &ws, const Coins &co, const int32_t *d_S, int32_t ns, long long *d_total,
+                    unsigned long long *d_edges, cudaStream_t st);
 sg_status run_row_desc(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
 sg_status run_fwd_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st);
 sg_status ensure_fwd_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model, cudaStream_t st);
@@ -302,7 +323,8 @@ sg_status run_init_gains(sg_graph *g, sg_workspace &ws, const Coins &co, int mod
                          const TierEvents *ev = nullptr);
 sg_status run_round(sg_graph *g, sg_workspace &ws, const Coins &co, int model, int heavy_on, int32_t round,
                     cudaStream_t st, cudaEvent_t after_fwd = nullptr);
-sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st);
+sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st,
+                         const int32_t *cid = nullptr);
 
 // host driver (sg_host.cu)
 sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,

@@ -2015,8 +2015,9 @@ __global__ void scan_add_kernel(long long *out, long long n, const long long *su
 
 // ============================================================== live masks
 
+// cid (undirected variant, else null): the arc id each coin hashes.
 __global__ void live_masks_kernel(Coins co, long long m, const uint2 *fw, uint32_t uic_tm1, int wic,
-                                  unsigned long long *out)
+                                  const int32_t *cid, unsigned long long *out)
 {
     const long long total = m * co.W;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -2024,7 +2025,8 @@ __global__ void live_masks_kernel(Coins co, long long m, const uint2 *fw, uint32
         const long long e = i / co.W;
         const int word = (int)(i - e * co.W);
         const uint32_t tm1 = wic ? fw[e].y : uic_tm1;
-        out[i] = live_bits(co, (uint32_t)e, (uint32_t)word * 64u, word_mask(word, co.R), tm1);
+        const uint32_t id = cid ? (uint32_t)__ldg(cid + e) : (uint32_t)e;
+        out[i] = live_bits(co, id, (uint32_t)word * 64u, word_mask(word, co.R), tm1);
     }
 }
 
@@ -2213,6 +2215,15 @@ sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
         g_launches += 2 * K + 2;
     }
     return launch_tiers<DIR_FWD, MODEL, TASK_INIT>(g, ws, a, st, ev);
+}
+
+sg_status launch_argmax(sg_graph *g, sg_workspace &ws, const Coins &co, int32_t round, cudaStream_t st)
+{
+    argmax_kernel<<<ws.am_blocks, AM_T, 0, st>>>(ws.s.p, (int)g->n, ws.ctl.p, ws.am_gain.p, ws.am_id.p,
+                                                 ws.out_seeds.p, ws.out_gains.p, round, ws.du_cnt.p, co.W);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
+    return SG_OK;
 }
 
 template <int MODEL>
@@ -2428,12 +2439,18 @@ sg_status run_round(sg_graph *g, sg_workspace &ws, const Coins &co, int model, i
                               : round_t<MODEL_UIC>(g, ws, co, heavy_on, round, st, after_fwd);
 }
 
-sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st)
+sg_status run_argmax(sg_graph *g, sg_workspace &ws, const Coins &co, int32_t round, cudaStream_t st)
+{
+    return launch_argmax(g, ws, co, round, st);
+}
+
+sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out, cudaStream_t st,
+                         const int32_t *cid)
 {
     const long long total = g->m * co.W;
     if (total == 0) return SG_OK;
     const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)g->num_sms * 16);
-    live_masks_kernel<<<blocks, 256, 0, st>>>(co, g->m, g->fw.p, co.uic_tm1, model == MODEL_WIC,
+    live_masks_kernel<<<blocks, 256, 0, st>>>(co, g->m, g->fw.p, co.uic_tm1, model == MODEL_WIC, cid,
                                               reinterpret_cast<unsigned long long *>(out));
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;

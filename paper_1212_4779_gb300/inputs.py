@@ -166,6 +166,15 @@ def random_small(n: int, m: int, seed: int, loops_and_dups: bool = False):
     return n, u.astype(np.int32), v.astype(np.int32)
 
 
+def symmetric(n: int, src, dst):
+    """Both arcs of every (non-loop) pair: an undirected graph stored as a
+    symmetric arc list."""
+    src = np.asarray(src, dtype=np.int32)
+    dst = np.asarray(dst, dtype=np.int32)
+    keep = src != dst
+    return n, np.concatenate([src[keep], dst[keep]]), np.concatenate([dst[keep], src[keep]])
+
+
 # ------------------------------------------------------------- named workloads
 
 

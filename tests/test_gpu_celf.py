@@ -39,6 +39,24 @@ def test_celf_matches_oracle(sg, name):
     assert np.array_equal(du.seeds, res.seeds) and np.array_equal(du.gains, res.gains)
 
 
+def test_celf_after_other_queries_on_the_same_graph(sg):
+    """Per-query caches (index, lists, landmarks) are rebuilt for each
+    query's coins: CELF after selections with other seeds and R, and a
+    selection after CELF, still equal the oracle."""
+    wl = inputs.workload("cl15k_wic")
+    n, s, d = wl.graph()
+    g = sg.Graph.from_coo(n, s, d)
+    o = oracle.Graph(n, s, d, wl.model, wl.p)
+    g.select(130, 12, wl.model, wl.p, 99)
+    ref = o.select(wl.R, 15, 4242, mode=oracle.CELF)
+    res, evals = g.select_celf(wl.R, 15, wl.model, wl.p, 4242)
+    assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+    assert evals == ref["evals"]
+    ref2 = o.select(70, 9, 17, mode=oracle.DU)
+    du = g.select(70, 9, wl.model, wl.p, 17)
+    assert np.array_equal(du.seeds, ref2["seeds"]) and np.array_equal(du.gains, ref2["gains"])
+
+
 def test_celf_closed_forms(sg):
     n, s, d = inputs.path_graph(12)
     g = sg.Graph.from_coo(n, s, d)

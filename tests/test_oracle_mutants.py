@@ -37,6 +37,7 @@ MUTANTS = {
     "fwd_counter_indeg": ("c_fwd += (uint64_t)(rp[u + 1] - rp[u]);", "c_fwd += (uint64_t)indeg[u];"),
     "celf_accepts_stale_bound": ("if (stamp == i) { s[v] = b; vs = v; break; }",
                                  "if (stamp <= i) { s[v] = b; vs = v; break; }"),
+    "coupled_higher_arc_id": ("cid[e] = e < lo ? e : lo;", "cid[e] = e > lo ? e : lo;"),
     "celf_ties_to_highest_id": ("return h->b[x] > h->b[y] || (h->b[x] == h->b[y] && h->v[x] < h->v[y]);",
                                 "return h->b[x] > h->b[y] || (h->b[x] == h->b[y] && h->v[x] > h->v[y]);"),
 }

@@ -309,6 +309,73 @@ def test_snapshot_mean_matches_exact_expectation(oracle_mod, model, p):
         assert abs(float(est - mean)) <= 5 * math.sqrt(float(var)) / math.sqrt(R) + 1e-12
 
 
+# ------------------------------------------- undirected variant (coupled coins)
+
+
+COUPLED_CASES = [(9, 12, 0.4, 1), (10, 15, 0.3, 2), (12, 14, 0.5, 3), (8, 10, 0.6, 4)]
+
+
+@pytest.mark.parametrize("n,m,p,gseed", COUPLED_CASES)
+def test_coupled_greedy_matches_brute_force(oracle_mod, n, m, p, gseed):
+    """One coin per undirected edge: every route of the oracle gives the
+    brute-force greedy (own coupling, Warshall closure)."""
+    _, s0, d0 = inputs.random_small(n, m, gseed)
+    _, s, d = inputs.symmetric(n, s0, d0)
+    R, k, seed = 24, 4, 500 + gseed
+    b = brute.Brute(n, s, d, "uic_undirected", p, R, seed)
+    bs, bg = b.greedy(k)
+    g = oracle.Graph(n, s, d, "uic_undirected", p)
+    for mode in MODES:
+        out = g.select(R=R, k=k, seed=seed, mode=mode)
+        assert list(out["seeds"]) == bs, mode
+        assert list(out["gains"]) == bg, mode
+    s_init = g.select(R=R, k=1, seed=seed, mode=oracle.DU, want_init=True)["s_init"]
+    assert list(s_init) == [b.f([v]) for v in range(n)]
+    # coupled snapshots are undirected: u reaches v iff v reaches u
+    for reach in b.reach:
+        for u in range(n):
+            for v in range(n):
+                assert bool(reach[u] >> v & 1) == bool(reach[v] >> u & 1)
+
+
+def test_coupled_masks_pair_up(oracle_mod):
+    n, s0, d0 = inputs.random_small(40, 120, 9)
+    _, s, d = inputs.symmetric(n, s0, d0)
+    g = oracle.Graph(n, s, d, "uic_undirected", 0.3)
+    gu = oracle.Graph(n, s, d, "uic", 0.3)
+    masks, masks_u = g.live_masks(130, 5), gu.live_masks(130, 5)
+    rp, col = g.rp, g.col
+    src_of = np.repeat(np.arange(n), np.diff(rp))
+    index = {(int(u), int(v)): e for e, (u, v) in enumerate(zip(src_of, col[: g.m]))}
+    differ = 0
+    for e, (u, v) in enumerate(zip(src_of, col[: g.m])):
+        r = index[(int(v), int(u))]
+        assert np.array_equal(masks[e], masks[r])
+        assert np.array_equal(masks[min(e, r)], masks_u[min(e, r)])  # the lower arc keeps its own coin
+        differ += not np.array_equal(masks_u[e], masks_u[r])
+    assert differ > 0  # uncoupled arcs of an edge disagree somewhere
+
+
+def test_coupled_snapshot_mean_matches_exact_expectation(oracle_mod):
+    """R = 2^16 coupled snapshots: the mean of |R(G'_r, S)| lies within 5
+    sigma/sqrt(R) of the exact expectation over all 2^(m/2) edge worlds."""
+    n, s0, d0 = inputs.random_small(7, 9, 13)
+    _, s, d = inputs.symmetric(n, s0, d0)
+    g = oracle.Graph(n, s, d, "uic_undirected", 0.4)
+    assert g.m // 2 <= 16
+    R = 1 << 16
+    for S in ([0], [2, 5]):
+        mean, var = brute.exact_spread(n, s, d, "uic_undirected", 0.4, S)
+        est = Fraction(g.spread(R, seed=31, S=S), R)
+        assert abs(float(est - mean)) <= 5 * math.sqrt(float(var)) / math.sqrt(R) + 1e-12
+
+
+def test_coupled_rejects_asymmetric_graph(oracle_mod):
+    n, s, d = inputs.path_graph(5)
+    with pytest.raises(oracle.OracleError):
+        oracle.Graph(n, s, d, "uic_undirected", 0.5)
+
+
 # ----------------------------------------------------------------- invariants
 
 
