@@ -275,6 +275,9 @@ def run_batched(args):
         serial()
     stream.synchronize()
     t_serial = (time.perf_counter() - t0) / args.steps
+    for g in graphs:  # the batch runs on workspaces of its own
+        g.trim()
+    torch.cuda.empty_cache()
 
     wss = [sg.sg_workspace_create(g.handle, q["R"], q["k"]) for q, g in zip(qs, graphs)]
     items = [(g.handle, w, q["R"], q["k"], q["model"], q["p"], q["seed"], so, go)

@@ -218,6 +218,13 @@ sg_status sg_spread(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, const i
 sg_status sg_load_graph_coo(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                             int is_device_ptr, void *stream, sg_graph **out);
 
+/* Release the device memory of the graph's own workspace (the one
+ * sg_select, sg_init_gains, sg_select_celf and sg_spread use); the graph
+ * itself stays resident and the next such call sizes the workspace again.
+ * Explicit workspaces (sg_workspace_create) are not affected.  Waits for
+ * the device.  Errors: SG_EINVAL for a NULL graph. */
+sg_status sg_graph_trim(sg_graph *g);
+
 /* Node count and canonical arc count. */
 sg_status sg_graph_info(const sg_graph *g, int64_t *n, int64_t *m_canonical);
 

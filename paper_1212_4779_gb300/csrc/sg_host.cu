@@ -770,6 +770,20 @@ sg_status sg_set_snapshot_lists(int32_t enable)
     return SG_OK;
 }
 
+sg_status sg_graph_trim(sg_graph *g)
+{
+    clear_error();
+    if (!g) {
+        set_error("sg_graph_trim: NULL graph");
+        return SG_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    SG_CUDA_TRY(cudaDeviceSynchronize());
+    free_workspace(g->ws, (cudaStream_t)0);
+    SG_CUDA_TRY(cudaDeviceSynchronize());
+    return SG_OK;
+}
+
 sg_status sg_set_forward_lists(int32_t enable)
 {
     if (enable != 0 && enable != 1) {

@@ -31,7 +31,7 @@ EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg
            "sg_batch_capture", "sg_batch_launch", "sg_batch_free", "sg_server_create", "sg_server_submit",
            "sg_server_poll", "sg_server_counts", "sg_server_destroy",
            "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-           "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+           "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_graph_trim", "sg_select",
            "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version")
 
 
@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
         L.sg_set_snapshot_lists.argtypes = [i32]
         L.sg_set_mask_cache.argtypes = [i32]
         L.sg_set_forward_lists.argtypes = [i32]
+        L.sg_graph_trim.argtypes = [P]
         L.sg_spread.argtypes = [P, i32, sg_cascade, u64, P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(u64)]
         L.sg_select_celf.argtypes = [P, i32, i32, sg_cascade, u64, P, P, P, ctypes.POINTER(i64), P]
         L.sg_argmax_noalloc.argtypes = [P, i64, P, P, P]
@@ -311,6 +312,11 @@ def sg_load_graph_coo(n, m, src, dst, stream=None):
     _check(lib().sg_load_graph_coo(int(n), int(m), ctypes.c_void_p(s_a), ctypes.c_void_p(d_a), s_dev,
                                    _stream_ptr(stream), ctypes.byref(h)))
     return h
+
+
+def sg_graph_trim(h):
+    """Free the graph's own workspace (the graph stays resident)."""
+    _check(lib().sg_graph_trim(h))
 
 
 def sg_graph_info(h):
@@ -526,6 +532,10 @@ class Graph:
         gains = np.zeros(k, dtype=np.int64)
         ev, st = sg_select_celf(self._h, R, k, model, p, seed, seeds, gains, stream, stats)
         return Selection(seeds, gains, st), ev
+
+    def trim(self):
+        """Release the device memory of this graph's own workspace."""
+        sg_graph_trim(self._h)
 
     def spread(self, R, model, p, seed, S, stream=None):
         """(sum_r |R(G'_r, S)|, snapshot-edge count) on R fresh snapshots."""

@@ -371,6 +371,19 @@ def test_workspace_reuse_across_queries(sg):
         assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
 
 
+def test_trim_releases_and_rebuilds_the_workspace(sg):
+    wl = inputs.workload("cl15k_wic")
+    n, s, d = wl.graph()
+    g = sg.Graph.from_coo(n, s, d)
+    a = g.select(wl.R, 12, wl.model, wl.p, wl.seed)
+    g.trim()
+    g.trim()  # twice is fine
+    b = g.select(wl.R, 12, wl.model, wl.p, wl.seed)
+    assert np.array_equal(a.seeds, b.seeds) and np.array_equal(a.gains, b.gains)
+    with pytest.raises(sg.SGError):
+        sg.sg_graph_trim(None)
+
+
 def test_device_outputs_and_stream(sg):
     import torch
 
