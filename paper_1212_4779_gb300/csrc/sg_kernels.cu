@@ -57,6 +57,9 @@ constexpr int MAX_LMK = 8;     // landmarks for the initial gains
 // snapshot bits through the per-snapshot live lists, one bit at a time
 // (the other bits go back to pending); denser states scan the word's index.
 constexpr int SPARSE_BITS = 4;
+// Newly covered targets of one snapshot walked together by one reverse
+// (dynamic-update) task, one state bit each (at most 64).
+constexpr int REV_GROUP = 64;
 
 // ------------------------------------------------------------------ coins
 // High 32 bits of splitmix64(base ^ (r << 40)) (Steele, Lea, Flood 2014,
@@ -472,8 +475,8 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         const long long c = t - a.coff[r];
         word = r >> 6;
         rs = (uint32_t)r;
-        const long long b0 = a.toff[r] + 64 * c;
-        const int cnt = (int)min(64LL, (long long)a.tcnt[r] - 64 * c);
+        const long long b0 = a.toff[r] + (long long)REV_GROUP * c;
+        const int cnt = (int)min((long long)REV_GROUP, (long long)a.tcnt[r] - (long long)REV_GROUP * c);
         for (int j = lane; j < cnt; j += 32) {
             const int x = a.tl[b0 + j];
             const int h = table_slot<LOGC>(T, x, LIMIT);
@@ -1317,8 +1320,8 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
             const long long ci = t - a.coff[r];
             word = r >> 6;
             rs = (uint32_t)r;
-            const long long b0 = a.toff[r] + 64 * ci;
-            const int cnt = (int)min(64LL, (long long)a.tcnt[r] - 64 * ci);
+            const long long b0 = a.toff[r] + (long long)REV_GROUP * ci;
+            const int cnt = (int)min((long long)REV_GROUP, (long long)a.tcnt[r] - (long long)REV_GROUP * ci);
             if (tid < cnt) coop_seed<TAB>(T, c, a.tl[b0 + tid], 1ull << tid, limit);
         }
         __syncthreads();
@@ -1568,7 +1571,7 @@ __global__ void __launch_bounds__(BT) fwd_post_kernel(EngineArgs a, FwdArgs f)
     long long carry = 0;
     for (int base = 0; base < NS; base += BT) {
         const int i = base + tid;
-        const int v = i < NS ? (*(volatile int32_t *)&f.tcnt[i] + 63) / 64 : 0;
+        const int v = i < NS ? (*(volatile int32_t *)&f.tcnt[i] + REV_GROUP - 1) / REV_GROUP : 0;
         int total;
         const int ex = block_excl_scan(v, S, &total);
         if (i < NS) f.coff[i] = carry + ex;
