@@ -138,10 +138,13 @@ sg_status sg_load_graph(int64_t n, int64_t m, const int64_t *row_ptr, const int3
 sg_status sg_set_heavy_threshold(int32_t min_degree);
 
 /* Traversal-engine limits: a task whose visited set grows past tier1_keys
- * nodes leaves the per-warp shared-memory table for a per-warp global
- * table, and past tier2_keys nodes for a whole-block engine with dense
- * arrays.  Values are clamped to 256 and 4096 (the defaults).  A tuning and
- * testing knob: results do not depend on it.  Applies to later calls.
+ * nodes leaves its warp's shared-memory table (tier 1) for block-shared
+ * shared-memory tables (tier 2: first 2048-slot tables holding up to
+ * min(1024, tier2_keys / 2) nodes, four blocks per SM, then 4096-slot
+ * tables, two blocks per SM), and past tier2_keys nodes for the engine
+ * with dense per-slot arrays in global memory (tier 3).  Values are
+ * clamped to 256 and 2048 (the defaults).  A tuning and testing knob:
+ * results do not depend on it.  Applies to later calls.
  * Errors: SG_EINVAL if either is < 1. */
 sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys);
 

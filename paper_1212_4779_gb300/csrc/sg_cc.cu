@@ -27,16 +27,6 @@ namespace {
 constexpr int CC_T = 256;
 constexpr long long CC_SPIN = 1LL << 24;
 
-// High 32 bits of the coin hash (the same function as the traversal
-// kernels: splitmix64 of seed ^ (r << 40) ^ e).
-__device__ __forceinline__ uint32_t cc_coin(uint64_t seed, uint64_t e, uint32_t r)
-{
-    uint64_t z = (seed ^ e ^ ((uint64_t)r << 40)) + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    const uint32_t hi = (uint32_t)(z >> 32);
-    return hi ^ (hi >> 31);
-}
 
 // Source of every arc and the lower id of each arc and its reverse;
 // *asym is set if some arc has no reverse.
@@ -111,7 +101,7 @@ __global__ void cc_hook_kernel(int n, long long m, int R, uint64_t seed, uint32_
         const long long e = i - (long long)r * m;
         int a = __ldg(esrc + e), b = __ldg(col + e);
         if (a >= b) continue;
-        if (cc_coin(seed, (uint64_t)e, (uint32_t)r) > tm1) continue;
+        if (coin_hi32(seed ^ (uint64_t)e, (uint32_t)r) > tm1) continue;
         int32_t *L = lab + (size_t)r * n;
         long long tries = 0;
         while (true) {

@@ -104,6 +104,19 @@ struct Coins {
     int32_t W;         // ceil(R / 64)
 };
 
+// High 32 bits of splitmix64(base ^ (r << 40)) (Steele, Lea, Flood 2014,
+// with Stafford's Mix13 finaliser), base = seed ^ e: arc e is live in
+// snapshot r iff this is at most thr(e) - 1 (Section 3.1's snapshot, with
+// the coin drawn from a counter-based hash).
+__device__ __forceinline__ uint32_t coin_hi32(uint64_t base, uint32_t r)
+{
+    uint64_t z = (base ^ ((uint64_t)r << 40)) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    const uint32_t hi = (uint32_t)(z >> 32);
+    return hi ^ (hi >> 31);
+}
+
 // Heavy rows of one direction and the query's live index over them.
 struct HeavyView {
     const int32_t *hid;

@@ -62,16 +62,7 @@ constexpr int SPARSE_BITS = 4;
 constexpr int REV_GROUP = 64;
 
 // ------------------------------------------------------------------ coins
-// High 32 bits of splitmix64(base ^ (r << 40)) (Steele, Lea, Flood 2014,
-// with Stafford's Mix13 finaliser), base = seed ^ e.
-__device__ __forceinline__ uint32_t coin_hi32(uint64_t base, uint32_t r)
-{
-    uint64_t z = (base ^ ((uint64_t)r << 40)) + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    const uint32_t hi = (uint32_t)(z >> 32);
-    return hi ^ (hi >> 31);
-}
+// coin_hi32 (sg_internal.cuh): the high 32 bits of the coin hash.
 
 // Live bits, among the snapshot bits F of the word starting at snapshot r0,
 // of arc eid with threshold-1 tm1 (live iff hi32 <= thr - 1).
@@ -962,21 +953,23 @@ struct SlotArgs {
 //   TAB_DENSE  dense per-block arrays in global memory indexed by node
 //              (tier 3; never overflows)
 
-// block size: the shared-memory tier runs one 1024-thread block per SM (its
-// table fills shared memory); the dense tier runs two 512-thread blocks
-template <int TAB>
-struct CoopShape;
-constexpr int CO_LOGC = 13;
+// Block shapes.  Shared-memory tables take 24 bytes per slot: 2048-slot
+// tables run in four 256-thread blocks per SM, 4096-slot tables in two
+// 512-thread blocks.  Tasks are deep and narrow walks, so tasks in flight
+// per SM set the throughput more than threads per task.  The dense tier
+// runs three 512-thread blocks per SM (40 registers).
+constexpr int CO_LOGC = 12;  // the largest shared-memory table
 constexpr long long CO_SPIN = 1LL << 22;
 constexpr unsigned short QE16 = 0xFFFF;
 enum { TAB_HASH = 0, TAB_DENSE = 1 };
-template <>
-struct CoopShape<TAB_HASH> {
-    static constexpr int T = 1024, MINB = 1;
+template <int TAB, int LOGC>
+struct CoopShape {
+    static constexpr int T = LOGC <= 11 ? 256 : (LOGC == 12 ? 512 : 1024);
+    static constexpr int MINB = LOGC <= 11 ? 4 : (LOGC == 12 ? 2 : 1);
 };
-template <>
-struct CoopShape<TAB_DENSE> {
-    static constexpr int T = 512, MINB = 2;
+template <int LOGC>
+struct CoopShape<TAB_DENSE, LOGC> {
+    static constexpr int T = 512, MINB = 3;
 };
 
 struct CoopCtl {
@@ -984,12 +977,12 @@ struct CoopCtl {
     unsigned long long xbits[MAX_LMK];  // initial gains: snapshots in which the task reached each landmark
 };
 
-template <int TAB>
+template <int TAB, int LOGC>
 struct CoopTab;
 
-template <>
-struct CoopTab<TAB_HASH> {
-    static constexpr int C = 1 << CO_LOGC;
+template <int LOGC>
+struct CoopTab<TAB_HASH, LOGC> {
+    static constexpr int C = 1 << LOGC;
     unsigned long long *vis, *pend;
     int *key;
     unsigned short *queue, *touched;
@@ -1008,7 +1001,7 @@ struct CoopTab<TAB_HASH> {
     // slot of y, inserting it; -1 (and overflow) past `limit` keys
     __device__ __forceinline__ int slot(int y, int limit, CoopCtl &c)
     {
-        uint32_t h = ((uint32_t)y * 2654435761u) >> (32 - CO_LOGC);
+        uint32_t h = ((uint32_t)y * 2654435761u) >> (32 - LOGC);
         volatile int *keys = key;
         for (int probe = 0; probe < C; ++probe) {
             const int k = keys[h];
@@ -1060,8 +1053,8 @@ struct CoopTab<TAB_HASH> {
     }
 };
 
-template <>
-struct CoopTab<TAB_DENSE> {
+template <int LOGC>
+struct CoopTab<TAB_DENSE, LOGC> {
     // vis(y) and pend(y) share one 16-byte record: st[2y], st[2y + 1]
     unsigned long long *st;
     int *queue, *touched;
@@ -1100,8 +1093,8 @@ struct CoopTab<TAB_DENSE> {
 };
 
 // Seed: entry `idx` carries bits M (vis and pend), queued.
-template <int TAB>
-__device__ __forceinline__ void coop_seed(CoopTab<TAB> &T, CoopCtl &c, int y, uint64_t M, int limit)
+template <int TAB, int LOGC>
+__device__ __forceinline__ void coop_seed(CoopTab<TAB, LOGC> &T, CoopCtl &c, int y, uint64_t M, int limit)
 {
     const int idx = T.slot(y, limit, c);
     if (idx < 0) return;
@@ -1113,8 +1106,8 @@ __device__ __forceinline__ void coop_seed(CoopTab<TAB> &T, CoopCtl &c, int y, ui
 
 // The block's warps expand the task's frontier until nothing is queued or
 // claimed.
-template <int TAB, int DIR, int MODEL, int TASK>
-__device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, CoopTab<TAB> &T, CoopCtl &c, int word,
+template <int TAB, int DIR, int MODEL, int TASK, int LOGC>
+__device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, CoopTab<TAB, LOGC> &T, CoopCtl &c, int word,
                                                           uint32_t rs, int limit, unsigned long long &elems,
                                                           unsigned long long &lel)
 {
@@ -1252,11 +1245,24 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
     return tedges;
 }
 
-// Tier 2 (TAB_HASH, tasks of list1) and tier 3 (TAB_DENSE, tasks of list2).
-template <int TAB, int DIR, int MODEL, int TASK>
-__global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_engine_kernel(EngineArgs a, SlotArgs sl)
+// The tasks of one stage: read from `in` (count *in_count, claimed through
+// *next); a task that outgrows the table goes to `out` (count *out_count).
+// stat: 1 counts the stage's tasks as tier-2 tasks, 2 as tier-3 tasks.
+struct StageIO {
+    const int32_t *in;
+    unsigned long long *in_count;
+    unsigned long long *next;
+    int32_t *out;
+    unsigned long long *out_count;
+    int stat;
+};
+
+// Tier 2 (TAB_HASH, one stage per table size) and tier 3 (TAB_DENSE).
+template <int TAB, int DIR, int MODEL, int TASK, int LOGC>
+__global__ void __launch_bounds__(CoopShape<TAB, LOGC>::T, CoopShape<TAB, LOGC>::MINB)
+    coop_engine_kernel(EngineArgs a, SlotArgs sl, StageIO io)
 {
-    constexpr int CO_T = CoopShape<TAB>::T;
+    constexpr int CO_T = CoopShape<TAB, LOGC>::T;
     constexpr int CO_W = CO_T / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ CoopCtl c;
@@ -1268,11 +1274,11 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
     const int wid = tid >> 5;
     const GraphView &g = a.g;
     Ctl *ctl = a.ctl;
-    CoopTab<TAB> T;
+    CoopTab<TAB, LOGC> T;
     int limit = 0x7fffffff;
     if constexpr (TAB == TAB_HASH) {
         T.bind(smem_raw);
-        for (int i = tid; i < CoopTab<TAB_HASH>::C; i += CO_T) {
+        for (int i = tid; i < CoopTab<TAB_HASH, LOGC>::C; i += CO_T) {
             T.key[i] = EMPTY_KEY;
             T.vis[i] = 0;
             T.pend[i] = 0;
@@ -1286,9 +1292,9 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
         T.queue = sl.qa + (size_t)blockIdx.x * (size_t)(sl.qmask + 1);
         T.qmask = sl.qmask;
     }
-    const long long count = (long long)*(volatile unsigned long long *)(TAB == TAB_HASH ? &ctl->l1_count : &ctl->l2_count);
-    unsigned long long *next = TAB == TAB_HASH ? &ctl->l1_next : &ctl->l2_next;
-    const int32_t *list = TAB == TAB_HASH ? a.list1 : a.list2;
+    const long long count = (long long)*(volatile unsigned long long *)io.in_count;
+    unsigned long long *next = io.next;
+    const int32_t *list = io.in;
     unsigned long long edges = 0, wk_keys = 0, wk_elems = 0, lel = 0;
     __syncthreads();
     while (true) {
@@ -1314,7 +1320,7 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
             rs = (uint32_t)word * 64u;
             if (tid < MAX_LMK)
                 c.xbits[tid] = tid < a.lmk_k ? lmk_reaches(a, word, x0, tid) & word_mask(word, a.co.R) : 0ull;
-            if (tid == 0) coop_seed<TAB>(T, c, x0, word_mask(word, a.co.R), limit);
+            if (tid == 0) coop_seed<TAB, LOGC>(T, c, x0, word_mask(word, a.co.R), limit);
         } else {
             const int r = find_off(a.coff, 64 * a.co.W, t);
             const long long ci = t - a.coff[r];
@@ -1322,10 +1328,10 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
             rs = (uint32_t)r;
             const long long b0 = a.toff[r] + (long long)REV_GROUP * ci;
             const int cnt = (int)min((long long)REV_GROUP, (long long)a.tcnt[r] - (long long)REV_GROUP * ci);
-            if (tid < cnt) coop_seed<TAB>(T, c, a.tl[b0 + tid], 1ull << tid, limit);
+            if (tid < cnt) coop_seed<TAB, LOGC>(T, c, a.tl[b0 + tid], 1ull << tid, limit);
         }
         __syncthreads();
-        unsigned long long tedges = coop_expand<TAB, DIR, MODEL, TASK>(a, T, c, word, rs, limit, wk_elems, lel);
+        unsigned long long tedges = coop_expand<TAB, DIR, MODEL, TASK, LOGC>(a, T, c, word, rs, limit, wk_elems, lel);
         __syncthreads();
         const int ovf = c.overflow | c.err;
         const int nt = c.nkeys;
@@ -1364,7 +1370,7 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
         if (tid == 0) {
             if (c.err) atomicOr(&ctl->flags, 2);
             if (ovf && !c.err) {
-                if (TAB == TAB_HASH) a.list2[atomicAdd(&ctl->l2_count, 1ull)] = (int32_t)t;
+                if (io.out) io.out[atomicAdd(io.out_count, 1ull)] = (int32_t)t;
             } else if (!ovf && TASK == TASK_INIT) {
                 long long tot = 0;
                 for (int w = 0; w < CO_W; ++w) tot += red_ll[w];
@@ -1396,10 +1402,10 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
         atomicAdd(&ctl->work_elems[TASK == TASK_INIT ? 0 : 1][tr], el);
         if (tot) atomicAdd(TASK == TASK_INIT ? &ctl->init_edges : &ctl->rev_edges, tot);
         if (blockIdx.x == 0) {
-            if (TAB == TAB_HASH) {
+            if (io.stat == 1) {
                 if (TASK == TASK_INIT) ctl->init_t2 += (unsigned long long)count;
                 else ctl->rev_t2 += (unsigned long long)count;
-            } else {
+            } else if (io.stat == 2) {
                 if (TASK == TASK_INIT) ctl->init_t3 += (unsigned long long)count;
                 else ctl->rev_t3 += (unsigned long long)count;
             }
@@ -1407,7 +1413,7 @@ __global__ void __launch_bounds__(CoopShape<TAB>::T, CoopShape<TAB>::MINB) coop_
     }
 }
 
-size_t coop_hash_smem() { return (size_t)(1 << CO_LOGC) * 24; }
+size_t coop_hash_smem(int logc) { return (size_t)(1 << logc) * 24; }
 
 // ========================================================== forward DU
 
@@ -2126,6 +2132,21 @@ SlotArgs slot_args(sg_workspace &ws)
 }
 
 // tier 1 -> tier 2 -> tier 3 for one task family
+// One shared-memory stage of tier 2: 2^LOGC-slot tables, blocks per SM
+// from CoopShape.
+template <int DIR, int MODEL, int TASK, int LOGC>
+sg_status launch_stage(sg_graph *g, sg_workspace &ws, EngineArgs a, int limit, StageIO io, cudaStream_t st)
+{
+    a.limit = limit;
+    auto kern = coop_engine_kernel<TAB_HASH, DIR, MODEL, TASK, LOGC>;
+    const size_t smem = coop_hash_smem(LOGC);
+    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<g->num_sms * CoopShape<TAB_HASH, LOGC>::MINB, CoopShape<TAB_HASH, LOGC>::T, smem, st>>>(a, slot_args(ws), io);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
+    return SG_OK;
+}
+
 template <int DIR, int MODEL, int TASK>
 sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cudaStream_t st, const TierEvents *ev)
 {
@@ -2145,16 +2166,23 @@ sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cuda
     }
     if (ev && ev->t1) SG_CUDA_TRY(cudaEventRecord(ev->t1, st));
     {
-        a.limit = std::max(1, std::min(g_tier_limit[1], (1 << CO_LOGC) / 2));
-        auto kern = coop_engine_kernel<TAB_HASH, DIR, MODEL, TASK>;
-        const size_t smem = coop_hash_smem();
-        SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<g->num_sms, CoopShape<TAB_HASH>::T, smem, st>>>(a, slot_args(ws));
-        SG_CUDA_TRY(cudaGetLastError());
-        ++g_launches;
+        // Tier 2: one shared-memory stage, chosen by the kind of task.
+        // Initial-gain tasks run in 2048-slot tables, four per SM (a
+        // 4096-slot second stage for their 1-2 K-node tasks was slower than
+        // sending those to tier 3); reverse tasks (about 1 K nodes on
+        // average) run in 4096-slot tables, two per SM.
+        const int lim1 = std::max(1, std::min(g_tier_limit[0], (1 << T1_LOGC) / 2));
+        const int t2 = std::max(1, std::min(g_tier_limit[1], (1 << CO_LOGC) / 2));
+        Ctl *ctl = ws.ctl.p;
+        const StageIO io{ws.list1.p, &ctl->l1_count, &ctl->l1_next, ws.list2.p, &ctl->l2_count, 1};
+        if (TASK == TASK_INIT)
+            SG_TRY((launch_stage<DIR, MODEL, TASK, 11>(g, ws, a, std::max(lim1, std::min(1 << 10, t2)), io, st)));
+        else
+            SG_TRY((launch_stage<DIR, MODEL, TASK, 12>(g, ws, a, std::max(lim1, t2), io, st)));
     }
     if (ev && ev->t2) SG_CUDA_TRY(cudaEventRecord(ev->t2, st));
-    coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK><<<ws.nslots, CoopShape<TAB_DENSE>::T, 0, st>>>(a, slot_args(ws));
+    coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK, 0><<<ws.nslots, CoopShape<TAB_DENSE, 0>::T, 0, st>>>(
+        a, slot_args(ws), StageIO{ws.list2.p, &ws.ctl.p->l2_count, &ws.ctl.p->l2_next, nullptr, nullptr, 2});
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
     if (ev && ev->t3) SG_CUDA_TRY(cudaEventRecord(ev->t3, st));

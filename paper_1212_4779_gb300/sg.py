@@ -254,7 +254,7 @@ def sg_set_heavy_threshold(min_degree: int):
     _check(lib().sg_set_heavy_threshold(int(min_degree)))
 
 
-def sg_set_engine_limits(tier1_keys: int = 256, tier2_keys: int = 4096):
+def sg_set_engine_limits(tier1_keys: int = 256, tier2_keys: int = 2048):
     """Visited-set sizes at which tasks move to the next engine tier."""
     _check(lib().sg_set_engine_limits(int(tier1_keys), int(tier2_keys)))
 
