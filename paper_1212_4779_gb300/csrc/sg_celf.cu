@@ -87,10 +87,10 @@ sg_status celf_impl(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) {
         SG_TRY(run_heavy_index(g, ws, co, model, st));
+        if (ws.fl_on) SG_TRY(run_fwd_lists(g, ws, co, st));
         SG_TRY(run_row_desc(g, ws, co, st));
         ws.rd_on = 1;
     }
-    if (ws.fl_on) SG_TRY(run_fwd_lists(g, ws, co, st));
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st, nullptr));
     if (stats) SG_CUDA_TRY(cudaEventRecord(ev[1], st));

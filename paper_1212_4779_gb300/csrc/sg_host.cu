@@ -456,7 +456,7 @@ sg_status ensure_heavy_index(sg_graph *g, sg_workspace &ws, int32_t W, cudaStrea
     if (ws.rd_cap < W) {
         dbuf_free(ws.rdesc, st);
         ws.rd_cap = 0;
-        SG_TRY(dbuf_alloc(ws.rdesc, (size_t)W * (size_t)g->n, st));
+        SG_TRY(dbuf_alloc(ws.rdesc, (size_t)W * (size_t)g->n * 2, st));
         ws.rd_cap = W;
     }
     if (ws.hw_cap >= W) return SG_OK;
@@ -527,7 +527,7 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
     b += (size_t)g->num_sms * 2 * 12 + (size_t)k * 12 + 4096;
     if (heavy_index_enabled(g, W)) {
         b += (size_t)(g->hsum_out + g->hsum_in) * W * 12 + (size_t)(g->nh_out + g->nh_in) * W * 4;
-        b += (size_t)g->n * W * 16;  // forward row descriptors
+        b += (size_t)g->n * W * 32;  // forward row descriptors
         {
             // forward per-snapshot lists (upper bound: WIC expectation or all arcs)
             const size_t nq = (size_t)g->n * 64 * W + 1;
@@ -1072,10 +1072,10 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) {
         SG_TRY(run_heavy_index(g, ws, co, model, st));
+        if (ws.fl_on) SG_TRY(run_fwd_lists(g, ws, co, st));
         SG_TRY(run_row_desc(g, ws, co, st));
         ws.rd_on = 1;
     }
-    if (ws.fl_on) SG_TRY(run_fwd_lists(g, ws, co, st));
     if (ws.slists_on) SG_TRY(run_snapshot_lists(g, ws, co, st));
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     if (stats) SG_CUDA_TRY(cudaEventRecord(e_index, st));
@@ -1332,10 +1332,10 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) {
         SG_TRY(run_heavy_index(g, ws, co, model, st));
+        if (ws.fl_on) SG_TRY(run_fwd_lists(g, ws, co, st));
         SG_TRY(run_row_desc(g, ws, co, st));
         ws.rd_on = 1;
     }
-    if (ws.fl_on) SG_TRY(run_fwd_lists(g, ws, co, st));
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));

@@ -148,9 +148,14 @@ struct GraphView {
     // the arc at CSC position j
     const unsigned long long *lm_out;
     const unsigned long long *lm_in;
-    // forward row descriptors (null when the heavy-row index is off):
-    // rdesc[w*n + x] = {segment base (lo, hi), elements to expand for word w,
-    // out-degree | (indexed << 31)}
+    // forward row descriptors (null when the heavy-row index is off), two
+    // int4 (one 32-byte sector) per (w, x):
+    // rdesc[2(w*n + x)]     = {segment base (lo, hi), elements to expand for
+    //                          word w, out-degree | (indexed << 31)}
+    // rdesc[2(w*n + x) + 1] = {live (lo, hi), list base (lo, hi | single << 31)}
+    // live: bit b set iff x has a live out-arc in snapshot 64w+b (all ones
+    // without the forward lists); single: every nonempty list of the word
+    // holds one arc, the lists of the word start at the list base
     const int4 *rdesc;
     // forward per-snapshot live lists (null when off): the live out-arcs of
     // node x in snapshot r are fsnbr[fsoff[x*64W + r] .. fsoff[x*64W + r + 1])
@@ -224,7 +229,7 @@ struct sg_workspace {
     sgi::DBuf<long long> scan_tmp;
     size_t soff_cap = 0, snbr_cap = 0;
     int32_t slists_on = 0;    // built for the current query
-    sgi::DBuf<int4> rdesc;    // [W][n] forward row descriptors (with the heavy-row index)
+    sgi::DBuf<int4> rdesc;    // [W][n][2] forward row descriptors (with the heavy-row index)
     // forward per-snapshot live lists of indexed rows, node-indexed
     sgi::DBuf<long long> fsoff, fscan;
     sgi::DBuf<int32_t> fsnbr, fsvalid;

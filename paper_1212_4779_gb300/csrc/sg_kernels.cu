@@ -109,6 +109,23 @@ __device__ __forceinline__ void arc_at(const GraphView &g, int j, uint32_t rtm1,
     }
 }
 
+// Position of the (j+1)-th lowest set bit of m (j < popc(m)): a binary
+// search on population counts of halves.
+__device__ __forceinline__ int nth_bit(uint64_t m, int j)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 32; w >= 1; w >>= 1) {
+        const int c = __popcll(m & ((1ull << w) - 1ull));
+        if (j >= c) {
+            j -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 // The elements one frontier entry expands: its arcs (light row) or its
 // row's index entries for the word (heavy row).
 struct Row {
@@ -117,21 +134,31 @@ struct Row {
     int deg;    // degree in the canonical graph (work counter)
     int heavy;
     uint32_t rtm1;
+    uint64_t live;    // snapshots of the word with a live out-arc (forward descriptors)
+    long long lbase;  // start of the word's per-snapshot lists when `single`
+    int single;       // every nonempty list of the word holds one arc
 };
 
 template <int DIR, int MODEL, int SLICE = SLICE_SNAP>
 __device__ __forceinline__ Row row_ref(const GraphView &g, const Coins &co, int x, int word, uint32_t rs = 0)
 {
     Row r;
+    r.live = ~0ull;
+    r.lbase = 0;
+    r.single = 0;
     if (DIR == DIR_FWD && g.rdesc) {
-        // one 16-byte load instead of the row offsets, index ordinal and
-        // segment prefix one after another
-        const int4 d = __ldg(g.rdesc + (size_t)word * (size_t)g.n + x);
+        // one 32-byte sector instead of the row offsets, index ordinal,
+        // segment prefix and list offsets one after another
+        const int4 *p = g.rdesc + 2 * ((size_t)word * (size_t)g.n + x);
+        const int4 d = __ldg(p), e = __ldg(p + 1);
         r.base = (long long)(((unsigned long long)(unsigned)d.y << 32) | (unsigned)d.x);
         r.vdeg = d.z;
         r.deg = d.w & 0x7fffffff;
         r.heavy = (int)((unsigned)d.w >> 31);
         r.rtm1 = co.uic_tm1;
+        r.live = ((unsigned long long)(unsigned)e.y << 32) | (unsigned)e.x;
+        r.lbase = (long long)(((unsigned long long)((unsigned)e.w & 0x7fffffffu) << 32) | (unsigned)e.z);
+        r.single = (int)((unsigned)e.w >> 31);
         return r;
     }
     int beg, end;
@@ -169,7 +196,7 @@ __device__ __forceinline__ Row row_ref(const GraphView &g, const Coins &co, int 
 // Live state carried from x to the element's neighbour y.
 template <int DIR, int MODEL, int SLICE>
 __device__ __forceinline__ uint64_t elem(const GraphView &g, const Coins &co, long long base, int heavy,
-                                         uint32_t rtm1, int j, uint64_t F, uint32_t rs, int &y)
+                                         uint32_t rtm1, int j, uint64_t F, uint32_t rs, int &y, uint64_t live = 0)
 {
     const HeavyView &hv = DIR == DIR_FWD ? g.hout : g.hin;
     if (SLICE == SLICE_TGT && DIR == DIR_REV && heavy == 2) {
@@ -180,6 +207,13 @@ __device__ __forceinline__ uint64_t elem(const GraphView &g, const Coins &co, lo
         // one snapshot's live out-arcs; F is that snapshot's bit
         y = __ldg(g.fsnbr + base + j);
         return F;
+    }
+    if (DIR == DIR_FWD && SLICE == SLICE_SNAP && heavy == 4) {
+        // one-arc lists: element j is the j-th state bit b, whose arc is the
+        // list of rank popc(live below b) from the word's list base
+        const int b = nth_bit(F, j);
+        y = __ldg(g.fsnbr + base + __popcll(live & ((1ull << b) - 1ull)));
+        return 1ull << b;
     }
     const unsigned long long *lm = DIR == DIR_FWD ? g.lm_out : g.lm_in;
     if (!heavy && lm) {
@@ -204,20 +238,31 @@ __device__ __forceinline__ uint64_t elem(const GraphView &g, const Coins &co, lo
     return coin_hi32(co.seed ^ (uint64_t)eid, rs) <= tm1 ? F : 0ull;
 }
 
-// Initial gains: a node x with state F of at most SPARSE_BITS bits and an
-// indexed row takes its lowest bit through that snapshot's live list; the
-// caller puts the other bits back to pending.  Returns the remaining bits
-// (F is then the single bit, rr the list), or F unchanged otherwise with
-// rest 0 and rr untouched.
+// Snapshot-sliced forward rows with per-snapshot lists (the caller has
+// checked that the lists are valid).  State bits whose snapshot has no live
+// out-arc at x need no expansion and are dropped from F.  A row whose
+// nonempty lists in this word hold one arc each expands one element per
+// remaining bit (heavy 4).  Otherwise a state of at most SPARSE_BITS bits
+// takes its lowest bit through that snapshot's list (heavy 3) and the other
+// bits are returned for the caller to put back to pending; larger states
+// keep the index.  Returns the bits put back (0 when none).
 template <int DIR, int SLICE>
-__device__ __forceinline__ uint64_t sparse_pick(const GraphView &g, const Coins &co, int x, int word, uint64_t &F,
-                                                Row &rr)
+__device__ __forceinline__ uint64_t pick_rows(const GraphView &g, const Coins &co, int x, int word, uint64_t &F,
+                                              Row &rr)
 {
-    if (DIR != DIR_FWD || SLICE != SLICE_SNAP || !g.fsoff || !F || __popcll(F) > SPARSE_BITS) return 0;
+    if (DIR != DIR_FWD || SLICE != SLICE_SNAP || !g.fsoff || !F || rr.heavy != 1) return 0;
+    F &= rr.live;
+    if (!F) return 0;
+    if (rr.single) {
+        rr.base = rr.lbase;
+        rr.vdeg = __popcll(F);
+        rr.heavy = 4;
+        return 0;
+    }
+    if (__popcll(F) > SPARSE_BITS) return 0;
     const int b = __ffsll((long long)F) - 1;
     const long long q = (long long)x * (64 * co.W) + 64 * word + b;
     const long long o0 = __ldg(g.fsoff + q), o1 = __ldg(g.fsoff + q + 1);
-    if (rr.heavy != 1) return 0;  // rows without an index have no lists
     const uint64_t rest = F & (F - 1);
     F = 1ull << b;
     rr.base = o0;
@@ -493,26 +538,29 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         long long base = 0;
         int vdeg = 0, heavy = 0;
         uint32_t rtm1 = 0;
-        uint64_t F = 0;
+        uint64_t F = 0, live = 0;
         if (lane < nb) {
             const int h = T.queue[(qhead + lane) & (C - 1)];
             const int x = T.key[h];
             F = T.pend[h];
             T.pend[h] = 0;
+            const uint64_t Fp = F;
+            uint64_t rest = 0;
             Row rr = row_ref<DIR, MODEL, SLICE>(g, co, x, word, rs);
             if (TASK == TASK_INIT && flists) {
-                const uint64_t rest = sparse_pick<DIR, SLICE>(g, co, x, word, F, rr);
+                rest = pick_rows<DIR, SLICE>(g, co, x, word, F, rr);
                 if (rest) {  // the other bits are expanded when x is popped again
                     T.pend[h] = rest;
                     T.queue[atomicAdd(&T.ctr[0], 1) & (C - 1)] = (unsigned short)h;
                 }
-                if (rr.heavy == 3) lel += (unsigned long long)rr.vdeg;
+                if (rr.heavy >= 3 && F) lel += (unsigned long long)rr.vdeg;
             }
             base = rr.base;
-            vdeg = rr.vdeg;
+            vdeg = F ? rr.vdeg : 0;
             heavy = rr.heavy;
             rtm1 = rr.rtm1;
-            if (TASK == TASK_INIT) tedges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
+            live = rr.live;
+            if (TASK == TASK_INIT) tedges += (unsigned long long)__popcll(Fp & ~rest) * (unsigned long long)rr.deg;
         }
         qhead += nb;
         __syncwarp();
@@ -537,11 +585,14 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
             const long long ib = __shfl_sync(FULL, base, lo);
             const int iex = __shfl_sync(FULL, excl, lo);
             const int ih = __shfl_sync(FULL, heavy, lo);
-            const uint32_t itm1 = __shfl_sync(FULL, rtm1, lo);
+            // forward rows share the uniform threshold; only initial gains
+            // use one-arc lists
+            const uint32_t itm1 = DIR == DIR_FWD ? co.uic_tm1 : __shfl_sync(FULL, rtm1, lo);
             const uint64_t iF = __shfl_sync(FULL, F, lo);
+            const uint64_t ilive = TASK == TASK_INIT ? __shfl_sync(FULL, live, lo) : 0ull;
             if (j < total) {
                 int y;
-                uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y);
+                uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y, ilive);
                 // nodes reaching v* in this snapshot were settled by the ancestor pass
                 if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                     ml = 0;
@@ -669,6 +720,7 @@ constexpr int BW = BT / 32;
 
 struct CtaShared {
     unsigned long long F[BT];
+    unsigned long long live[BT];
     long long base[BT];
     int ex[BT];
     int heavy[BT];
@@ -827,11 +879,13 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                 const int x = cur[i];
                 uint64_t F = w.gm == ~0ull ? atomicExch(&w.pend[x], 0ull)
                                            : (atomicAnd(&w.pend[x], ~w.gm) & w.gm);
+                const uint64_t Fp = F;
+                uint64_t rest = 0;
                 Row rr = row_ref<DIR, MODEL, SLICE>(g, co, x, word, rs);
                 if (flists) {
                     // sparse state: one snapshot's live out-arcs now, the
                     // other bits at the next level (reachability only)
-                    const uint64_t rest = sparse_pick<DIR, SLICE>(g, co, x, word, F, rr);
+                    rest = pick_rows<DIR, SLICE>(g, co, x, word, F, rr);
                     if (rest && (atomicOr(&w.pend[x], (unsigned long long)rest) & w.gm) == 0ull)
                         nxt[atomicAdd(&S.qnext, 1)] = x;
                 }
@@ -840,8 +894,9 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                 S.base[tid] = rr.base;
                 S.heavy[tid] = rr.heavy;
                 S.tm1[tid] = rr.rtm1;
+                S.live[tid] = rr.live;
                 if (TASK == TASK_INIT || TASK == TASK_FWD || TASK == TASK_SPREAD)
-                    edges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
+                    edges += (unsigned long long)__popcll(Fp & ~rest) * (unsigned long long)rr.deg;
             }
             int total;
             const int ex = block_excl_scan(vd, S, &total);
@@ -859,7 +914,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                     }
                     int y;
                     uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, S.base[lo], S.heavy[lo], S.tm1[lo], j - S.ex[lo],
-                                                          S.F[lo], rs, y);
+                                                          S.F[lo], rs, y, S.live[lo]);
                     if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                         ml = 0;
                     if (ml) {
@@ -1172,25 +1227,29 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
         long long base = 0;
         int vdeg = 0, heavy = 0;
         uint32_t rtm1 = 0;
-        uint64_t F = 0;
+        uint64_t F = 0, live = 0;
         if (lane < nb) {
             const int idx = T.take(qb + lane, c);
             if (idx >= 0) {
                 F = atomicExch(&T.pendr(idx), 0ull);
+                const uint64_t Fp = F;
+                uint64_t rest = 0;
                 Row rr = row_ref<DIR, MODEL, SLICE>(g, co, T.node(idx), word, rs);
                 if (TASK == TASK_INIT && flists) {
-                    const uint64_t rest = sparse_pick<DIR, SLICE>(g, co, T.node(idx), word, F, rr);
+                    rest = pick_rows<DIR, SLICE>(g, co, T.node(idx), word, F, rr);
                     // the other bits go back to pending; re-queue unless an
                     // arrival already did
                     if (rest && atomicOr(&T.pendr(idx), (unsigned long long)rest) == 0ull)
                         T.put(atomicAdd(&c.tail, 1), idx);
-                    if (rr.heavy == 3 && F) lel += (unsigned long long)rr.vdeg;
+                    if (rr.heavy >= 3 && F) lel += (unsigned long long)rr.vdeg;
                 }
                 base = rr.base;
                 vdeg = F ? rr.vdeg : 0;
                 heavy = rr.heavy;
                 rtm1 = rr.rtm1;
-                if (TASK == TASK_INIT) tedges += (unsigned long long)__popcll(F) * (unsigned long long)rr.deg;
+                live = rr.live;
+                if (TASK == TASK_INIT)
+                    tedges += (unsigned long long)__popcll(Fp & ~rest) * (unsigned long long)rr.deg;
             }
         }
         int incl = vdeg;
@@ -1214,11 +1273,14 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
             const long long ib = __shfl_sync(FULL, base, lo);
             const int iex = __shfl_sync(FULL, excl, lo);
             const int ih = __shfl_sync(FULL, heavy, lo);
-            const uint32_t itm1 = __shfl_sync(FULL, rtm1, lo);
+            // forward rows share the uniform threshold; only initial gains
+            // use one-arc lists
+            const uint32_t itm1 = DIR == DIR_FWD ? co.uic_tm1 : __shfl_sync(FULL, rtm1, lo);
             const uint64_t iF = __shfl_sync(FULL, F, lo);
+            const uint64_t ilive = TASK == TASK_INIT ? __shfl_sync(FULL, live, lo) : 0ull;
             if (j < total) {
                 int y;
-                uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y);
+                uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y, ilive);
                 if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                     ml = 0;
                 if (TASK == TASK_INIT) ml = lmk_filter(a, word, y, ml, c.xbits, xany);
@@ -1700,8 +1762,8 @@ __global__ void __launch_bounds__(256) landmark_hist_kernel(EngineArgs a, LmkArg
         const int y = (int)(t - (long long)word * n);
         uint64_t rx[MAX_LMK];
         uint64_t any = 0;
-#pragma unroll
         const unsigned long long *rec = l.rx + (((size_t)word * (size_t)n + (size_t)y) << 3);
+#pragma unroll
         for (int i = 0; i < MAX_LMK; ++i) {
             rx[i] = i < K ? rec[i] : 0ull;
             any |= rx[i];
@@ -2041,11 +2103,15 @@ __global__ void live_masks_kernel(Coins co, long long m, const uint2 *fw, uint32
 
 // ================================================== forward row descriptors
 
-__global__ void __launch_bounds__(256) row_desc_kernel(GraphView g, int W, int4 *out)
+// One warp per (word, node).  With the forward lists, the word's 65 list
+// offsets of an indexed row give its live mask (nonempty lists), its list
+// base and whether every nonempty list holds one arc.
+__global__ void __launch_bounds__(256) row_desc_kernel(GraphView g, int W, const long long *fsoff, int4 *out)
 {
+    const int lane = threadIdx.x & 31;
     const long long total = (long long)W * g.n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; i < total; i += nwarps) {
         const int word = (int)(i / g.n);
         const int x = (int)(i - (long long)word * g.n);
         const int beg = __ldg(g.rp + x), deg = __ldg(g.rp + x + 1) - beg;
@@ -2057,8 +2123,26 @@ __global__ void __launch_bounds__(256) row_desc_kernel(GraphView g, int W, int4 
             vdeg = __ldg(g.hout.hcnt + (long long)h * W + word);
             heavy = 1;
         }
-        out[i] = make_int4((int)(unsigned)(unsigned long long)base, (int)(unsigned)((unsigned long long)base >> 32),
-                           vdeg, deg | (heavy << 31));
+        unsigned long long live = ~0ull, lb = 0;
+        int single = 0;
+        if (h >= 0 && fsoff) {
+            // offsets of lists 64x*W + 64w + b for b = 0..64 (the last is
+            // the end of list 63)
+            const long long *o = fsoff + (long long)x * 64 * W + 64LL * word;
+            const long long a0 = __ldg(o + lane), a1 = __ldg(o + lane + 1);
+            const long long b0 = __ldg(o + 32 + lane), b1 = __ldg(o + 33 + lane);
+            const unsigned lo = __ballot_sync(FULL, a1 > a0), hi = __ballot_sync(FULL, b1 > b0);
+            live = ((unsigned long long)hi << 32) | lo;
+            const long long first = __shfl_sync(FULL, a0, 0), end = __shfl_sync(FULL, b1, 31);
+            lb = (unsigned long long)first;
+            single = (end - first == (long long)__popcll(live)) && first < (1LL << 62) ? 1 : 0;
+        }
+        if (lane == 0) {
+            out[2 * i] = make_int4((int)(unsigned)(unsigned long long)base,
+                                   (int)(unsigned)((unsigned long long)base >> 32), vdeg, deg | (heavy << 31));
+            out[2 * i + 1] = make_int4((int)(unsigned)live, (int)(unsigned)(live >> 32), (int)(unsigned)lb,
+                                       (int)((unsigned)(lb >> 32) | ((unsigned)single << 31)));
+        }
     }
 }
 
@@ -2327,10 +2411,10 @@ sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int mod
 sg_status run_row_desc(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStream_t st)
 {
     const long long total = g->n * co.W;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)g->num_sms * 16);
+    const int blocks = (int)std::min<long long>((total * 32 + 255) / 256, (long long)g->num_sms * 16);
     GraphView v = view_of(g, ws, 1);
     v.rdesc = nullptr;
-    row_desc_kernel<<<blocks, 256, 0, st>>>(v, co.W, ws.rdesc.p);
+    row_desc_kernel<<<blocks, 256, 0, st>>>(v, co.W, ws.fl_on ? ws.fsoff.p : nullptr, ws.rdesc.p);
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
     return SG_OK;
