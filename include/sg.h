@@ -164,13 +164,16 @@ sg_status sg_set_landmarks(int32_t count);
  * it.  Applies to later calls.  Errors: SG_EINVAL unless 0 or 1. */
 sg_status sg_set_snapshot_lists(int32_t enable);
 
-/* Forward per-snapshot live lists for the initial gains: 1 (the default)
- * builds, per query, each indexed row's live out-arcs per snapshot (from
- * the heavy-row index), and a node reached in at most 4 of a word's
- * snapshots is expanded through those lists one snapshot at a time instead
- * of scanning all its index entries; 0 disables.  Skipped when the lists
- * would pass 8 GiB.  Results do not depend on it.  Applies to later calls.
- * Errors: SG_EINVAL unless 0 or 1. */
+/* Forward per-snapshot live lists for the initial gains and the forward
+ * walks: 1 (the default) builds, per query, each indexed row's live
+ * out-arcs per snapshot (from the heavy-row index).  With them, state bits
+ * of snapshots in which a node has no live out-arc are finished without a
+ * read; a node whose nonempty lists in a word hold one arc each expands
+ * one list entry per state bit; another node reached in at most 4 of a
+ * word's snapshots is expanded through those lists one snapshot at a time
+ * instead of scanning all its index entries.  0 disables.  Skipped when
+ * the lists would pass 8 GiB.  Results do not depend on it.  Applies to
+ * later calls.  Errors: SG_EINVAL unless 0 or 1. */
 sg_status sg_set_forward_lists(int32_t enable);
 
 /* Live-mask cache: 1 makes each later query first evaluate every arc's coin
