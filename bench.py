@@ -197,8 +197,7 @@ def run_reference(args, wl):
         return 0
     n, s, d = wl.graph()
     vals = []
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; warm-up steps are not repeated
+    # the oracle keeps no state between steps, so warm-up steps are not run
     sample = cores = None
     for _ in range(args.steps):
         v, sample, _t, cores = cpu_baseline(wl, n, s, d, target_s=args.ref_seconds)
