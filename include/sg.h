@@ -26,6 +26,15 @@
  *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Work is enqueued on it in stream order.
  *   - node ids are int32 in [0, n); arcs are directed u -> v.
+ *   - device-side failures: every device-side wait is bounded and every
+ *     device step checks its invariants; a failure sets the query's device
+ *     flags (a wait that gave up: SG_ETIMEOUT; a failed check:
+ *     SG_EINTERNAL).  A call that returns after the stream has finished
+ *     (stats requested or pageable host outputs) returns that status.  A
+ *     call that returns once the work is enqueued cannot; its outputs carry
+ *     the failure instead: every seed reads -1 and every gain (or initial
+ *     gain) reads -flags, where flag 2 marks a wait that gave up.  Valid
+ *     outputs are never negative.  The CUDA context stays usable.
  */
 #ifndef SG_H
 #define SG_H
@@ -88,7 +97,7 @@ typedef struct {
     float ms_rounds;            /* device time of the k selection rounds */
     float ms_fwd;               /* ... of which argmax + forward update, summed */
     float ms_total;             /* device time of the whole call */
-    int32_t status_flags;       /* nonzero: device-side check failed */
+    int32_t status_flags;       /* device flags: 1 no argmax candidate, 2 a bounded wait gave up, 8 union-find out of retries */
     int32_t kernel_launches;    /* kernels this call launched */
     int32_t heavy_index;        /* 1 if the heavy-row live index was used */
     int32_t mask_cache;         /* 1 if the live-mask cache was used */
@@ -251,7 +260,8 @@ sg_status sg_graph_info(const sg_graph *g, int64_t *n, int64_t *m_canonical);
  * Ties in the argmax go to the lowest node id among non-seeds, also when
  * every remaining gain is 0; seeds are never re-picked.
  * Errors: SG_EINVAL (bounds above, p outside [0,1] or NaN, unknown model),
- * SG_ENOMEM, SG_ECUDA. */
+ * SG_ENOMEM, SG_ECUDA; SG_ETIMEOUT / SG_EINTERNAL for a device-side failure
+ * (see the conventions above). */
 sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
                     int32_t *out_seeds, int64_t *out_gains, sg_stats *stats);
 
@@ -381,6 +391,16 @@ sg_status sg_graph_csr(const sg_graph *g, void *stream, int64_t *row_ptr, int32_
  * Errors: SG_EINVAL (NULL pointer, n out of range, device ordinal >= 64),
  * SG_ECUDA. */
 sg_status sg_argmax_noalloc(const int64_t *s, int64_t n, void *stream, int32_t *out_id, int64_t *out_gain);
+
+/* Testing hook (host fault injection): the next query started on any
+ * thread (sg_select, sg_select_ws, sg_init_gains, sg_select_celf, a batch
+ * or a server request) ORs `flags` into its device flags after its
+ * kernels, as a failing device step would, and then reports it as
+ * described in the conventions above (flag 2: a bounded wait gave up,
+ * SG_ETIMEOUT; flag 1: a failed check, SG_EINTERNAL).  0 clears a pending
+ * injection.  No kernel is made to wait, fault or trap.
+ * Errors: SG_EINVAL if flags < 0. */
+sg_status sg_debug_inject_flags(int32_t flags);
 
 /* Free a graph handle (NULL is a no-op).  Waits for the device. */
 void sg_free_graph(sg_graph *g);

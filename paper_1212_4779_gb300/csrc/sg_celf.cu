@@ -93,16 +93,14 @@ sg_status celf_impl(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     }
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st, nullptr));
+    SG_TRY(plant_injected_flags(ws, st));
     if (stats) SG_CUDA_TRY(cudaEventRecord(ev[1], st));
     std::vector<long long> s0(n);
     Ctl h;
     SG_CUDA_TRY(cudaMemcpyAsync(s0.data(), ws.s.p, n * 8, cudaMemcpyDeviceToHost, st));
     SG_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     SG_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h.flags) {
-        set_error("device-side check failed (flags 0x%x)", h.flags);
-        return SG_EINTERNAL;
-    }
+    SG_TRY(flags_status(h.flags));
 
     // scratch: the coverage copy of an evaluation, two counters, the source
     DBuf<unsigned long long> scratch;

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <new>
 #include <thread>
@@ -30,6 +31,57 @@ void set_error(const char *fmt, ...)
 }
 
 void clear_error() { g_err[0] = 0; }
+
+// ------------------------------------------------------------ device flags
+namespace {
+// flags the next query plants into its device flags (sg_debug_inject_flags)
+std::atomic<int> g_inject_flags{0};
+
+__global__ void set_flags_kernel(Ctl *ctl, int flags) { atomicOr(&ctl->flags, flags); }
+
+__global__ void poison_kernel(const Ctl *ctl, int32_t *seeds, long long *vals, long long count)
+{
+    const int32_t f = *(volatile const int32_t *)&ctl->flags;
+    if (!f) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (seeds) seeds[i] = -1;
+        vals[i] = -(long long)f;
+    }
+}
+}  // namespace
+
+sg_status flags_status(int32_t flags)
+{
+    if (!flags) return SG_OK;
+    if (flags & FLAG_WAIT) {
+        set_error("a bounded device-side wait gave up (device flags 0x%x)", flags);
+        return SG_ETIMEOUT;
+    }
+    set_error("device-side check failed (device flags 0x%x)", flags);
+    return SG_EINTERNAL;
+}
+
+sg_status plant_injected_flags(sg_workspace &ws, cudaStream_t st)
+{
+    const int f = g_inject_flags.exchange(0);
+    if (!f) return SG_OK;
+    set_flags_kernel<<<1, 1, 0, st>>>(ws.ctl.p, f);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
+    return SG_OK;
+}
+
+sg_status run_poison(const sg_graph *g, sg_workspace &ws, int32_t *seeds, long long *vals, long long count,
+                     cudaStream_t st)
+{
+    if (count <= 0) return SG_OK;
+    const int blocks = (int)std::min<long long>((count + 255) / 256, (long long)g->num_sms * 4);
+    poison_kernel<<<blocks, 256, 0, st>>>(ws.ctl.p, seeds, vals, count);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
+    return SG_OK;
+}
 
 // ------------------------------------------------------------------ memory
 int g_snapshot_lists = 1;
@@ -983,6 +1035,8 @@ sg_status cc_select_impl(sg_graph *g, sg_workspace &ws, const Coins &co, int32_t
         SG_TRY(run_argmax(g, ws, co, i, st));
         SG_TRY(cc_round(g, ws, co, st));
     }
+    SG_TRY(plant_injected_flags(ws, st));
+    SG_TRY(run_poison(g, ws, ws.out_seeds.p, ws.out_gains.p, k, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_seeds, ws.out_seeds.p, (size_t)k * 4, cudaMemcpyDefault, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_gains, ws.out_gains.p, (size_t)k * 8, cudaMemcpyDefault, st));
     if (stats) {
@@ -999,12 +1053,13 @@ sg_status cc_select_impl(sg_graph *g, sg_workspace &ws, const Coins &co, int32_t
         cudaEventElapsedTime(&stats->ms_init, ev[0], ev[1]);
         cudaEventElapsedTime(&stats->ms_rounds, ev[1], ev[2]);
         cudaEventElapsedTime(&stats->ms_total, ev[0], ev[2]);
-        if (h.flags) {
-            set_error("device-side check failed (flags 0x%x)", h.flags);
-            return SG_EINTERNAL;
-        }
-    } else if (is_pageable(out_seeds) || is_pageable(out_gains)) {
+        return flags_status(h.flags);
+    }
+    if (is_pageable(out_seeds) || is_pageable(out_gains)) {
+        int32_t fl = 0;
+        SG_CUDA_TRY(cudaMemcpyAsync(&fl, &ws.ctl.p->flags, 4, cudaMemcpyDeviceToHost, st));
         SG_CUDA_TRY(cudaStreamSynchronize(st));
+        return flags_status(fl);
     }
     return SG_OK;
 }
@@ -1085,6 +1140,8 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
         if (stats) SG_CUDA_TRY(cudaEventRecord(e_round[(size_t)i], st));
         SG_TRY(run_round(g, ws, co, model, heavy_on, i, st, stats ? e_fwd[(size_t)i] : nullptr));
     }
+    SG_TRY(plant_injected_flags(ws, st));
+    SG_TRY(run_poison(g, ws, ws.out_seeds.p, ws.out_gains.p, k, st));
     if (stats) {
         SG_CUDA_TRY(cudaEventRecord(e_round[(size_t)k], st));
         SG_CUDA_TRY(cudaEventRecord(e_end, st));
@@ -1127,12 +1184,13 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
             fsum += t;
         }
         stats->ms_fwd = fsum;
-        if (h.flags) {
-            set_error("device-side check failed (flags 0x%x)", h.flags);
-            return SG_EINTERNAL;
-        }
-    } else if (is_pageable(out_seeds) || is_pageable(out_gains)) {
+        return flags_status(h.flags);
+    }
+    if (is_pageable(out_seeds) || is_pageable(out_gains)) {
+        int32_t fl = 0;
+        SG_CUDA_TRY(cudaMemcpyAsync(&fl, &ws.ctl.p->flags, 4, cudaMemcpyDeviceToHost, st));
         SG_CUDA_TRY(cudaStreamSynchronize(st));
+        return flags_status(fl);
     }
     return SG_OK;
 }
@@ -1140,6 +1198,17 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
 }  // namespace
 
 extern "C" {
+
+sg_status sg_debug_inject_flags(int32_t flags)
+{
+    clear_error();
+    if (flags < 0) {
+        set_error("sg_debug_inject_flags: flags must be >= 0, got %d", flags);
+        return SG_EINVAL;
+    }
+    g_inject_flags.store(flags);
+    return SG_OK;
+}
 
 sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
                     int32_t *out_seeds, int64_t *out_gains, sg_stats *stats)
@@ -1311,16 +1380,14 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
         SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
         SG_TRY(cc_init_gains(g, ws, co, st));
+        SG_TRY(plant_injected_flags(ws, st));
+        SG_TRY(run_poison(g, ws, nullptr, ws.s.p, g->n, st));
         SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));
         Ctl h;
         SG_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         SG_CUDA_TRY(cudaStreamSynchronize(st));
         if (init_edges) *init_edges = h.init_edges;
-        if (h.flags) {
-            set_error("device-side check failed (flags 0x%x)", h.flags);
-            return SG_EINTERNAL;
-        }
-        return SG_OK;
+        return flags_status(h.flags);
     }
     const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
@@ -1338,18 +1405,21 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
     }
     if (ws.lm_on) SG_TRY(run_mask_cache(g, ws, co, model, st));
     SG_TRY(run_init_gains(g, ws, co, model, heavy_on, st));
+    SG_TRY(plant_injected_flags(ws, st));
+    SG_TRY(run_poison(g, ws, nullptr, ws.s.p, g->n, st));
     SG_CUDA_TRY(cudaMemcpyAsync(out_s, ws.s.p, (size_t)g->n * 8, cudaMemcpyDefault, st));
     if (init_edges) {
         Ctl h;
         SG_CUDA_TRY(cudaMemcpyAsync(&h, ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         SG_CUDA_TRY(cudaStreamSynchronize(st));
         *init_edges = h.init_edges;
-        if (h.flags) {
-            set_error("device-side check failed (flags 0x%x)", h.flags);
-            return SG_EINTERNAL;
-        }
-    } else if (is_pageable(out_s)) {
+        return flags_status(h.flags);
+    }
+    if (is_pageable(out_s)) {
+        int32_t fl = 0;
+        SG_CUDA_TRY(cudaMemcpyAsync(&fl, &ws.ctl.p->flags, 4, cudaMemcpyDeviceToHost, st));
         SG_CUDA_TRY(cudaStreamSynchronize(st));
+        return flags_status(fl);
     }
     return SG_OK;
 }

@@ -345,6 +345,21 @@ sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out,
                          const int32_t *cid = nullptr);
 
 // host driver (sg_host.cu)
+// Device flags (Ctl::flags) a query can leave: FLAG_NO_CANDIDATE, the argmax
+// found no candidate; FLAG_WAIT, a bounded device-side wait gave up;
+// FLAG_UNION_FIND, the union-find ran out of hooking retries.
+enum { FLAG_NO_CANDIDATE = 1, FLAG_WAIT = 2, FLAG_UNION_FIND = 8 };
+// SG_OK for flags 0; SG_ETIMEOUT when FLAG_WAIT is set; SG_EINTERNAL for
+// any other flag.  Sets the thread's error text on failure.
+sg_status flags_status(int32_t flags);
+// Testing hook (sg_debug_inject_flags): OR the flags set aside for the next
+// query into ws's device flags, as a failing device step would.
+sg_status plant_injected_flags(sg_workspace &ws, cudaStream_t st);
+// When ws's device flags are set: seeds[0..count) = -1 (if seeds) and
+// vals[0..count) = -flags, so that outputs of an asynchronous call carry
+// the failure.  Nothing is written otherwise.
+sg_status run_poison(const sg_graph *g, sg_workspace &ws, int32_t *seeds, long long *vals, long long count,
+                     cudaStream_t st);
 sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
                       int32_t *out_seeds, int64_t *out_gains, sg_stats *stats, bool prepare_only);
 sg_status check_query(const sg_graph *g, int32_t R, int32_t k);

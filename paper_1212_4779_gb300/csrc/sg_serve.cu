@@ -202,6 +202,9 @@ void srv_retire(sg_server *s)
         } else {
             r->seeds.assign(sl.h_seeds, sl.h_seeds + r->k);
             r->gains.assign(sl.h_gains, sl.h_gains + r->k);
+            // a failed device step leaves seeds of -1 and gains of -flags
+            if (r->k > 0 && sl.h_seeds[0] == -1 && sl.h_gains[0] < 0)
+                r->status = flags_status((int32_t)(-sl.h_gains[0]));
         }
         r->t_done = now_ms();
         r->state = 2;
