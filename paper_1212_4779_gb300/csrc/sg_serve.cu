@@ -236,6 +236,10 @@ int srv_workspace(sg_server *s, sg_graph *g, int32_t W, bool *impossible)
         delete w;
         s->used -= s->pool[(size_t)lru].bytes;
         s->pool.erase(s->pool.begin() + lru);
+        // running slots index the pool: entries after the erased one moved
+        // down (the erased entry was idle, so no slot held it)
+        for (auto &sl : s->slots)
+            if (sl.req && sl.ws_index > lru) --sl.ws_index;
     }
     if (s->used + need > s->budget) {
         *impossible = s->running == 0;  // nothing will ever free memory

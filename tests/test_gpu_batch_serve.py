@@ -176,3 +176,35 @@ def test_server_admission_limits(sg, mixed):
             pytest.fail("request never finished")
     finally:
         sg.sg_server_destroy(srv)
+
+
+def test_server_evicts_idle_workspaces_while_others_run(sg, mixed):
+    """A memory budget of two workspaces over five graphs: admitting a
+    request evicts idle workspaces of other graphs while up to two requests
+    run.  Running requests must keep their own workspaces through the
+    evictions, so every result still equals the query run alone."""
+    graphs, queries, alone = mixed
+    k_cap = 32
+    need = max(sg.sg_workspace_bytes(g.handle, 256, k_cap) for g, *_ in graphs)
+    srv = sg.sg_server_create(max_running=2, memory_budget=2 * need + (1 << 20), k_cap=k_cap)
+    try:
+        pending = []
+        for rep in range(2):
+            for i, qq in enumerate(queries):
+                rid = sg.sg_server_submit(srv, graphs[qq["gi"]][0].handle, qq["R"], qq["k"], qq["model"], qq["p"],
+                                          qq["seed"])
+                pending.append((rid, i))
+        deadline = time.time() + 300
+        while pending and time.time() < deadline:
+            rest = []
+            for rid, i in pending:
+                done, seeds, gains, _ = sg.sg_server_poll(srv, rid, queries[i]["k"])
+                if not done:
+                    rest.append((rid, i))
+                    continue
+                assert np.array_equal(seeds, alone[i].seeds) and np.array_equal(gains, alone[i].gains)
+            pending = rest
+            time.sleep(0.001)
+        assert not pending
+    finally:
+        sg.sg_server_destroy(srv)
