@@ -47,9 +47,10 @@ UNIT = "GTEPS"
 # neighbour's 8-byte state word: an arc record is 8 bytes (destination and
 # threshold); a live-index entry (heavy rows) or a cached arc is a 4-byte
 # destination and an 8-byte live mask; a list entry is a 4-byte destination.
-BYTES_PER_ELEMENT = 16
-BYTES_PER_ELEMENT_INDEXED = 20
-BYTES_PER_LIST_ELEMENT = 12
+# algorithmic bytes of one expanded element of the dominant kernel
+BYTES_PER_ELEMENT = 16  # hashed arc: 8-byte arc record (destination, threshold) + 8-byte state word
+BYTES_PER_ELEMENT_INDEXED = 20  # index entry: 4-byte neighbour + 8-byte live mask + 8-byte state word
+BYTES_PER_LIST_ELEMENT = 12  # per-snapshot list entry: 4-byte neighbour + 8-byte state word
 LANES_PER_SM = 128  # INT32 lanes per SM per clock (4 SMSP x 32)
 
 
@@ -553,8 +554,10 @@ def main():
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     # dominant kernel: the initial-gain tier-3 launch (cooperative engine over
-    # dense per-block arrays); algorithmic bytes = elements expanded x 16 B
-    # (an 8-byte arc record or index entry plus the neighbour's 8-byte state)
+    # dense per-block arrays).  Algorithmic bytes per element: an index entry
+    # (4-byte neighbour + 8-byte live mask) or arc record, plus the
+    # neighbour's 8-byte state word; a per-snapshot list entry is a 4-byte
+    # neighbour plus the state word.
     t3_ms = float(np.mean(t_t3))
     bpe = BYTES_PER_ELEMENT_INDEXED if (st_last["mask_cache"] or st_last["heavy_index"]) else BYTES_PER_ELEMENT
     t3_list = st_last["list_elems"][2]
