@@ -370,10 +370,10 @@ sg_status sg_graph_csr(const sg_graph *g, void *stream, int64_t *row_ptr, int32_
 
 /* Argmax over a gain vector the caller owns, with no device allocation.
  * The paper has no counterpart: this exists for callers that cannot
- * allocate device memory where they need the argmax -- code recording a
- * CUDA graph (an allocation would break the capture), latency-bound serving
- * loops that must not stall on an allocation, or plug-ins whose host
- * framework owns all device memory.
+ * allocate device memory where they need the argmax -- latency-bound
+ * serving loops that must not stall on a synchronous allocation, or
+ * plug-ins whose host framework owns all device memory through its own
+ * pool and hands out only the buffers it manages.
  *   s         int64[n] in device-accessible memory; entries < 0 are
  *             excluded (sg_select marks seeds that way)
  *   n         1 <= n <= 2^31 - 1
@@ -383,12 +383,14 @@ sg_status sg_graph_csr(const sg_graph *g, void *stream, int64_t *row_ptr, int32_
  * Work is enqueued on `stream`; the call returns without waiting.
  * Scratch: one statically sized array of about 12 KB per device (1024
  * block partials and a counter), held until the process exits.  The first
- * call on a device looks up that array's address (cudaGetSymbolAddress), so
- * make the first call before any stream capture.  Every call shares the
- * array: calls that overlap on the GPU (other streams, other threads) race
- * and must be serialised by the caller.  No cudaMalloc, cudaFree or other
- * allocating routine is called.
- * Errors: SG_EINVAL (NULL pointer, n out of range, device ordinal >= 64),
+ * call in a CUDA context (normally the device's primary context; with none
+ * current, the current device's primary context is bound) looks up that
+ * array's address there with cudaGetSymbolAddress and caches it for that
+ * context, so make the first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  No cudaMalloc,
+ * cudaFree or other allocating routine is called.
+ * Errors: SG_EINVAL (NULL pointer, n out of range, more than 64 contexts),
  * SG_ECUDA. */
 sg_status sg_argmax_noalloc(const int64_t *s, int64_t n, void *stream, int32_t *out_id, int64_t *out_gain);
 
@@ -401,6 +403,17 @@ sg_status sg_argmax_noalloc(const int64_t *s, int64_t n, void *stream, int32_t *
  * injection.  No kernel is made to wait, fault or trap.
  * Errors: SG_EINVAL if flags < 0. */
 sg_status sg_debug_inject_flags(int32_t flags);
+
+/* Testing hook: the number of polls a bounded device-side wait of the
+ * traversal engines makes before it gives up (an idle warp waiting for work
+ * in a block-shared queue, a warp waiting for a claimed queue entry to
+ * land; each poll sleeps 32-64 ns).  A wait that runs out sets flag 2 in
+ * the query's device flags and returns, and the query reports SG_ETIMEOUT
+ * as described in the conventions above; the engine's per-block state is
+ * cleaned up so the next query is exact.  0 restores the default (2^22
+ * polls, about a second).  Applies to queries started later, on every
+ * thread.  Errors: SG_EINVAL if polls < 0. */
+sg_status sg_debug_set_wait_limit(int64_t polls);
 
 /* Free a graph handle (NULL is a no-op).  Waits for the device. */
 void sg_free_graph(sg_graph *g);

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(CC_T) cc_gains_kernel(int n, int R, const int3
 {
     __shared__ unsigned long long red[CC_T / 32];
     unsigned long long ed = 0;
-    for (int v = blockIdx.x * CC_T + threadIdx.x; v < n; v += gridDim.x * CC_T) {
+    for (long long v = (long long)blockIdx.x * CC_T + threadIdx.x; v < n; v += (long long)gridDim.x * CC_T) {
         long long acc = 0;
         for (int r = 0; r < R; ++r) {
             const size_t q = (size_t)r * n + __ldg(lab + (size_t)r * n + v);
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(CC_T) cc_dec_kernel(int n, int R, const int32_
         sh[R + r] = nsz[r];
     }
     __syncthreads();
-    for (int v = blockIdx.x * CC_T + threadIdx.x; v < n; v += gridDim.x * CC_T) {
+    for (long long v = (long long)blockIdx.x * CC_T + threadIdx.x; v < n; v += (long long)gridDim.x * CC_T) {
         long long dec = 0;
         for (int r = 0; r < R; ++r)
             if (sh[R + r] && __ldg(lab + (size_t)r * n + v) == sh[r]) dec += sh[R + r];

@@ -1210,6 +1210,17 @@ sg_status sg_debug_inject_flags(int32_t flags)
     return SG_OK;
 }
 
+sg_status sg_debug_set_wait_limit(int64_t polls)
+{
+    clear_error();
+    if (polls < 0) {
+        set_error("sg_debug_set_wait_limit: polls must be >= 0, got %lld", (long long)polls);
+        return SG_EINVAL;
+    }
+    g_wait_polls = polls == 0 ? WAIT_POLLS_DEFAULT : (long long)polls;
+    return SG_OK;
+}
+
 sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
                     int32_t *out_seeds, int64_t *out_gains, sg_stats *stats)
 {

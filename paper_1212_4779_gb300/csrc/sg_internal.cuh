@@ -295,6 +295,10 @@ extern thread_local int g_launches;
 extern int g_tier_limit[2];
 // landmark nodes used for the initial gains (0 .. 8)
 extern int g_landmarks;
+// polls a bounded device-side wait of the traversal engines makes before it
+// gives up (default 2^22; a testing hook can shorten it)
+extern long long g_wait_polls;
+constexpr long long WAIT_POLLS_DEFAULT = 1LL << 22;
 // per-snapshot live in-lists of heavy rows for the reverse update (0 or 1)
 extern int g_snapshot_lists;
 // nonzero: queries build and use the live-mask cache when it fits

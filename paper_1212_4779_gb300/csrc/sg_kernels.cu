@@ -316,6 +316,7 @@ struct EngineArgs {
     const unsigned long long *lmk_E;
     long long ntasks;       // TASK_INIT: n * W
     int limit;              // keys a warp table may hold before the task moves up a tier
+    long long spin;         // polls a bounded wait makes before it gives up
 };
 
 
@@ -1014,7 +1015,6 @@ struct SlotArgs {
 // per SM set the throughput more than threads per task.  The dense tier
 // runs three 512-thread blocks per SM (40 registers).
 constexpr int CO_LOGC = 12;  // the largest shared-memory table
-constexpr long long CO_SPIN = 1LL << 22;
 constexpr unsigned short QE16 = 0xFFFF;
 enum { TAB_HASH = 0, TAB_DENSE = 1 };
 template <int TAB, int LOGC>
@@ -1081,10 +1081,10 @@ struct CoopTab<TAB_HASH, LOGC> {
     __device__ __forceinline__ void note_new(int, CoopCtl &) {}
     __device__ __forceinline__ int node(int idx) const { return key[idx]; }
     __device__ __forceinline__ void put(int pos, int idx) { *(volatile unsigned short *)&queue[pos & (C - 1)] = (unsigned short)idx; }
-    __device__ __forceinline__ int take(int pos, CoopCtl &c)
+    __device__ __forceinline__ int take(int pos, CoopCtl &c, long long spin)
     {
         volatile unsigned short *q = &queue[pos & (C - 1)];
-        for (long long i = 0; i < CO_SPIN; ++i) {
+        for (long long i = 0; i < spin; ++i) {
             const unsigned short v = *q;
             if (v != QE16) {
                 *q = QE16;
@@ -1121,10 +1121,10 @@ struct CoopTab<TAB_DENSE, LOGC> {
     __device__ __forceinline__ void note_new(int y, CoopCtl &c) { touched[atomicAdd(&c.nkeys, 1)] = y; }
     __device__ __forceinline__ int node(int idx) const { return idx; }
     __device__ __forceinline__ void put(int pos, int idx) { *(volatile int *)&queue[pos & qmask] = idx; }
-    __device__ __forceinline__ int take(int pos, CoopCtl &c)
+    __device__ __forceinline__ int take(int pos, CoopCtl &c, long long spin)
     {
         volatile int *q = &queue[pos & qmask];
-        for (long long i = 0; i < CO_SPIN; ++i) {
+        for (long long i = 0; i < spin; ++i) {
             const int v = *q;
             if (v != EMPTY_KEY) {
                 *q = EMPTY_KEY;
@@ -1216,7 +1216,7 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
             }
             done = __shfl_sync(FULL, done, 0);
             if (done) break;
-            if (++idle > CO_SPIN) {
+            if (++idle > a.spin) {
                 if (lane == 0) c.err = 1;
                 break;
             }
@@ -1229,7 +1229,7 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
         uint32_t rtm1 = 0;
         uint64_t F = 0, live = 0;
         if (lane < nb) {
-            const int idx = T.take(qb + lane, c);
+            const int idx = T.take(qb + lane, c, a.spin);
             if (idx >= 0) {
                 F = atomicExch(&T.pendr(idx), 0ull);
                 const uint64_t Fp = F;
@@ -1842,11 +1842,12 @@ __global__ void __launch_bounds__(AM_T) argmax_kernel(long long *s, int n, Ctl *
     __shared__ int sh_last;
     long long bg = -1;
     int bi = -1;
-    for (int v = blockIdx.x * AM_T + threadIdx.x; v < n; v += gridDim.x * AM_T) {
+    // 64-bit index: n may lie within one grid stride of 2^31
+    for (long long v = (long long)blockIdx.x * AM_T + threadIdx.x; v < n; v += (long long)gridDim.x * AM_T) {
         const long long x = s[v];
         if (x > bg) {
             bg = x;
-            bi = v;
+            bi = (int)v;
         }
     }
 #pragma unroll
@@ -2201,6 +2202,7 @@ EngineArgs engine_args(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
     a.lmk_E = ws.lmk_E.p;
     a.ntasks = 0;
     a.limit = 1;
+    a.spin = g_wait_polls;
     return a;
 }
 
@@ -2379,6 +2381,7 @@ sg_status round_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy_on, 
 }  // namespace
 
 thread_local int g_launches = 0;
+long long g_wait_polls = WAIT_POLLS_DEFAULT;
 int g_tier_limit[2] = {(1 << T1_LOGC) / 2, (1 << CO_LOGC) / 2};
 int g_landmarks = 8;
 
@@ -2440,6 +2443,7 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
         return rc;
     }
     EngineArgs a{};
+    a.spin = g_wait_polls;
     a.g = view_of(g, g->ws, 0);
     a.g.lm_out = nullptr;  // caches belong to another query's snapshots
     a.g.lm_in = nullptr;
@@ -2475,6 +2479,7 @@ sg_status run_walk(sg_graph *g, const sg_workspace &ws, const Coins &co, int mod
                    int32_t *qb, long long *d_total, unsigned long long *d_edges, cudaStream_t st)
 {
     EngineArgs a{};
+    a.spin = g_wait_polls;
     a.g = view_of(g, ws, heavy_on);
     a.co = co;
     a.lmk_k = 0;

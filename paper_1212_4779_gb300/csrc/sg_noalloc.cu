@@ -1,14 +1,15 @@
 // sg_noalloc.cu -- argmax over a caller's gain vector without allocating.
 //
 // Who needs this: code that cannot call cudaMalloc (or any allocator) at
-// the moment it needs the argmax -- for example code recording a CUDA graph
-// (an allocation inside stream capture breaks the capture), a latency-bound
-// serving loop that must not stall on a synchronous allocation, or a
-// plug-in running inside a host framework that owns every byte of device
-// memory through its own pool.  Such callers pass their own input and
-// output buffers; the only scratch used here is the statically sized
-// `na_scratch` array below, which the CUDA runtime places in device memory
-// when the library is loaded.
+// the moment it needs the argmax -- for example a latency-bound serving
+// loop that must not stall on a synchronous allocation, or a plug-in
+// running inside a host framework that owns every byte of device memory
+// through its own pool and hands out only the buffers it manages.  Such
+// callers pass their own input and output buffers; the only scratch used
+// here is the statically sized `na_scratch` array below, which the CUDA
+// runtime places in device memory when the library is loaded.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,7 +22,7 @@ namespace {
 
 constexpr int NA_THREADS = 256;
 constexpr int NA_MAX_BLOCKS = 1024;
-constexpr int NA_MAX_DEVICES = 64;
+constexpr int NA_MAX_CONTEXTS = 64;
 
 // Per-block partial maxima and the arrival counter of the last-block
 // reduction: 1024 x 12 bytes + 4 bytes.
@@ -36,8 +37,16 @@ struct NaScratch {
 // address comes from cudaGetSymbolAddress (na_scratch_address below).
 static __device__ __align__(256) NaScratch na_scratch;
 
+// The looked-up address is only valid in the CUDA context it was looked up
+// in, so it is cached per context, keyed by the driver's process-unique
+// context id (a context created after a device reset gets a new id).
 std::mutex na_mu;
-NaScratch *na_addr[NA_MAX_DEVICES] = {};
+struct NaEntry {
+    unsigned long long ctx_id;
+    NaScratch *addr;
+};
+NaEntry na_cache[NA_MAX_CONTEXTS] = {};
+int na_cached = 0;
 
 __device__ __forceinline__ bool na_better(long long g1, int i1, long long g2, int i2)
 {
@@ -66,11 +75,13 @@ __global__ void __launch_bounds__(NA_THREADS) na_argmax_kernel(const long long *
     __shared__ int last;
     long long bg = -1;
     int bi = -1;
-    for (int v = blockIdx.x * NA_THREADS + threadIdx.x; v < n; v += gridDim.x * NA_THREADS) {
+    // 64-bit index: n may lie within one grid stride of 2^31
+    for (long long v = (long long)blockIdx.x * NA_THREADS + threadIdx.x; v < n;
+         v += (long long)gridDim.x * NA_THREADS) {
         const long long x = s[v];
         if (x > bg) {
             bg = x;
-            bi = v;
+            bi = (int)v;
         }
     }
     na_warp_best(bg, bi);
@@ -123,27 +134,62 @@ __global__ void __launch_bounds__(NA_THREADS) na_argmax_kernel(const long long *
     }
 }
 
-// Device address of na_scratch on the current device, looked up once per
-// device (cudaGetSymbolAddress with that device current).
-sg_status na_scratch_address(NaScratch **out)
+// Id of the current CUDA context (the current device's primary context
+// when no context is current yet), via the driver entry points the runtime
+// exposes, so no link against the driver library is needed.
+sg_status na_context_id(unsigned long long *id)
 {
-    int dev = 0;
-    SG_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NA_MAX_DEVICES) {
-        sgi::set_error("sg_argmax_noalloc: device ordinal %d is beyond %d", dev, NA_MAX_DEVICES);
-        return SG_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(na_mu);
-    if (!na_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
-        if (e != cudaSuccess || !p) {
-            sgi::set_error("sg_argmax_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    if (!get_cur || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            sgi::set_error("sg_argmax_noalloc: driver entry points cuCtxGetCurrent/cuCtxGetId unavailable");
             return SG_ECUDA;
         }
-        na_addr[dev] = static_cast<NaScratch *>(p);
+        get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+        get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
     }
-    *out = na_addr[dev];
+    CUcontext ctx = nullptr;
+    if (get_cur(&ctx) == CUDA_SUCCESS && !ctx) {
+        // nothing current yet: bind the current device's primary context
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) get_cur(&ctx);
+    }
+    if (!ctx || get_id(ctx, id) != CUDA_SUCCESS) {
+        sgi::set_error("sg_argmax_noalloc: no current CUDA context");
+        return SG_ECUDA;
+    }
+    return SG_OK;
+}
+
+// Device address of na_scratch in the current context, looked up once per
+// context (cudaGetSymbolAddress with that context's device current).
+sg_status na_scratch_address(NaScratch **out)
+{
+    unsigned long long id = 0;
+    SG_TRY(na_context_id(&id));
+    std::lock_guard<std::mutex> lock(na_mu);
+    for (int i = 0; i < na_cached; ++i)
+        if (na_cache[i].ctx_id == id) {
+            *out = na_cache[i].addr;
+            return SG_OK;
+        }
+    if (na_cached >= NA_MAX_CONTEXTS) {
+        sgi::set_error("sg_argmax_noalloc: more than %d CUDA contexts", NA_MAX_CONTEXTS);
+        return SG_EINVAL;
+    }
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
+    if (e != cudaSuccess || !p) {
+        sgi::set_error("sg_argmax_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        return SG_ECUDA;
+    }
+    na_cache[na_cached++] = NaEntry{id, static_cast<NaScratch *>(p)};
+    *out = static_cast<NaScratch *>(p);
     return SG_OK;
 }
 

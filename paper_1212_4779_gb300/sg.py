@@ -33,7 +33,7 @@ EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg
            "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
            "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_graph_trim", "sg_select",
            "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version",
-           "sg_debug_inject_flags")
+           "sg_debug_inject_flags", "sg_debug_set_wait_limit")
 
 
 class SGError(RuntimeError):
@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
         L.sg_set_forward_lists.argtypes = [i32]
         L.sg_graph_trim.argtypes = [P]
         L.sg_debug_inject_flags.argtypes = [i32]
+        L.sg_debug_set_wait_limit.argtypes = [i64]
         L.sg_spread.argtypes = [P, i32, sg_cascade, u64, P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(u64)]
         L.sg_select_celf.argtypes = [P, i32, i32, sg_cascade, u64, P, P, P, ctypes.POINTER(i64), P]
         L.sg_argmax_noalloc.argtypes = [P, i64, P, P, P]
@@ -145,7 +146,7 @@ def lib() -> ctypes.CDLL:
                      "sg_server_poll", "sg_server_counts", "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
                      "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
                      "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr",
-                     "sg_debug_inject_flags"):
+                     "sg_debug_inject_flags", "sg_debug_set_wait_limit"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -320,6 +321,11 @@ def sg_load_graph_coo(n, m, src, dst, stream=None):
 def sg_debug_inject_flags(flags: int):
     """Testing hook: the next query plants `flags` into its device flags."""
     _check(lib().sg_debug_inject_flags(int(flags)))
+
+
+def sg_debug_set_wait_limit(polls: int):
+    """Testing hook: polls a bounded device wait makes before giving up (0: default)."""
+    _check(lib().sg_debug_set_wait_limit(int(polls)))
 
 
 def sg_graph_trim(h):

@@ -157,3 +157,35 @@ def test_server_request_reports_the_status(sg, case):
         assert np.array_equal(gains, want["gains"])
     finally:
         sg.sg_server_destroy(srv)
+
+
+def test_real_bounded_wait_runs_out_and_reports_timeout(sg):
+    """A real device wait running out, without a fault: every task is sent to
+    the block-shared engines (tier limits of one key), whose idle warps poll
+    the block's queue while one warp expands; with the wait budget cut to one
+    poll they give up, set the wait flag and return.  The call reports
+    SG_ETIMEOUT; with the default budget restored the next query on the same
+    context is exact again (the engines clean their state on the way out)."""
+    n, s, d = inputs.workload("cl15k_wic").graph()
+    g = sg.Graph.from_coo(n, s, d)
+    want = oracle.Graph(n, s, d, "wic").select(100, 10, 7)
+    try:
+        sg.sg_set_engine_limits(1, 1)
+        sg.sg_debug_set_wait_limit(1)
+        with pytest.raises(sg.SGError) as e:
+            g.select(100, 10, "wic", 0.0, 7, stats=True)
+        assert e.value.status == sg.SG_ETIMEOUT
+        with pytest.raises(sg.SGError) as e:
+            g.init_gains(100, "wic", 0.0, 7)
+        assert e.value.status == sg.SG_ETIMEOUT
+    finally:
+        sg.sg_debug_set_wait_limit(0)
+    try:
+        r = g.select(100, 10, "wic", 0.0, 7, stats=True)  # still all in the block-shared engines
+        assert r.stats["status_flags"] == 0
+        assert np.array_equal(r.seeds, want["seeds"]) and np.array_equal(r.gains, want["gains"])
+    finally:
+        sg.sg_set_engine_limits(256, 2048)
+    r = g.select(100, 10, "wic", 0.0, 7)
+    assert np.array_equal(r.seeds, want["seeds"]) and np.array_equal(r.gains, want["gains"])
+    g.close()

@@ -426,17 +426,34 @@ def rmat20(sg):
     return wl, g, o, res
 
 
-def test_rmat20_sampled_initial_gains(sg, rmat20):
+@pytest.fixture(scope="module")
+def rmat20_oracle(rmat20):
+    """The oracle's whole selection on the full R-MAT scale-20 query (R = 256,
+    k = 50, hash seed 11) by lazy forward evaluation (StaticGreedyCELF, the
+    route the pins prove equal to Algorithm 2), with its initial gains."""
     wl, g, o, res = rmat20
-    s_gpu, _ = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
-    rng = np.random.default_rng(20)
-    outdeg = np.diff(o.rp)
-    hubs = np.argsort(-outdeg)[:16]
-    sample = np.unique(np.r_[rng.choice(g.n, 48, replace=False), hubs, res.seeds[:4]]).astype(np.int32)
-    want, _ = o.reach_sums(wl.R, wl.seed, sample)
-    assert np.array_equal(s_gpu[sample], want)
-    # the first seed is the argmax (lowest id on ties) of the initial gains
-    assert res.seeds[0] == int(np.argmax(s_gpu)) and res.gains[0] == s_gpu.max()
+    return o.select(wl.R, wl.k, wl.seed, mode=oracle.CELF, want_init=True)
+
+
+def test_rmat20_seeds_and_gains_equal_oracle(sg, rmat20, rmat20_oracle):
+    """Full size, no sampling: all 50 seeds and gains of sg_select equal the
+    oracle's, as do the initial and forward snapshot-edge counters."""
+    wl, g, o, res = rmat20
+    ref = rmat20_oracle
+    assert np.array_equal(res.seeds, ref["seeds"])
+    assert np.array_equal(res.gains, ref["gains"])
+    assert res.stats["init_edges"] == int(ref["counters"][0])
+    assert res.stats["fwd_edges"] == int(ref["counters"][1])
+    assert res.stats["status_flags"] == 0
+
+
+def test_rmat20_full_initial_gains_equal_oracle(sg, rmat20, rmat20_oracle):
+    """The whole 1,048,576-entry initial-gain vector (Algorithm 2, first
+    loop) against the oracle's, element by element."""
+    wl, g, o, res = rmat20
+    s_gpu, e_gpu = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
+    assert np.array_equal(s_gpu, rmat20_oracle["s_init"])
+    assert e_gpu == int(rmat20_oracle["counters"][0])
 
 
 def test_rmat20_gains_are_exact_marginals(sg, rmat20):
@@ -453,11 +470,10 @@ def test_rmat20_gains_are_exact_marginals(sg, rmat20):
     assert prev == int(gains.sum())
 
 
-def test_rmat20_mask_cache_equals_in_register_coins(sg, rmat20):
+def test_rmat20_mask_cache_equals_in_register_coins(sg, rmat20, rmat20_oracle):
     """Full size: the live-mask cache gives the same seeds, gains and
-    counters as in-register hashing (which the tests above tie to the
-    oracle), and the same initial gains on a sample checked against the
-    oracle."""
+    counters as in-register hashing, and the same full initial-gain vector
+    as the oracle."""
     wl, g, o, res = rmat20
     sg.sg_set_mask_cache(1)
     try:
@@ -469,9 +485,7 @@ def test_rmat20_mask_cache_equals_in_register_coins(sg, rmat20):
     assert np.array_equal(r2.seeds, res.seeds) and np.array_equal(r2.gains, res.gains)
     for key in ("init_edges", "fwd_edges", "rev_edges"):
         assert r2.stats[key] == res.stats[key]
-    sample = np.unique(np.r_[np.random.default_rng(21).choice(g.n, 32, replace=False), res.seeds[:4]]).astype(np.int32)
-    want, _ = o.reach_sums(wl.R, wl.seed, sample)
-    assert np.array_equal(s_gpu[sample], want)
+    assert np.array_equal(s_gpu, rmat20_oracle["s_init"])
 
 
 def test_rmat20_greedy_choice_beats_sampled_candidates(sg, rmat20):

@@ -61,6 +61,36 @@ def test_coin_word_layout(oracle_mod):
     assert not oracle.live(0x1234, 77, 99, hi)
 
 
+@pytest.mark.parametrize("R", [1, 63, 64, 65, 130])
+@pytest.mark.parametrize("model,p", [("uic", 0.3), ("wic", 0.0), ("uic_undirected", 0.4)])
+def test_live_masks_bit_by_bit(oracle_mod, R, model, p):
+    """or_live_masks against the pure-Python coin, bit by bit: bit b of word
+    w of arc e is the coin of snapshot 64w + b (Section 3.1 snapshot; reading
+    A9: snapshots 0..R-1, the last word masked to R mod 64 bits), for every
+    arc and snapshot of a small graph, including the word boundary cases."""
+    if model == "uic_undirected":
+        n, s, d = inputs.chung_lu_undirected(40, 90, 2.5, 4.0, 11)
+    else:
+        n, s, d = inputs.random_small(40, 160, 9)
+    g = oracle.Graph(n, s, d, model, p)
+    seed = 0xF00DFACE12345 ^ R
+    masks = g.live_masks(R, seed)
+    W = (R + 63) // 64
+    assert masks.shape == (g.m, W)
+    arcs = brute.canonical_arcs(s, d)
+    assert len(arcs) == g.m
+    thr = brute.thresholds(n, arcs, model, p)
+    cid = brute.coin_ids(arcs, model)
+    for e in range(g.m):
+        for w in range(W):
+            want = 0
+            for b in range(64):
+                r = 64 * w + b
+                if r < R and brute.coin(seed, r, cid[e], thr[e]):
+                    want |= 1 << b
+            assert int(masks[e, w]) == want, (e, w)
+
+
 @pytest.mark.parametrize("p,want", [(0.1, 429496729), (0.01, 42949672), (0.02, 85899345),
                                     (0.05, 214748364), (0.0, 0), (1.0, 1 << 32), (0.5, 1 << 31)])
 def test_uic_threshold_exact(oracle_mod, p, want):

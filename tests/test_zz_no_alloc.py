@@ -1,8 +1,8 @@
 """The allocation-free argmax entry point agrees with sg_select.
 
 Callers that cannot allocate device memory where they need the argmax --
-code recording a CUDA graph, latency-bound serving loops, plug-ins whose
-host framework owns all device memory -- use sg_argmax_noalloc, whose only
+latency-bound serving loops that must not stall on an allocation, plug-ins
+whose host framework owns all device memory -- use sg_argmax_noalloc, whose only
 scratch is a statically sized device array shared by every call.  These
 tests call it through the C ABI on two gain vectors in a row (the second
 call sees the first call's leftover scratch) and compare with the seed and
