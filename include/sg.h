@@ -185,6 +185,31 @@ sg_status sg_set_snapshot_lists(int32_t enable);
  * later calls.  Errors: SG_EINVAL unless 0 or 1. */
 sg_status sg_set_forward_lists(int32_t enable);
 
+/* Direction-optimising switch of the level-synchronous walks (the forward
+ * dynamic update's walk from each new seed, its walk back over the seed's
+ * ancestors, the landmark walks of the initial gains, and sg_spread).  A
+ * top-down level expands every frontier node's arcs; a bottom-up level
+ * instead lets every node still missing some snapshot bits scan its arcs
+ * from the other side (in-arcs of a forward walk) for frontier nodes with
+ * live arcs, stopping once nothing is missing -- cheaper once the frontier
+ * is a large part of the graph (Beamer et al., SC 2012).
+ *   mode 0: top-down only; 1 (default): a level runs bottom-up when its
+ *   frontier holds more than n / divisor nodes (default divisor 4); 2:
+ *   every level after the first runs bottom-up (for testing).
+ * Results and the snapshot-edge counters do not depend on it.  Applies to
+ * later calls.  Errors: SG_EINVAL unless 0 <= mode <= 2 and divisor >= 1. */
+sg_status sg_set_direction(int32_t mode, int32_t divisor);
+
+/* Blocks per 64-snapshot word of the level-synchronous walks (the forward
+ * dynamic update's walk from each new seed and the landmark walks of the
+ * initial gains): each block owns 64/groups of the word's snapshot bits.
+ * 8, 16, 32 or 64 (default 8); more blocks spread one walk over more SMs.
+ * Workspaces size their level queues for max(8, groups) at creation (4
+ * bytes per node, word and block, twice); a query on an older workspace
+ * uses at most what it was sized for.  Results do not depend on it.
+ * Applies to later calls.  Errors: SG_EINVAL for any other value. */
+sg_status sg_set_walk_groups(int32_t groups);
+
 /* Live-mask cache: 1 makes each later query first evaluate every arc's coin
  * for all R snapshots once (the hash of Section 3.1's snapshot definition,
  * 64 snapshots per 64-bit word) into a per-workspace table of 2 x W x m

@@ -87,6 +87,7 @@ sg_status run_poison(const sg_graph *g, sg_workspace &ws, int32_t *seeds, long l
 int g_snapshot_lists = 1;
 int g_mask_cache = 0;
 int g_fwd_lists = 1;
+int g_walk_groups = 8;
 
 namespace {
 int g_heavy_min_deg = 2;
@@ -371,7 +372,6 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.cov, st);
     dbuf_free(ws.nbits, st);
     dbuf_free(ws.pendf, st);
-    dbuf_free(ws.du_m, st);
     dbuf_free(ws.fq_a, st);
     dbuf_free(ws.fq_b, st);
     dbuf_free(ws.du_x, st);
@@ -383,6 +383,7 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.tcnt, st);
     dbuf_free(ws.du_cnt, st);
     dbuf_free(ws.anc, st);
+    dbuf_free(ws.frw, st);
     dbuf_free(ws.anc_list, st);
     dbuf_free(ws.anc_cnt, st);
     dbuf_free(ws.lmk_rx, st);
@@ -563,13 +564,13 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
 {
     const size_t n = (size_t)g->n, nw = n * (size_t)W, W64 = (size_t)64 * W;
     size_t b = 8 * n;                                  // s
-    b += 8 * nw * 4;                                   // cov, nbits, pendf, du_m
-    b += 4 * nw * 8 * 2;                               // forward queues
+    b += 8 * nw * 4;                                   // cov, nbits, pendf, bottom-up frontier
+    b += 4 * nw * (size_t)std::max(8, g_walk_groups) * 2;  // forward queues
     b += 4 * nw;                                       // du_x
     b += 4 * (nw + W64 + 64) * 2;                      // task lists
     b += 4 * nw * 64;                                  // per-snapshot targets
     b += (8 + 8 + 4) * W64 + 4 * (size_t)W;            // offsets, counts
-    b += 8 * nw + 4 * nw + 4 * (size_t)W;              // ancestors
+    b += 8 * nw + (4 * nw + 4 * (size_t)W) * 8;        // ancestors, per (word, group) lists
     b += 2 * 8 * nw * 8 + (W64 << 8) * (4 + 4 + 8 + 8);  // landmarks
     int qcap = 1;
     while ((size_t)qcap < n) qcap <<= 1;
@@ -604,9 +605,10 @@ sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, 
         SG_TRY(dbuf_alloc(ws.cov, nw, st));
         SG_TRY(dbuf_alloc(ws.nbits, nw, st));
         SG_TRY(dbuf_alloc(ws.pendf, nw, st));
-        SG_TRY(dbuf_alloc(ws.du_m, nw, st));
-        SG_TRY(dbuf_alloc(ws.fq_a, nw * 8, st));  // one queue per (word, forward group)
-        SG_TRY(dbuf_alloc(ws.fq_b, nw * 8, st));
+        // one level queue per (word, walk group)
+        ws.fq_groups = std::max(8, g_walk_groups);
+        SG_TRY(dbuf_alloc(ws.fq_a, nw * (size_t)ws.fq_groups, st));
+        SG_TRY(dbuf_alloc(ws.fq_b, nw * (size_t)ws.fq_groups, st));
         SG_TRY(dbuf_alloc(ws.du_x, nw, st));
         const size_t ltasks = nw + (size_t)64 * W + 64;
         SG_TRY(dbuf_alloc(ws.list1, ltasks, st));
@@ -617,8 +619,9 @@ sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, 
         SG_TRY(dbuf_alloc(ws.tcnt, (size_t)64 * W, st));
         SG_TRY(dbuf_alloc(ws.du_cnt, (size_t)W, st));
         SG_TRY(dbuf_alloc(ws.anc, nw, st));
-        SG_TRY(dbuf_alloc(ws.anc_list, nw, st));
-        SG_TRY(dbuf_alloc(ws.anc_cnt, (size_t)W, st));
+        SG_TRY(dbuf_alloc(ws.frw, nw, st));
+        SG_TRY(dbuf_alloc(ws.anc_list, nw * 8, st));  // one list per (word, forward group)
+        SG_TRY(dbuf_alloc(ws.anc_cnt, (size_t)W * 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_rx, nw * 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_ux, nw * 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_U, ((size_t)64 * W) << 8, st));
@@ -629,6 +632,7 @@ sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, 
 
         SG_CUDA_TRY(cudaMemsetAsync(ws.nbits.p, 0, ws.nbits.bytes, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.pendf.p, 0, ws.pendf.bytes, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.frw.p, 0, ws.frw.bytes, st));
         // tier-3 slots: dense per-slot arrays (vis, pend, ring queue, touched), <= ~16 GiB in total
         int qcap = 1;
         while (qcap < n) qcap <<= 1;
@@ -833,6 +837,27 @@ sg_status sg_graph_trim(sg_graph *g)
     SG_CUDA_TRY(cudaDeviceSynchronize());
     free_workspace(g->ws, (cudaStream_t)0);
     SG_CUDA_TRY(cudaDeviceSynchronize());
+    return SG_OK;
+}
+
+sg_status sg_set_direction(int32_t mode, int32_t divisor)
+{
+    if (mode < 0 || mode > 2 || divisor < 1) {
+        set_error("direction mode must be 0, 1 or 2 and the divisor >= 1 (got %d, %d)", mode, divisor);
+        return SG_EINVAL;
+    }
+    g_bu_mode = mode;
+    g_bu_div = divisor;
+    return SG_OK;
+}
+
+sg_status sg_set_walk_groups(int32_t groups)
+{
+    if (groups != 8 && groups != 16 && groups != 32 && groups != 64) {
+        set_error("walk groups must be 8, 16, 32 or 64, got %d", groups);
+        return SG_EINVAL;
+    }
+    g_walk_groups = groups;
     return SG_OK;
 }
 
@@ -1090,6 +1115,7 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     ws.fl_on = 0;
     if (heavy_on) SG_TRY(ensure_fwd_lists(g, ws, co, c.p, model, st));
     SG_TRY(ensure_mask_cache(g, ws, co.W, st));
+    ws.walk_groups = std::min(g_walk_groups, ws.fq_groups);
     if (prepare_only) return SG_OK;
     // events: 0 start, 1 after index, 2 after init tier 1, 3 after init,
     // 4 end; per round: after forward update
@@ -1123,7 +1149,7 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.cov.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.anc.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
-    SG_CUDA_TRY(cudaMemsetAsync(ws.anc_cnt.p, 0, (size_t)co.W * 4, st));
+    SG_CUDA_TRY(cudaMemsetAsync(ws.anc_cnt.p, 0, (size_t)co.W * 8 * 4, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) {
         SG_TRY(run_heavy_index(g, ws, co, model, st));

@@ -19,7 +19,7 @@
 //                         reached from the seed set in snapshot 64w+b
 //   nbits uint64[W][n]    bits newly covered in the current round
 //   pendf uint64[W][n]    forward-DU frontier bits not yet expanded
-//   du_x / du_m [W][n]    newly covered (node, mask) list of the round, per word
+//   du_x [W][n]           nodes gaining coverage bits this round, per word
 //   tl    int32[W][64n]   newly covered nodes of the round, per snapshot,
 //                         minus those that reach the round's seed
 //   anc   uint64[W][n]    bit b: the node reaches the round's seed in snapshot 64w+b
@@ -198,15 +198,18 @@ struct sg_workspace {
     int64_t n = 0;
     int32_t wcap = 0;     // words of capacity of the [W][n] arrays
     int32_t nslots = 0;   // tier-3 (CTA engine) slots
+    int32_t fq_groups = 0;    // forward-walk blocks per word the queues fq_a/fq_b were sized for
+    int32_t walk_groups = 8;  // forward/landmark walk blocks per word for the current query
     sgi::DBuf<long long> s;
-    sgi::DBuf<unsigned long long> cov, nbits, pendf, du_m;
+    sgi::DBuf<unsigned long long> cov, nbits, pendf;
     sgi::DBuf<int32_t> fq_a, fq_b, du_x, list1, list2, tl;
     sgi::DBuf<long long> toff, coff;     // per snapshot: target list offset, chunk-task offset [64W+1]
     sgi::DBuf<int32_t> tcnt;             // per snapshot: newly covered count [64W]
     sgi::DBuf<int32_t> du_cnt;           // [W] entries per word
     sgi::DBuf<unsigned long long> anc;   // [W][n] ancestors of the round's seed, per snapshot bit
-    sgi::DBuf<int32_t> anc_list;         // [W][n] nodes with ancestor bits set
-    sgi::DBuf<int32_t> anc_cnt;          // [W]
+    sgi::DBuf<unsigned long long> frw;   // [W][n] bottom-up frontier bits of the walks (zero between levels)
+    sgi::DBuf<int32_t> anc_list;         // [W][8][n] nodes given ancestor bits, per (word, 8-bit group)
+    sgi::DBuf<int32_t> anc_cnt;          // [W][8]
     sgi::DBuf<unsigned long long> lmk_rx;    // [W][n][8] landmark reach bits (R(x_i) membership)
     sgi::DBuf<unsigned long long> lmk_ux;    // [W][n][8] ... and which landmarks the node reaches
     sgi::DBuf<int32_t> lmk_U, lmk_H;         // [64W << K] union sizes / membership histogram
@@ -295,6 +298,14 @@ extern thread_local int g_launches;
 extern int g_tier_limit[2];
 // landmark nodes used for the initial gains (0 .. 8)
 extern int g_landmarks;
+// blocks per 64-snapshot word of the level-synchronous forward and landmark
+// walks (8, 16, 32 or 64; each owns 64/groups snapshot bits)
+extern int g_walk_groups;
+// direction-optimising switch of the level-synchronous walks: mode 0
+// top-down only, 1 bottom-up once a level's frontier holds more than
+// n / g_bu_div nodes, 2 bottom-up from the second level on
+extern int g_bu_mode;
+extern int g_bu_div;
 // polls a bounded device-side wait of the traversal engines makes before it
 // gives up (default 2^22; a testing hook can shorten it)
 extern long long g_wait_polls;

@@ -317,6 +317,8 @@ struct EngineArgs {
     long long ntasks;       // TASK_INIT: n * W
     int limit;              // keys a warp table may hold before the task moves up a tier
     long long spin;         // polls a bounded wait makes before it gives up
+    int bu_mode;            // level-synchronous walks: 0 top-down only, 1 switch by frontier size, 2 bottom-up after level 0
+    int bu_div;             // mode 1: a level runs bottom-up when its frontier holds more than n / bu_div nodes
 };
 
 
@@ -630,14 +632,18 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         if (!ovf) {
             const int u = T.key[h];
             if (TASK == TASK_INIT) {
-                // bits recorded before the task reached the landmark in that
-                // snapshot are credited by the landmark instead
                 const uint64_t v = T.vis[h];
-                const uint64_t ve = lmk_effective(a, word, u, v, xb);
-                cnt += __popcll(ve);
-                if (ve != v)
-                    tedges -= (unsigned long long)__popcll(v & ~ve) *
-                              (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
+                if (u != x0) {
+                    cnt += __popcll(v);  // arrivals passed the landmark filter
+                } else {
+                    // the source's seeded bits inside a credited landmark
+                    // set are credited by the landmark instead
+                    const uint64_t ve = lmk_effective(a, word, u, v, xb);
+                    cnt += __popcll(ve);
+                    if (ve != v)
+                        tedges -= (unsigned long long)__popcll(v & ~ve) *
+                                  (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
+                }
             } else {
                 const int c = __popcll(T.vis[h]);
                 atomicAdd((unsigned long long *)&a.s[u], (unsigned long long)(-(long long)c));
@@ -788,7 +794,88 @@ struct CtaState {
     unsigned long long gm;      // snapshot bits this block owns (several blocks may share a word)
     long long *cnt_out;               // TASK_SPREAD: reached (node, snapshot) pairs are added here
     unsigned long long *edges_out;    // TASK_SPREAD: snapshot-edge count
+    unsigned long long *fr = nullptr;  // bottom-up levels: the level's frontier bits per node (zero between
+                                       // levels; shared by the word's blocks, bit-disjoint); NULL: top-down only
 };
+
+// Bottom-up level of a level-synchronous walk (direction-optimising BFS,
+// Beamer, Asanovic and Patterson, SC 2012), bit-sliced: the frontier's state
+// bits go into w.fr; then every node y still missing some of the block's
+// snapshot bits scans its arcs from the walk's other side (in-arcs of a
+// forward walk, out-arcs of a reverse walk) and takes
+//     new(y) = OR over arcs e = (x, y) of (fr[x] & live(e)) & ~vis(y),
+// stopping once no bit is missing.  The same set of (node, bit) pairs is
+// reached as by a top-down level; the snapshot-edge counters count the
+// frontier's expansions as a top-down level would.
+template <int DIR, int MODEL, int TASK, size_t VS>
+__device__ void bu_level(const EngineArgs &a, const CtaState &w, int word, uint32_t rs, int L, const int32_t *cur,
+                         int32_t *nxt, long long &cnt, unsigned long long &edges, CtaShared &S)
+{
+    constexpr int BDIR = DIR == DIR_FWD ? DIR_REV : DIR_FWD;
+    const GraphView &g = a.g;
+    const Coins &co = a.co;
+    const int tid = threadIdx.x;
+    const unsigned long long *lm = BDIR == DIR_FWD ? g.lm_out : g.lm_in;
+    for (int i = tid; i < L; i += BT) {
+        const int x = cur[i];
+        const uint64_t F = w.gm == ~0ull ? atomicExch(&w.pend[x], 0ull) : (atomicAnd(&w.pend[x], ~w.gm) & w.gm);
+        if (!F) continue;
+        atomicOr(&w.fr[x], (unsigned long long)F);
+        if (TASK == TASK_FWD || TASK == TASK_SPREAD)
+            edges += (unsigned long long)__popcll(F) * (unsigned long long)(__ldg(g.rp + x + 1) - __ldg(g.rp + x));
+    }
+    __syncthreads();
+    const uint64_t wm = word_mask(word, co.R) & w.gm;
+    for (long long yl = tid; yl < g.n; yl += BT) {
+        const int y = (int)yl;
+        uint64_t miss = ~*(volatile unsigned long long *)&w.vis[(size_t)y * VS] & wm;
+        if (!miss) continue;
+        const Row rr = row_ref<BDIR, MODEL, SLICE_SNAP>(g, co, y, word, rs);
+        uint64_t acc = 0;
+        for (int j = 0; j < rr.vdeg && miss; ++j) {
+            const long long q = rr.base + j;
+            int x;
+            uint64_t mk = ~0ull;
+            uint32_t eid = 0, tm1 = 0;
+            bool hashed = false;
+            if (rr.heavy) {
+                const HeavyView &hv = BDIR == DIR_FWD ? g.hout : g.hin;
+                x = __ldg(hv.hnbr + q);
+                mk = __ldg(hv.hmask + q);
+            } else if (lm) {
+                x = BDIR == DIR_FWD ? __ldg(g.col + q) : __ldg(&g.cin[q].x);
+                mk = __ldg(lm + (long long)(rs >> 6) * g.m + q);
+            } else {
+                arc_at<BDIR, MODEL>(g, (int)q, rr.rtm1, x, eid, tm1);
+                hashed = true;
+            }
+            uint64_t f = *(volatile unsigned long long *)&w.fr[x] & miss & mk;
+            if (!f) continue;
+            if (hashed) f = live_bits(co, eid, rs, f, tm1);
+            acc |= f;
+            miss &= ~f;
+        }
+        if (!acc) continue;
+        const uint64_t old = atomicOr(&w.vis[(size_t)y * VS], (unsigned long long)acc);
+        const uint64_t nw = acc & ~old;
+        if (!nw) continue;
+        if (TASK == TASK_SPREAD) cnt += __popcll(nw);
+        if (TASK == TASK_ANC && (old & w.gm) == 0) w.touched[atomicAdd(&S.ntouch, 1)] = y;
+        if ((TASK == TASK_FWD || TASK == TASK_LMK) && w.du_x) {
+            const uint64_t ob = atomicOr(&w.nbits[y], (unsigned long long)nw);
+            if (ob == 0) w.du_x[atomicAdd(w.ndu, 1)] = y;
+        }
+        const uint64_t op = atomicOr(&w.pend[y], (unsigned long long)nw);
+        if ((op & w.gm) == 0) nxt[atomicAdd(&S.qnext, 1)] = y;
+    }
+    __syncthreads();
+    for (int i = tid; i < L; i += BT) {
+        const int x = cur[i];
+        if (w.gm == ~0ull) w.fr[x] = 0;
+        else atomicAnd(&w.fr[x], ~w.gm);
+    }
+    __syncthreads();
+}
 
 // One traversal by the whole block over dense arrays, level-synchronous.
 // TASK_INIT / TASK_REVT: vis/pend are a zeroed slot and are zero again on
@@ -853,6 +940,17 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                 S.qlen = 1;
                 if (w.du_x && atomicOr(&w.nbits[x0], (unsigned long long)M) == 0) w.du_x[atomicAdd(w.ndu, 1)] = x0;
             }
+        } else if (TASK == TASK_ANC) {
+            // the word's groups walk their own bits of the shared words
+            M &= w.gm;
+            if (M) {
+                atomicOr(&w.vis[x0], (unsigned long long)M);
+                atomicOr(&w.pend[x0], (unsigned long long)M);
+                w.qa[0] = x0;
+                S.qlen = 1;
+                w.touched[0] = x0;
+                S.ntouch = 1;
+            }
         } else if (M) {
             w.vis[x0] |= M;
             w.pend[x0] = M;
@@ -870,9 +968,28 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
     const bool flists = DIR == DIR_FWD && (TASK == TASK_FWD || TASK == TASK_LMK || TASK == TASK_SPREAD) && g.fsoff &&
                         __ldg(g.fsvalid);
     __syncthreads();
+    int level = 0;
     while (true) {
         const int L = S.qlen;
         if (L == 0) break;
+        // Direction-optimising step: once the frontier is a large part of
+        // the graph, a level is cheaper pulled from the unreached side.
+        constexpr bool CAN_BU = TASK == TASK_FWD || TASK == TASK_LMK || TASK == TASK_SPREAD || TASK == TASK_ANC;
+        const bool bu = CAN_BU && w.fr && level > 0 &&
+                        (a.bu_mode == 2 || (a.bu_mode == 1 && (long long)L * a.bu_div > (long long)g.n));
+        ++level;
+        if (bu) {
+            bu_level<DIR, MODEL, TASK, VS>(a, w, word, rs, L, cur, nxt, cnt, edges, S);
+            if (tid == 0) {
+                S.qlen = S.qnext;
+                S.qnext = 0;
+            }
+            int32_t *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+            __syncthreads();
+            continue;
+        }
         for (int cbase = 0; cbase < L; cbase += BT) {
             const int i = cbase + tid;
             int vd = 0;
@@ -923,7 +1040,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
                         const uint64_t nw = ml & ~old;
                         if (nw) {
                             if (TASK == TASK_INIT || TASK == TASK_SPREAD) cnt += __popcll(nw);
-                            if (TASK != TASK_FWD && TASK != TASK_LMK && TASK != TASK_SPREAD && old == 0)
+                            if (TASK != TASK_FWD && TASK != TASK_LMK && TASK != TASK_SPREAD && (old & w.gm) == 0)
                                 w.touched[atomicAdd(&S.ntouch, 1)] = y;
                             if ((TASK == TASK_FWD || TASK == TASK_LMK) && w.du_x) {
                                 const uint64_t ob = atomicOr(&w.nbits[y], (unsigned long long)nw);
@@ -961,7 +1078,7 @@ __device__ void cta_bfs(const EngineArgs &a, CtaState w, int x0, uint64_t M0, in
         const int nt = S.ntouch;
         for (int i = tid; i < nt; i += BT) {
             const int y = w.touched[i];
-            uint64_t b = w.vis[y];
+            uint64_t b = w.vis[y] & w.gm;
             long long d = 0;
             while (b) {
                 const int k = __ffsll((long long)b) - 1;
@@ -1164,7 +1281,7 @@ __device__ __forceinline__ void coop_seed(CoopTab<TAB, LOGC> &T, CoopCtl &c, int
 template <int TAB, int DIR, int MODEL, int TASK, int LOGC>
 __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, CoopTab<TAB, LOGC> &T, CoopCtl &c, int word,
                                                           uint32_t rs, int limit, unsigned long long &elems,
-                                                          unsigned long long &lel)
+                                                          unsigned long long &lel, long long &acnt)
 {
     constexpr int SLICE = TASK == TASK_REVT ? SLICE_TGT : SLICE_SNAP;
     const GraphView &g = a.g;
@@ -1290,6 +1407,8 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                         const uint64_t old = atomicOr(&T.visr(idx), (unsigned long long)ml);
                         const uint64_t nw = ml & ~old;
                         if (nw) {
+                            // initial gains count (node, snapshot) pairs as they are first reached
+                            if (TASK == TASK_INIT) acnt += __popcll(nw);
                             if (TAB == TAB_DENSE && old == 0) T.note_new(y, c);
                             const uint64_t oldp = atomicOr(&T.pendr(idx), (unsigned long long)nw);
                             if (oldp == 0) T.put(atomicAdd(&c.tail, 1), idx);
@@ -1393,26 +1512,34 @@ __global__ void __launch_bounds__(CoopShape<TAB, LOGC>::T, CoopShape<TAB, LOGC>:
             if (tid < cnt) coop_seed<TAB, LOGC>(T, c, a.tl[b0 + tid], 1ull << tid, limit);
         }
         __syncthreads();
-        unsigned long long tedges = coop_expand<TAB, DIR, MODEL, TASK, LOGC>(a, T, c, word, rs, limit, wk_elems, lel);
+        long long cnt = 0;
+        unsigned long long tedges =
+            coop_expand<TAB, DIR, MODEL, TASK, LOGC>(a, T, c, word, rs, limit, wk_elems, lel, cnt);
         __syncthreads();
         const int ovf = c.overflow | c.err;
         const int nt = c.nkeys;
         uint64_t xb[MAX_LMK];
 #pragma unroll
         for (int i = 0; i < MAX_LMK; ++i) xb[i] = (TASK == TASK_INIT && i < a.lmk_k) ? c.xbits[i] : 0ull;
-        long long cnt = 0;
+        if (TASK == TASK_INIT && tid == 0 && !ovf) {
+            // Every bit recorded by an arrival passed the landmark filter and
+            // was counted then; only the source's own seeded bits can lie in
+            // a credited landmark set (x0 in R(G'_r, x_i) for a reached x_i):
+            // those are credited by the landmark instead.
+            const uint64_t M0 = word_mask(word, a.co.R);
+            const uint64_t ve = lmk_effective(a, word, x0, M0, xb);
+            cnt += __popcll(ve);
+            if (ve != M0)
+                tedges -= (unsigned long long)__popcll(M0 & ~ve) *
+                          (unsigned long long)(__ldg(g.rp + x0 + 1) - __ldg(g.rp + x0));
+        }
         unsigned long long redges = 0;
         for (int i = tid; i < nt; i += CO_T) {
             const int idx = T.touched_at(i);
             if (!ovf) {
                 const int u = T.node(idx);
                 if (TASK == TASK_INIT) {
-                    const uint64_t v = T.visr(idx);
-                    const uint64_t ve = lmk_effective(a, word, u, v, xb);
-                    cnt += __popcll(ve);
-                    if (ve != v)
-                        tedges -= (unsigned long long)__popcll(v & ~ve) *
-                                  (unsigned long long)(__ldg(g.rp + u + 1) - __ldg(g.rp + u));
+                    // counted on arrival; the slot only needs clearing
                 } else {
                     const int cc = __popcll(T.visr(idx));
                     atomicAdd((unsigned long long *)&a.s[u], (unsigned long long)(-(long long)cc));
@@ -1480,11 +1607,13 @@ size_t coop_hash_smem(int logc) { return (size_t)(1 << logc) * 24; }
 // ========================================================== forward DU
 
 struct FwdArgs {
-    unsigned long long *cov, *nbits, *pendf, *du_m, *anc;
+    unsigned long long *cov, *nbits, *pendf, *anc;
     int32_t *fq_a, *fq_b, *du_x, *du_cnt, *tl, *anc_list, *anc_cnt;
     long long *toff, *coff;
     int32_t *tcnt;
     long long tcap;  // per-word capacity of tl
+    int groups;      // blocks per word of the forward walk (8, 16, 32 or 64)
+    unsigned long long *frw;  // [W][n] bottom-up frontier bits (zero between levels)
 };
 
 constexpr int FWD_GROUPS = 8;  // blocks per 64-snapshot word in the forward walk
@@ -1499,11 +1628,11 @@ __global__ void __launch_bounds__(BT) fwd_walk_kernel(EngineArgs a, FwdArgs f)
 {
     __shared__ CtaShared S;
     const int n = a.g.n;
-    const int word = blockIdx.x / FWD_GROUPS;
-    const int grp = blockIdx.x - word * FWD_GROUPS;
+    const int word = blockIdx.x / f.groups;
+    const int grp = blockIdx.x - word * f.groups;
     const int vstar = *(volatile int32_t *)&a.ctl->vstar;
     if (vstar < 0) return;
-    constexpr int GB = 64 / FWD_GROUPS;
+    const int GB = 64 / f.groups;
     const size_t so = (size_t)word * (size_t)n;
     const size_t qo = (size_t)blockIdx.x * (size_t)n;
     CtaState w;
@@ -1516,115 +1645,135 @@ __global__ void __launch_bounds__(BT) fwd_walk_kernel(EngineArgs a, FwdArgs f)
     w.du_x = f.du_x + so;
     w.ndu = f.du_cnt + word;
     w.gm = (GB == 64 ? ~0ull : ((1ull << GB) - 1ull)) << (grp * GB);
+    w.fr = f.frw ? f.frw + so : nullptr;
     cta_bfs<DIR_FWD, MODEL, TASK_FWD>(a, w, vstar, word_mask(word, a.co.R), word, (uint32_t)word * 64u, nullptr, 0,
                                       nullptr, S);
 }
 
-// Forward DU, per word after the walk:
-//  1. |N_r| for the word's snapshots;
-//  2. walk back from v* over live in-arcs: every u reaching v* in snapshot
-//     r reaches all of N_r (N_r lies inside R(G'_r, v*)), so s_u drops by
-//     |N_r| at once; these ancestors are marked so that
-//  3. the per-snapshot lists of the remaining targets (N_r minus the
-//     ancestors) feed the target-sliced reverse tasks, which never enter a
-//     marked node (a path through one would make its start an ancestor).
-// The last block to finish turns the per-snapshot counts into the offsets
-// of the reverse tasks.
+// Forward DU after the walk, in three launches over (word, group) blocks,
+// group g owning snapshot bits 8g..8g+7 of the word (bit-disjoint atomics on
+// the shared words, as in the walk):
+//  fwd_anc_kernel    clears the group's bits of the previous round's
+//                    ancestor marks; |N_r| for its snapshots; then walks back
+//                    from v* over live in-arcs: every u reaching v* in
+//                    snapshot r reaches all of N_r (N_r lies inside
+//                    R(G'_r, v*)), so s_u drops by |N_r| at once, and u is
+//                    marked an ancestor;
+//  fwd_lists_kernel  per-snapshot lists of the remaining targets (N_r minus
+//                    the ancestors), one fixed region of n entries per
+//                    snapshot, for the target-sliced reverse tasks, which
+//                    never enter a marked node (a path through one would make
+//                    its start an ancestor); the last block turns the counts
+//                    into the reverse tasks' offsets;
+//  fwd_clear_kernel  clears the round's new-bit words.
+constexpr int FPB = 64 / FWD_GROUPS;  // snapshot bits per group
+
+__device__ __forceinline__ uint64_t group_mask(int grp)
+{
+    return (FPB == 64 ? ~0ull : ((1ull << FPB) - 1ull)) << (grp * FPB);
+}
+
 template <int MODEL>
-__global__ void __launch_bounds__(BT) fwd_post_kernel(EngineArgs a, FwdArgs f)
+__global__ void __launch_bounds__(BT) fwd_anc_kernel(EngineArgs a, FwdArgs f)
 {
     __shared__ CtaShared S;
-    __shared__ int sh_last;
-    __shared__ unsigned long long sh_mv;
     const int n = a.g.n;
-    const int word = blockIdx.x;
-    const int tid = threadIdx.x;
-    Ctl *ctl = a.ctl;
-    const int vstar = *(volatile int32_t *)&ctl->vstar;
+    const int word = blockIdx.x / FWD_GROUPS;
+    const int grp = blockIdx.x - word * FWD_GROUPS;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint64_t gm = group_mask(grp);
+    const int vstar = *(volatile int32_t *)&a.ctl->vstar;
     const size_t so = (size_t)word * (size_t)n;
     unsigned long long *ancw = f.anc + so;
-    int32_t *anclw = f.anc_list + so;
-    // the previous round's ancestor marks of this word
+    int32_t *anclw = f.anc_list + (size_t)blockIdx.x * (size_t)n;
     {
-        const int na = f.anc_cnt[word];
-        for (int i = tid; i < na; i += BT) ancw[anclw[i]] = 0;
+        // this group's bits of the previous round's marks (other groups
+        // clear theirs of the same words at the same time)
+        const int na = f.anc_cnt[blockIdx.x];
+        for (int i = tid; i < na; i += BT) atomicAnd(&ancw[anclw[i]], ~gm);
     }
-    if (tid == 0) sh_mv = vstar >= 0 ? f.nbits[so + vstar] : 0ull;  // bits v* newly covers
+    if (tid < 64) S.boff[tid] = 0;
     __syncthreads();
     const int nd = vstar >= 0 ? *(volatile int32_t *)&f.du_cnt[word] : 0;
-    int32_t *dux = f.du_x + so;
-    unsigned long long *dum = f.du_m + so;
-    unsigned long long *nb = f.nbits + so;
-    if (tid < 64) {
-        S.bcnt[tid] = 0;
-        S.bcur[tid] = 0;
+    const int32_t *dux = f.du_x + so;
+    const unsigned long long *nb = f.nbits + so;
+    // |N_r| for the group's snapshots: ballots over 32 entries at a time
+    int c[FPB];
+#pragma unroll
+    for (int j = 0; j < FPB; ++j) c[j] = 0;
+    for (int base = (tid >> 5) * 32; base < nd; base += BT) {
+        const int i = base + lane;
+        const uint64_t M = i < nd ? (__ldg(nb + dux[i]) & gm) >> (grp * FPB) : 0ull;
+#pragma unroll
+        for (int j = 0; j < FPB; ++j) c[j] += __popc(__ballot_sync(FULL, (M >> j) & 1ull));
     }
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < FPB; ++j)
+            if (c[j]) atomicAdd(&S.boff[grp * FPB + j], c[j]);
     __syncthreads();
-    // |N_r| for the 64 snapshots of the word
-    for (int i = tid; i < nd; i += BT) {
-        const int y = dux[i];
-        uint64_t M = nb[y];
-        nb[y] = 0;
-        dum[i] = M;
-        while (M) {
-            const int b = __ffsll((long long)M) - 1;
-            M &= M - 1;
-            atomicAdd(&S.bcnt[b], 1);
-        }
-    }
-    __syncthreads();
-    if (tid < 64) S.boff[tid] = S.bcnt[tid];  // keep |N_r| while bcnt is reused
-    __syncthreads();
-    // ancestors of v* over the snapshots where v* newly covers nodes
+    const uint64_t mv = vstar >= 0 ? nb[vstar] & gm : 0ull;  // bits v* newly covers
     int nanc = 0;
-    if (sh_mv) {
+    if (mv) {
         CtaState w;
         w.vis = ancw;
         w.pend = f.pendf + so;
-        w.qa = f.fq_a + (size_t)word * FWD_GROUPS * (size_t)n;
-        w.qb = f.fq_b + (size_t)word * FWD_GROUPS * (size_t)n;
+        w.qa = f.fq_a + (size_t)blockIdx.x * (size_t)n;
+        w.qb = f.fq_b + (size_t)blockIdx.x * (size_t)n;
         w.touched = anclw;
         w.nbits = nullptr;
         w.du_x = nullptr;
         w.ndu = nullptr;
-        w.gm = ~0ull;
-        cta_bfs<DIR_REV, MODEL, TASK_ANC>(a, w, vstar, sh_mv, word, (uint32_t)word * 64u, nullptr, 0, S.boff, S);
+        w.gm = gm;
+        w.fr = f.frw ? f.frw + so : nullptr;
+        cta_bfs<DIR_REV, MODEL, TASK_ANC>(a, w, vstar, mv, word, (uint32_t)word * 64u, nullptr, 0, S.boff, S);
         nanc = S.ntouch;
     }
-    if (tid == 0) f.anc_cnt[word] = nanc;
-    // per-snapshot target lists: newly covered nodes that are not ancestors
-    if (tid < 64) S.bcnt[tid] = 0;
+    if (tid == 0) f.anc_cnt[blockIdx.x] = nanc;
+}
+
+__global__ void __launch_bounds__(BT) fwd_lists_kernel(FwdArgs f, Ctl *ctl, int n)
+{
+    __shared__ CtaShared S;
+    __shared__ int sh_last;
+    __shared__ int cnt[FPB];
+    const int word = blockIdx.x / FWD_GROUPS;
+    const int grp = blockIdx.x - word * FWD_GROUPS;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint64_t gm = group_mask(grp);
+    const int vstar = *(volatile int32_t *)&ctl->vstar;
+    const size_t so = (size_t)word * (size_t)n;
+    if (tid < FPB) cnt[tid] = 0;
     __syncthreads();
-    for (int i = tid; i < nd; i += BT) {
-        uint64_t M = dum[i] & ~ancw[dux[i]];
-        while (M) {
-            const int b = __ffsll((long long)M) - 1;
-            M &= M - 1;
-            atomicAdd(&S.bcnt[b], 1);
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int b = 0; b < 64; ++b) {
-            S.boff[b] = acc;
-            acc += S.bcnt[b];
-        }
-    }
-    __syncthreads();
-    if (tid < 64) {
-        f.toff[64 * word + tid] = (long long)word * f.tcap + S.boff[tid];
-        f.tcnt[64 * word + tid] = S.bcnt[tid];
-    }
+    const int nd = vstar >= 0 ? *(volatile int32_t *)&f.du_cnt[word] : 0;
+    const int32_t *dux = f.du_x + so;
+    const unsigned long long *nb = f.nbits + so, *ancw = f.anc + so;
     int32_t *tlw = f.tl + (size_t)word * (size_t)f.tcap;
-    for (int i = tid; i < nd; i += BT) {
-        const int y = dux[i];
-        uint64_t M = dum[i] & ~ancw[y];
-        while (M) {
-            const int b = __ffsll((long long)M) - 1;
-            M &= M - 1;
-            tlw[S.boff[b] + atomicAdd(&S.bcur[b], 1)] = y;
+    const unsigned lt = (1u << lane) - 1u;
+    // whole warps take 32 entries at a time (every lane joins the ballots)
+    for (int base = (tid >> 5) * 32; base < nd; base += BT) {
+        const int i = base + lane;
+        int y = 0;
+        uint64_t T = 0;
+        if (i < nd) {
+            y = dux[i];
+            T = ((nb[y] & ~ancw[y]) & gm) >> (grp * FPB);
         }
+#pragma unroll
+        for (int j = 0; j < FPB; ++j) {
+            const unsigned bal = __ballot_sync(FULL, (T >> j) & 1ull);
+            if (!bal) continue;
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(&cnt[j], __popc(bal));
+            pos = __shfl_sync(FULL, pos, 0);
+            if ((T >> j) & 1ull) tlw[(size_t)(grp * FPB + j) * (size_t)n + pos + __popc(bal & lt)] = y;
+        }
+    }
+    __syncthreads();
+    if (tid < FPB) {
+        const int b = grp * FPB + tid;
+        f.toff[64 * word + b] = (long long)word * f.tcap + (long long)b * n;
+        f.tcnt[64 * word + b] = cnt[tid];
     }
     if (tid == 0) {
         __threadfence();
@@ -1635,7 +1784,8 @@ __global__ void __launch_bounds__(BT) fwd_post_kernel(EngineArgs a, FwdArgs f)
     if (!sh_last) return;
     __threadfence();
     // last block: chunk-task offsets over every snapshot
-    const int NS = 64 * gridDim.x;
+    const int W = gridDim.x / FWD_GROUPS;
+    const int NS = 64 * W;
     long long carry = 0;
     for (int base = 0; base < NS; base += BT) {
         const int i = base + tid;
@@ -1647,7 +1797,7 @@ __global__ void __launch_bounds__(BT) fwd_post_kernel(EngineArgs a, FwdArgs f)
         __syncthreads();
     }
     long long entries = 0;
-    for (int i = tid; i < (int)gridDim.x; i += BT) entries += *(volatile int32_t *)&f.du_cnt[i];
+    for (int i = tid; i < W; i += BT) entries += *(volatile int32_t *)&f.du_cnt[i];
     entries = block_sum(entries, S.red_ll);
     if (tid == 0) {
         f.coff[NS] = carry;
@@ -1655,6 +1805,20 @@ __global__ void __launch_bounds__(BT) fwd_post_kernel(EngineArgs a, FwdArgs f)
         ctl->rev_tasks += (unsigned long long)carry;
         ctl->du_entries += (unsigned long long)entries;
         ctl->fwd_arrivals = 0;
+    }
+}
+
+// The round's new-bit words back to zero (the next walk lists a node when
+// its word goes from zero to nonzero).
+__global__ void __launch_bounds__(256) fwd_clear_kernel(FwdArgs f, Ctl *ctl, int n, int W)
+{
+    if (*(volatile int32_t *)&ctl->vstar < 0) return;
+    for (int word = 0; word < W; ++word) {
+        const int nd = *(volatile int32_t *)&f.du_cnt[word];
+        const size_t so = (size_t)word * (size_t)n;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nd;
+             i += (long long)gridDim.x * blockDim.x)
+            f.nbits[so + f.du_x[so + i]] = 0;
     }
 }
 
@@ -1667,6 +1831,8 @@ __global__ void __launch_bounds__(BT) fwd_post_kernel(EngineArgs a, FwdArgs f)
 struct LmkArgs {
     unsigned long long *rx, *ux, *pendf, *E, *HE;
     int32_t *fq_a, *fq_b, *U, *H;
+    int groups;  // blocks per word (8, 16, 32 or 64)
+    unsigned long long *frw;  // [W][n] bottom-up frontier bits (zero between levels)
 };
 
 template <int DIR, int MODEL>
@@ -1674,9 +1840,9 @@ __global__ void __launch_bounds__(BT) landmark_walk_kernel(EngineArgs a, LmkArgs
 {
     __shared__ CtaShared S;
     const int n = a.g.n;
-    const int word = blockIdx.x / FWD_GROUPS;
-    const int grp = blockIdx.x - word * FWD_GROUPS;
-    constexpr int GB = 64 / FWD_GROUPS;
+    const int word = blockIdx.x / l.groups;
+    const int grp = blockIdx.x - word * l.groups;
+    const int GB = 64 / l.groups;
     const size_t qo = (size_t)blockIdx.x * (size_t)n;
     CtaState w;
     w.vis = (DIR == DIR_FWD ? l.rx : l.ux) + (((size_t)word * (size_t)n) << 3) + i;
@@ -1688,6 +1854,7 @@ __global__ void __launch_bounds__(BT) landmark_walk_kernel(EngineArgs a, LmkArgs
     w.du_x = nullptr;
     w.ndu = nullptr;
     w.gm = (GB == 64 ? ~0ull : ((1ull << GB) - 1ull)) << (grp * GB);
+    w.fr = l.frw ? l.frw + (size_t)word * (size_t)n : nullptr;
     // In a snapshot where x_i and an earlier landmark x_j reach each other
     // (one strongly connected component), R(x_i) = R(x_j) and U(x_i) =
     // U(x_j): copy those bits of word j instead of walking them.
@@ -1723,6 +1890,7 @@ struct SpreadArgs {
     int groups;                      // 1, 2, 4 or 8
     long long *total;
     unsigned long long *edges;
+    unsigned long long *fr;          // [words][n] bottom-up frontier bits, zero on entry (NULL: top-down only)
 };
 
 template <int MODEL>
@@ -1745,6 +1913,7 @@ __global__ void __launch_bounds__(BT) spread_kernel(EngineArgs a, SpreadArgs sp)
     w.gm = gb == 64 ? ~0ull : (((1ull << gb) - 1ull) << (grp * gb));
     w.cnt_out = sp.total;
     w.edges_out = sp.edges;
+    w.fr = sp.fr ? sp.fr + (size_t)wi * n : nullptr;
     cta_bfs<DIR_FWD, MODEL, TASK_SPREAD>(a, w, -1, word_mask(word, a.co.R) & w.gm, word, (uint32_t)word * 64u, sp.S,
                                          sp.ns, nullptr, S);
 }
@@ -2203,6 +2372,8 @@ EngineArgs engine_args(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
     a.ntasks = 0;
     a.limit = 1;
     a.spin = g_wait_polls;
+    a.bu_mode = g_bu_mode;
+    a.bu_div = g_bu_div;
     return a;
 }
 
@@ -2315,10 +2486,12 @@ sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
         l.E = ws.lmk_E.p;
         l.H = ws.lmk_H.p;
         l.HE = ws.lmk_HE.p;
+        l.groups = ws.walk_groups;
+        l.frw = ws.frw.p;
         for (int i = 0; i < K; ++i) {
-            landmark_walk_kernel<DIR_FWD, MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, l, i);
+            landmark_walk_kernel<DIR_FWD, MODEL><<<co.W * l.groups, BT, 0, st>>>(a, l, i);
             SG_CUDA_TRY(cudaGetLastError());
-            landmark_walk_kernel<DIR_REV, MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, l, i);
+            landmark_walk_kernel<DIR_REV, MODEL><<<co.W * l.groups, BT, 0, st>>>(a, l, i);
             SG_CUDA_TRY(cudaGetLastError());
         }
         const size_t nq = ((size_t)64 * co.W) << K;
@@ -2356,7 +2529,6 @@ sg_status round_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy_on, 
     f.cov = ws.cov.p;
     f.nbits = ws.nbits.p;
     f.pendf = ws.pendf.p;
-    f.du_m = ws.du_m.p;
     f.fq_a = ws.fq_a.p;
     f.fq_b = ws.fq_b.p;
     f.du_x = ws.du_x.p;
@@ -2369,11 +2541,17 @@ sg_status round_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy_on, 
     f.anc = ws.anc.p;
     f.anc_list = ws.anc_list.p;
     f.anc_cnt = ws.anc_cnt.p;
-    fwd_walk_kernel<MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, f);
+    f.groups = ws.walk_groups;
+    f.frw = ws.frw.p;
+    fwd_walk_kernel<MODEL><<<co.W * f.groups, BT, 0, st>>>(a, f);
     SG_CUDA_TRY(cudaGetLastError());
-    fwd_post_kernel<MODEL><<<co.W, BT, 0, st>>>(a, f);
+    fwd_anc_kernel<MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, f);
     SG_CUDA_TRY(cudaGetLastError());
-    g_launches += 2;
+    fwd_lists_kernel<<<co.W * FWD_GROUPS, BT, 0, st>>>(f, ws.ctl.p, (int)g->n);
+    SG_CUDA_TRY(cudaGetLastError());
+    fwd_clear_kernel<<<g->num_sms * 2, 256, 0, st>>>(f, ws.ctl.p, (int)g->n, co.W);
+    SG_CUDA_TRY(cudaGetLastError());
+    g_launches += 4;
     if (after_fwd) SG_CUDA_TRY(cudaEventRecord(after_fwd, st));
     return launch_tiers<DIR_REV, MODEL, TASK_REVT>(g, ws, a, st, nullptr);
 }
@@ -2382,6 +2560,8 @@ sg_status round_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy_on, 
 
 thread_local int g_launches = 0;
 long long g_wait_polls = WAIT_POLLS_DEFAULT;
+int g_bu_mode = 1;
+int g_bu_div = 4;
 int g_tier_limit[2] = {(1 << T1_LOGC) / 2, (1 << CO_LOGC) / 2};
 int g_landmarks = 8;
 
@@ -2429,21 +2609,29 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
     const size_t n = (size_t)g->n;
     // words per launch: dense vis/pend (8 B each) and two level queues (4 B
     // each) per node and word, within 4 GiB
-    const size_t per_word = n * 24;
+    const size_t per_word = n * 32;
     const int wc = (int)std::max<size_t>(1, std::min<size_t>((size_t)co.W, ((size_t)4 << 30) / per_word));
-    DBuf<unsigned long long> vis, pend;
+    DBuf<unsigned long long> vis, pend, fr;
     DBuf<int32_t> qa, qb;
     sg_status rc = SG_OK;
     if ((rc = dbuf_alloc(vis, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(pend, (size_t)wc * n, st)) != SG_OK ||
-        (rc = dbuf_alloc(qa, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(qb, (size_t)wc * n, st)) != SG_OK) {
+        (rc = dbuf_alloc(qa, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(qb, (size_t)wc * n, st)) != SG_OK ||
+        (rc = dbuf_alloc(fr, (size_t)wc * n, st)) != SG_OK) {
         dbuf_free(vis, st);
         dbuf_free(pend, st);
         dbuf_free(qa, st);
         dbuf_free(qb, st);
+        dbuf_free(fr, st);
         return rc;
+    }
+    if (cudaMemsetAsync(fr.p, 0, (size_t)wc * n * 8, st) != cudaSuccess) {
+        set_error("sg_spread: memset failed");
+        rc = SG_ECUDA;
     }
     EngineArgs a{};
     a.spin = g_wait_polls;
+    a.bu_mode = g_bu_mode;
+    a.bu_div = g_bu_div;
     a.g = view_of(g, g->ws, 0);
     a.g.lm_out = nullptr;  // caches belong to another query's snapshots
     a.g.lm_in = nullptr;
@@ -2458,7 +2646,7 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
             rc = SG_ECUDA;
             break;
         }
-        SpreadArgs sp{vis.p, pend.p, qa.p, qb.p, d_S, ns, w0, 1, d_total, d_edges};
+        SpreadArgs sp{vis.p, pend.p, qa.p, qb.p, d_S, ns, w0, 1, d_total, d_edges, fr.p};
         if (model == MODEL_WIC) spread_kernel<MODEL_WIC><<<words, BT, 0, st>>>(a, sp);
         else spread_kernel<MODEL_UIC><<<words, BT, 0, st>>>(a, sp);
         if (cudaGetLastError() != cudaSuccess) {
@@ -2471,6 +2659,7 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
     dbuf_free(pend, st);
     dbuf_free(qa, st);
     dbuf_free(qb, st);
+    dbuf_free(fr, st);
     return rc;
 }
 
@@ -2480,10 +2669,12 @@ sg_status run_walk(sg_graph *g, const sg_workspace &ws, const Coins &co, int mod
 {
     EngineArgs a{};
     a.spin = g_wait_polls;
+    a.bu_mode = 0;  // the marginal-gain walks get no frontier array
+    a.bu_div = 1;
     a.g = view_of(g, ws, heavy_on);
     a.co = co;
     a.lmk_k = 0;
-    SpreadArgs sp{vis, pend, qa, qb, d_S, ns, 0, FWD_GROUPS, d_total, d_edges};
+    SpreadArgs sp{vis, pend, qa, qb, d_S, ns, 0, FWD_GROUPS, d_total, d_edges, nullptr};
     if (model == MODEL_WIC) spread_kernel<MODEL_WIC><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, sp);
     else spread_kernel<MODEL_UIC><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, sp);
     SG_CUDA_TRY(cudaGetLastError());

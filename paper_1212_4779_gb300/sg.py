@@ -31,7 +31,7 @@ EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg
            "sg_batch_capture", "sg_batch_launch", "sg_batch_free", "sg_server_create", "sg_server_submit",
            "sg_server_poll", "sg_server_counts", "sg_server_destroy",
            "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-           "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_graph_trim", "sg_select",
+           "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_set_walk_groups", "sg_set_direction", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_graph_trim", "sg_select",
            "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version",
            "sg_debug_inject_flags", "sg_debug_set_wait_limit")
 
@@ -108,6 +108,8 @@ def lib() -> ctypes.CDLL:
         L.sg_set_snapshot_lists.argtypes = [i32]
         L.sg_set_mask_cache.argtypes = [i32]
         L.sg_set_forward_lists.argtypes = [i32]
+        L.sg_set_walk_groups.argtypes = [i32]
+        L.sg_set_direction.argtypes = [i32, i32]
         L.sg_graph_trim.argtypes = [P]
         L.sg_debug_inject_flags.argtypes = [i32]
         L.sg_debug_set_wait_limit.argtypes = [i64]
@@ -144,7 +146,7 @@ def lib() -> ctypes.CDLL:
         for name in ("sg_workspace_create", "sg_workspace_bytes", "sg_select_ws", "sg_select_batch",
                      "sg_batch_capture", "sg_batch_launch", "sg_server_create", "sg_server_submit",
                      "sg_server_poll", "sg_server_counts", "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-                     "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+                     "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_set_walk_groups", "sg_set_direction", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
                      "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr",
                      "sg_debug_inject_flags", "sg_debug_set_wait_limit"):
             getattr(L, name).restype = ctypes.c_int
@@ -271,6 +273,16 @@ def sg_set_snapshot_lists(enable: int = 1):
 def sg_set_forward_lists(enable: int = 1):
     """Forward per-snapshot live lists for sparse initial-gain expansions (0: off)."""
     _check(lib().sg_set_forward_lists(int(enable)))
+
+
+def sg_set_direction(mode: int = 1, divisor: int = 4):
+    """Walk levels: 0 top-down only, 1 bottom-up past n/divisor frontier nodes, 2 bottom-up after level 0."""
+    _check(lib().sg_set_direction(int(mode), int(divisor)))
+
+
+def sg_set_walk_groups(groups: int = 8):
+    """Blocks per 64-snapshot word of the forward and landmark walks (8/16/32/64)."""
+    _check(lib().sg_set_walk_groups(int(groups)))
 
 
 def sg_set_mask_cache(enable: int = 0):

@@ -93,6 +93,11 @@ def test_setters_validate_without_gpu(libpath):
     assert L.sg_set_heavy_threshold(2) == sg.SG_OK
     assert L.sg_debug_inject_flags(-1) == sg.SG_EINVAL
     assert L.sg_debug_inject_flags(0) == sg.SG_OK  # clears; no query runs here
+    assert L.sg_set_direction(3, 4) == sg.SG_EINVAL
+    assert L.sg_set_direction(1, 0) == sg.SG_EINVAL
+    assert L.sg_set_direction(1, 4) == sg.SG_OK
+    assert L.sg_set_walk_groups(12) == sg.SG_EINVAL
+    assert L.sg_set_walk_groups(8) == sg.SG_OK
     assert L.sg_debug_set_wait_limit(-1) == sg.SG_EINVAL
     assert L.sg_debug_set_wait_limit(0) == sg.SG_OK  # restores the default; no query runs here
 

@@ -127,6 +127,60 @@ def limits(sg):
     sg.sg_set_snapshot_lists(1)
     sg.sg_set_mask_cache(0)
     sg.sg_set_forward_lists(1)
+    sg.sg_set_walk_groups(8)
+    sg.sg_set_direction(1, 4)
+
+
+@pytest.mark.parametrize("mode,div", [(0, 4), (1, 4), (1, 64), (2, 1)])
+@pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01", "er2k_uic0.1", "giant"])
+def test_direction_optimising_gives_identical_results(sg, limits, name, mode, div):
+    """Top-down only, switching by frontier size, and bottom-up forced after
+    the first level: the forward update's walk and ancestor walk and the
+    landmark walks reach the same (node, snapshot) pairs, so initial gains,
+    seeds, gains and all three counters equal the oracle's; so does the
+    spread of the chosen seeds.  "giant" is UIC 0.05 on a Chung-Lu graph with
+    a giant component, where frontiers pass n / 4 and the switch is taken."""
+    if name == "giant":
+        n, s, d = inputs.chung_lu_undirected(4000, 30000, 2.5, 15.0, 77)
+        model, p, R, seed = "uic", 0.05, 128, 99
+    else:
+        wl = inputs.workload(name)
+        n, s, d = wl.graph()
+        model, p, R, seed = wl.model, wl.p, wl.R, wl.seed
+    sg.sg_set_direction(mode, div)
+    for groups in (8, 32):
+        sg.sg_set_walk_groups(groups)
+        g, o = _both(sg, n, s, d, model, p)
+        ref = o.select(R, 12, seed, mode=oracle.DU, want_init=True)
+        s_gpu, ed = g.init_gains(R, model, p, seed)
+        assert np.array_equal(s_gpu, ref["s_init"]) and ed == int(ref["counters"][0])
+        res = g.select(R, 12, model, p, seed, stats=True)
+        assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+        got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+        assert got == [int(x) for x in ref["counters"]]
+        tot, edges = g.spread(R + 64, model, p, seed + 1, res.seeds)
+        want_t, want_e = o.spread(R + 64, seed + 1, res.seeds, want_edges=True)
+        assert tot == want_t and edges == want_e
+        g.close()
+
+
+@pytest.mark.parametrize("groups", [8, 16, 32, 64])
+@pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01", "er2k_uic0.1"])
+def test_walk_groups_give_identical_results(sg, limits, name, groups):
+    """The forward update's walk and the landmark walks split each 64-snapshot
+    word over 8 to 64 blocks (bit-disjoint atomics on shared words): the
+    oracle's initial gains, seeds, gains and counters for every split."""
+    wl = inputs.workload(name)
+    n, s, d = wl.graph()
+    sg.sg_set_walk_groups(groups)
+    g, o = _both(sg, n, s, d, wl.model, wl.p)  # the workspace's queues are sized for this split
+    ref = o.select(wl.R, 12, wl.seed, mode=oracle.DU, want_init=True)
+    s_gpu, ed = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
+    assert np.array_equal(s_gpu, ref["s_init"]) and ed == int(ref["counters"][0])
+    res = g.select(wl.R, 12, wl.model, wl.p, wl.seed, stats=True)
+    assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+    got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+    assert got == [int(x) for x in ref["counters"]]
 
 
 @pytest.mark.parametrize("fl", [0, 1])
