@@ -335,6 +335,73 @@ def run_batched(args):
     return 0
 
 
+def batched_served_summary(sg, args):
+    """Bounded versions of the batched and served workloads for the default
+    line: the first `summary_queries` batched recipes (Chung-Lu, n
+    log-uniform in [1e3, 2e5], mixed cascades, R in {64, 128, 256}, k in
+    [10, 100]) one query per launch and as one captured CUDA graph; then a
+    Poisson trace (`summary_requests` requests at `summary_rate`/s, R in
+    {100, 200}, k in [10, 100]) against those resident graphs through the
+    continuous-batching server and one query per launch.  Every result of
+    the batch, the graph replay and the server equals the one-per-launch
+    result."""
+    import torch
+
+    from paper_1212_4779_gb300 import serve
+
+    qs = inputs.batch_queries(args.summary_queries)
+    coo = _batch_graphs(qs)
+    graphs = [sg.Graph.from_coo(*c) for c in coo]
+    del coo
+    dev = torch.device("cuda", torch.cuda.current_device())
+    outs = [(torch.zeros(q["k"], dtype=torch.int32, device=dev), torch.zeros(q["k"], dtype=torch.int64, device=dev))
+            for q in qs]
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    for q, g, (so, go) in zip(qs, graphs, outs):
+        sg.sg_select(g.handle, q["R"], q["k"], q["model"], q["p"], q["seed"], so, go, stream=stream)
+    stream.synchronize()
+    t_serial = time.perf_counter() - t0
+    ref = [(so.cpu().numpy().copy(), go.cpu().numpy().copy()) for so, go in outs]
+    for g in graphs:
+        g.trim()
+    wss = [sg.sg_workspace_create(g.handle, q["R"], q["k"]) for q, g in zip(qs, graphs)]
+    items = [(g.handle, w, q["R"], q["k"], q["model"], q["p"], q["seed"], so, go)
+             for q, g, w, (so, go) in zip(qs, graphs, wss, outs)]
+    b = sg.sg_batch_capture(items, concurrency=args.concurrency, stream=stream)
+    sg.sg_batch_launch(b, stream=stream)
+    stream.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    ev0.record(stream)
+    for _ in range(reps):
+        sg.sg_batch_launch(b, stream=stream)
+    ev1.record(stream)
+    ev1.synchronize()
+    t_graph = ev0.elapsed_time(ev1) / 1e3 / reps
+    same_batch = all(np.array_equal(so.cpu().numpy(), a) and np.array_equal(go.cpu().numpy(), b_)
+                     for (so, go), (a, b_) in zip(outs, ref))
+    sg.sg_batch_free(b)
+    for w in wss:
+        sg.sg_workspace_free(w)
+    nq = len(qs)
+    batched = {"queries": nq, "one_query_per_launch_qps": nq / t_serial, "batch_graph_qps": nq / t_graph,
+               "speedup": t_serial / t_graph, "results_equal": bool(same_batch)}
+    models = [(q["model"], q["p"]) for q in qs]
+    trace = serve.poisson_trace(args.summary_requests, args.summary_rate, 5000, models)
+    st_served, res_s = serve.run_served(graphs, trace, max_running=args.concurrency, k_cap=128)
+    st_serial, res_1 = serve.run_serial(graphs, trace)
+    same = all(np.array_equal(res_s[i][0], res_1[i][0]) and np.array_equal(res_s[i][1], res_1[i][1])
+               for i in range(len(trace)))
+    served = {"workload": f"Poisson {args.summary_rate}/s, {len(trace)} requests over the {nq} recipe graphs, "
+                          f"R in {{100,200}}, k in [10,100]",
+              "max_running": args.concurrency, "served": st_served, "one_query_per_launch": st_serial,
+              "results_equal": bool(same)}
+    for g in graphs:
+        g.close()
+    return batched, served
+
+
 def run_served(args):
     """Config 5: Poisson arrivals against resident graphs -- a directed R-MAT
     (scale 22 by default, WIC) plus the first 64 batched-recipe graphs;
@@ -496,6 +563,15 @@ def main():
     ap.add_argument("--celf-workload", default="rmat20_wic", help="celf: the query compared with the dynamic update")
     ap.add_argument("--mask-cache", type=int, default=0, choices=[0, 1],
                     help="1: evaluate every arc's coins once per query into the live-mask cache")
+    ap.add_argument("--no-summary", action="store_true",
+                    help="skip the bounded batched and served summary of the default line")
+    ap.add_argument("--summary-queries", type=int, default=64, help="summary: batched recipes (and served graphs)")
+    ap.add_argument("--summary-requests", type=int, default=256, help="summary: served trace length")
+    ap.add_argument("--summary-rate", type=float, default=200.0, help="summary: served arrivals per second")
+    ap.add_argument("--walk-groups", type=int, default=None, choices=[8, 16, 32, 64],
+                    help="blocks per 64-snapshot word of the forward and landmark walks (library default if unset)")
+    ap.add_argument("--direction", type=str, default=None,
+                    help="MODE,DIVISOR of the walks' direction-optimising switch (library default if unset)")
     args = ap.parse_args()
     if args.workload == "batched" and args.impl == "ours":
         return run_batched(args)
@@ -525,6 +601,7 @@ def main():
     from paper_1212_4779_gb300 import sg
 
     sg.sg_set_mask_cache(args.mask_cache)
+    apply_knobs(sg, args)
     n, s, d = wl.graph()
     g = sg.Graph.from_coo(n, s, d)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -597,6 +674,11 @@ def main():
     if not args.no_e2e:
         e2e = measure_e2e(sg, wl, n, s, d, args, stream)
 
+    batched = served = None
+    if not args.no_summary and ws == 1:
+        g.trim()
+        batched, served = batched_served_summary(sg, args)
+
     cpu = None
     if not args.no_cpu_baseline and ws == 1 and rank == 0:
         v, sample, _t, cores, _rs = cpu_baseline(wl, n, s, d, target_s=args.ref_seconds)
@@ -609,7 +691,9 @@ def main():
         "dtype": "int64", "data": "synthetic",
         "config": {"workload": wl_desc(wl), "n": n, "m": int(g.m), "R": wl.R, "k": wl.k,
                    "l2": "512 MB buffer written between timed steps", "parallelism": f"replicas x{ws}",
-                   "mask_cache": bool(st_last["mask_cache"])},
+                   "mask_cache": bool(st_last["mask_cache"]),
+                   "walk_groups": args.walk_groups or "library default",
+                   "direction": args.direction or "library default"},
         "snapshot_edges_per_step": edges_step,
         "phase_ms": {k: round(st_last[k], 3) for k in ("ms_index", "ms_landmarks", "ms_init_tier1", "ms_init_tier2",
                                                       "ms_init_tier3", "ms_init", "ms_fwd", "ms_rounds", "ms_total")},
@@ -625,6 +709,8 @@ def main():
         "e2e": e2e,
         "clocks": clocks,
         "peaks_source": src,
+        "batched": batched,
+        "served": served,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -632,6 +718,15 @@ def main():
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def apply_knobs(sg, args):
+    """Library tuning knobs named on the command line (none changes a result)."""
+    if args.walk_groups:
+        sg.sg_set_walk_groups(args.walk_groups)
+    if args.direction:
+        mode, div = (int(x) for x in args.direction.split(","))
+        sg.sg_set_direction(mode, div)
 
 
 def phase_rates(st):

@@ -185,6 +185,18 @@ sg_status sg_set_snapshot_lists(int32_t enable);
  * later calls.  Errors: SG_EINVAL unless 0 or 1. */
 sg_status sg_set_forward_lists(int32_t enable);
 
+/* Per-snapshot SCC condensation of the initial-gain sources: 1 (the default)
+ * or 0.  The landmarks serve as pivots: a landmark's strongly connected
+ * component in snapshot r is R(G'_r, x_i) intersected with U(G'_r, x_i)
+ * (forward-backward from the pivot, exact), and every member v has
+ * R(G'_r, v) = R(G'_r, x_i).  A source inside such a component skips its
+ * walk for that snapshot and is credited the pivot's reach through the
+ * landmark union (which already counts it); without the switch the walk
+ * runs and all it finds is filtered out.  Needs landmarks (sg_set_landmarks
+ * > 0).  Results and counters do not depend on it.  Applies to later
+ * calls.  Errors: SG_EINVAL unless 0 or 1. */
+sg_status sg_set_scc_condensation(int32_t enable);
+
 /* Direction-optimising switch of the level-synchronous walks (the forward
  * dynamic update's walk from each new seed, its walk back over the seed's
  * ancestors, the landmark walks of the initial gains, and sg_spread).  A
@@ -310,6 +322,53 @@ void sg_workspace_free(sg_workspace *ws);
 sg_status sg_select_ws(sg_graph *g, sg_workspace *ws, int32_t R, int32_t k, sg_cascade c, uint64_t seed,
                        void *stream, int32_t *out_seeds, int64_t *out_gains, sg_stats *stats);
 
+/* Tuning knobs of a query (no counterpart in the paper; none changes a
+ * result, only how the same counts are computed):
+ *   walk_groups     blocks per 64-snapshot word of the forward and landmark
+ *                   walks (8, 16, 32, 64; see sg_set_walk_groups)
+ *   direction_mode, direction_div   the walks' top-down/bottom-up switch
+ *                   (see sg_set_direction)
+ *   tier1_keys, tier2_keys          engine tier limits (sg_set_engine_limits)
+ *   landmarks       0..8 (sg_set_landmarks)
+ *   scc             0/1 (sg_set_scc_condensation)
+ *   forward_lists   0/1 (sg_set_forward_lists)
+ * The slice width is fixed at 64 snapshots (one 64-bit word per node and
+ * task) and is not a knob. */
+typedef struct {
+    int32_t walk_groups;
+    int32_t direction_mode;
+    int32_t direction_div;
+    int32_t tier1_keys;
+    int32_t tier2_keys;
+    int32_t landmarks;
+    int32_t scc;
+    int32_t forward_lists;
+} sg_tuning;
+
+/* The process-wide knobs (what the sg_set_* calls set) / set all of them.
+ * Errors: SG_EINVAL for a NULL pointer or a value out of range. */
+sg_status sg_get_tuning(sg_tuning *out);
+sg_status sg_set_tuning(const sg_tuning *t);
+
+/* Autotuner.  Finds the fastest knobs for one query: times whole
+ * selections of (g, R, k, c, seed) on `stream` under candidate settings,
+ * one knob at a time (walk groups, direction switch, landmarks, SCC
+ * condensation, tier limits, forward lists; each candidate the fastest of
+ * two timed runs after one untimed), checks that every candidate returns
+ * the same seeds and gains, and keeps a change only when it is at least 1%
+ * faster.  *out receives the tuning and *out_ms (may be NULL) its time per
+ * selection.  With cache_path (may be NULL) a JSON-lines file is read
+ * first -- a line whose key (node and arc counts, largest out-degree,
+ * model, UIC probability, word count) matches is returned without timing --
+ * and a new result is appended.  The process-wide knobs are not changed:
+ * pass *out to sg_set_tuning, or put it in sg_query.tuning.  The graph's
+ * own workspace is released and sized again (its queues for 64 walk
+ * groups).  Synchronises `stream`; takes about 20 selections' time.
+ * Errors: as sg_select; SG_EINTERNAL if two settings gave different
+ * results. */
+sg_status sg_autotune(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                      const char *cache_path, sg_tuning *out, double *out_ms);
+
 /* One query of a batch. */
 typedef struct {
     sg_graph *graph;
@@ -321,6 +380,8 @@ typedef struct {
     int32_t *out_seeds;   /* int32[k], device or pinned host memory */
     int64_t *out_gains;   /* int64[k], device or pinned host memory */
     sg_status status;     /* written by the call */
+    const sg_tuning *tuning;  /* NULL: the process-wide knobs; else this query's (e.g. from sg_autotune);
+                                 a workspace's walk queues cap walk_groups at what it was sized for */
 } sg_query;
 
 /* Run nq independent queries (different graphs, R, k, cascades) at once:

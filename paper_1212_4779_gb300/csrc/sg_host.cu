@@ -89,6 +89,21 @@ int g_mask_cache = 0;
 int g_fwd_lists = 1;
 int g_walk_groups = 8;
 
+Knobs knobs()
+{
+    if (t_knobs) return *t_knobs;
+    Knobs k;
+    k.walk_groups = g_walk_groups;
+    k.bu_mode = g_bu_mode;
+    k.bu_div = g_bu_div;
+    k.t1_keys = g_tier_limit[0];
+    k.t2_keys = g_tier_limit[1];
+    k.landmarks = g_landmarks;
+    k.scc = g_scc;
+    k.fwd_lists = g_fwd_lists;
+    return k;
+}
+
 namespace {
 int g_heavy_min_deg = 2;
 sg_alloc_fn g_alloc = nullptr;
@@ -565,7 +580,7 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
     const size_t n = (size_t)g->n, nw = n * (size_t)W, W64 = (size_t)64 * W;
     size_t b = 8 * n;                                  // s
     b += 8 * nw * 4;                                   // cov, nbits, pendf, bottom-up frontier
-    b += 4 * nw * (size_t)std::max(8, g_walk_groups) * 2;  // forward queues
+    b += 4 * nw * (size_t)std::max(8, knobs().walk_groups) * 2;  // forward queues
     b += 4 * nw;                                       // du_x
     b += 4 * (nw + W64 + 64) * 2;                      // task lists
     b += 4 * nw * 64;                                  // per-snapshot targets
@@ -586,7 +601,7 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
             const size_t nq = (size_t)g->n * 64 * W + 1;
             const double want = 1.5 * 64.0 * W * std::max(g->hlive_out_wic, 0.1 * (double)g->hsum_out) + (1u << 20);
             const double fb = want * 4.0 + (double)(2 * nq + nq / 1024 + 16) * 8.0;
-            if (g_fwd_lists && fb <= 8.0 * (double)(1ull << 30)) b += (size_t)fb;
+            if (knobs().fwd_lists && fb <= 8.0 * (double)(1ull << 30)) b += (size_t)fb;
         }
         const size_t nq = (size_t)g->nh_in * W64 + 1;
         b += nq * 16 + ((size_t)1 << 20) * 4 + (size_t)(1.5 * 64.0 * W * (double)g->nh_in) * 4;
@@ -606,7 +621,7 @@ sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, 
         SG_TRY(dbuf_alloc(ws.nbits, nw, st));
         SG_TRY(dbuf_alloc(ws.pendf, nw, st));
         // one level queue per (word, walk group)
-        ws.fq_groups = std::max(8, g_walk_groups);
+        ws.fq_groups = std::max(8, knobs().walk_groups);
         SG_TRY(dbuf_alloc(ws.fq_a, nw * (size_t)ws.fq_groups, st));
         SG_TRY(dbuf_alloc(ws.fq_b, nw * (size_t)ws.fq_groups, st));
         SG_TRY(dbuf_alloc(ws.du_x, nw, st));
@@ -704,7 +719,7 @@ sg_status ensure_fwd_lists(sg_graph *g, sg_workspace &ws, const Coins &co, doubl
                            cudaStream_t st)
 {
     ws.fl_on = 0;
-    if (!g_fwd_lists || g->nh_out == 0) return SG_OK;
+    if (!knobs().fwd_lists || g->nh_out == 0) return SG_OK;
     const double R = 64.0 * co.W;
     const double expect = model == MODEL_WIC ? R * g->hlive_out_wic : R * p_uic * (double)g->hsum_out;
     const size_t want = (size_t)(expect * 1.5) + (1u << 20);
@@ -848,6 +863,16 @@ sg_status sg_set_direction(int32_t mode, int32_t divisor)
     }
     g_bu_mode = mode;
     g_bu_div = divisor;
+    return SG_OK;
+}
+
+sg_status sg_set_scc_condensation(int32_t enable)
+{
+    if (enable != 0 && enable != 1) {
+        set_error("SCC condensation switch must be 0 or 1");
+        return SG_EINVAL;
+    }
+    g_scc = enable;
     return SG_OK;
 }
 
@@ -1115,7 +1140,7 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     ws.fl_on = 0;
     if (heavy_on) SG_TRY(ensure_fwd_lists(g, ws, co, c.p, model, st));
     SG_TRY(ensure_mask_cache(g, ws, co.W, st));
-    ws.walk_groups = std::min(g_walk_groups, ws.fq_groups);
+    ws.walk_groups = std::min(knobs().walk_groups, ws.fq_groups);
     if (prepare_only) return SG_OK;
     // events: 0 start, 1 after index, 2 after init tier 1, 3 after init,
     // 4 end; per round: after forward update

@@ -306,6 +306,38 @@ extern int g_walk_groups;
 // n / g_bu_div nodes, 2 bottom-up from the second level on
 extern int g_bu_mode;
 extern int g_bu_div;
+// nonzero: initial-gain sources inside a landmark's strongly connected
+// component skip those snapshots' walks (the landmark credit counts them)
+extern int g_scc;
+// The tunable knobs one query runs with (none changes a result).
+struct Knobs {
+    int walk_groups;  // blocks per word of the forward and landmark walks
+    int bu_mode;      // direction-optimising switch of the walks
+    int bu_div;
+    int t1_keys;      // tier-1 / tier-2 key limits of the traversal engines
+    int t2_keys;
+    int landmarks;    // landmarks for the initial gains (0 .. 8)
+    int scc;          // SCC condensation of initial-gain sources
+    int fwd_lists;    // forward per-snapshot live lists
+};
+// The calling thread's current query knobs: the per-query tuning it was
+// given (t_knobs, set for the duration of one query) or else the
+// process-wide values of the sg_set_* calls.
+extern thread_local const Knobs *t_knobs;
+Knobs knobs();
+// Applies a query's tuning (NULL: none) to the calling thread for its
+// lifetime.
+struct KnobScope {
+    explicit KnobScope(const sg_tuning *t);
+    ~KnobScope();
+    KnobScope(const KnobScope &) = delete;
+    KnobScope &operator=(const KnobScope &) = delete;
+
+  private:
+    const Knobs *prev_ = nullptr;
+    Knobs own_{};
+};
+sg_status check_query_tuning(const sg_tuning *t);
 // polls a bounded device-side wait of the traversal engines makes before it
 // gives up (default 2^22; a testing hook can shorten it)
 extern long long g_wait_polls;

@@ -319,6 +319,7 @@ struct EngineArgs {
     long long spin;         // polls a bounded wait makes before it gives up
     int bu_mode;            // level-synchronous walks: 0 top-down only, 1 switch by frontier size, 2 bottom-up after level 0
     int bu_div;             // mode 1: a level runs bottom-up when its frontier holds more than n / bu_div nodes
+    int scc;                // initial gains: condense sources inside a landmark's strongly connected component
 };
 
 
@@ -392,6 +393,25 @@ __device__ __forceinline__ void lmk_totals(const EngineArgs &a, int word, const 
         cnt += a.lmk_U[q];
         edges += a.lmk_E[q];
     }
+}
+
+// Snapshot bits of word `word` in which source v lies in the strongly
+// connected component of a landmark x_i (v in R(G'_r, x_i) and v reaches
+// x_i: forward-backward from the landmark as pivot, exact).  There
+// R(G'_r, v) = R(G'_r, x_i), which the landmark credit already counts, so
+// the source's walk for those snapshots is skipped (condensation); without
+// the switch the walk runs and every arrival is filtered out.
+__device__ __forceinline__ uint64_t lmk_scc_bits(const EngineArgs &a, int word, int v)
+{
+    if (!a.scc) return 0;
+    const unsigned long long *rx = lmk_bits(a.lmk_rx, a, word, v), *ux = lmk_bits(a.lmk_ux, a, word, v);
+    uint64_t m = 0;
+#pragma unroll
+    for (int i = 0; i < MAX_LMK; ++i) {
+        if (i >= a.lmk_k) break;
+        m |= __ldg(rx + i) & __ldg(ux + i);
+    }
+    return m;
 }
 
 // ============================================================ warp engine
@@ -499,7 +519,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         if (lane < MAX_LMK)
             T.xbits[lane] = lane < a.lmk_k ? lmk_reaches(a, word, x0, lane) & word_mask(word, co.R) : 0ull;
         if (lane == 0) {
-            const uint64_t M0 = word_mask(word, co.R);
+            const uint64_t M0 = word_mask(word, co.R) & ~lmk_scc_bits(a, word, x0);
             const uint32_t h = slot_of<LOGC>(x0);
             T.key[h] = x0;
             T.vis[h] = M0;
@@ -1501,7 +1521,7 @@ __global__ void __launch_bounds__(CoopShape<TAB, LOGC>::T, CoopShape<TAB, LOGC>:
             rs = (uint32_t)word * 64u;
             if (tid < MAX_LMK)
                 c.xbits[tid] = tid < a.lmk_k ? lmk_reaches(a, word, x0, tid) & word_mask(word, a.co.R) : 0ull;
-            if (tid == 0) coop_seed<TAB, LOGC>(T, c, x0, word_mask(word, a.co.R), limit);
+            if (tid == 0) coop_seed<TAB, LOGC>(T, c, x0, word_mask(word, a.co.R) & ~lmk_scc_bits(a, word, x0), limit);
         } else {
             const int r = find_off(a.coff, 64 * a.co.W, t);
             const long long ci = t - a.coff[r];
@@ -1526,7 +1546,7 @@ __global__ void __launch_bounds__(CoopShape<TAB, LOGC>::T, CoopShape<TAB, LOGC>:
             // was counted then; only the source's own seeded bits can lie in
             // a credited landmark set (x0 in R(G'_r, x_i) for a reached x_i):
             // those are credited by the landmark instead.
-            const uint64_t M0 = word_mask(word, a.co.R);
+            const uint64_t M0 = word_mask(word, a.co.R) & ~lmk_scc_bits(a, word, x0);  // the seeded bits
             const uint64_t ve = lmk_effective(a, word, x0, M0, xb);
             cnt += __popcll(ve);
             if (ve != M0)
@@ -2372,8 +2392,10 @@ EngineArgs engine_args(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
     a.ntasks = 0;
     a.limit = 1;
     a.spin = g_wait_polls;
-    a.bu_mode = g_bu_mode;
-    a.bu_div = g_bu_div;
+    const Knobs kn = knobs();
+    a.bu_mode = kn.bu_mode;
+    a.bu_div = kn.bu_div;
+    a.scc = kn.scc;
     return a;
 }
 
@@ -2410,7 +2432,7 @@ sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cuda
     if (ev && ev->start) SG_CUDA_TRY(cudaEventRecord(ev->start, st));
     EngineArgs a = a0;
     {
-        a.limit = std::max(1, std::min(g_tier_limit[0], (1 << T1_LOGC) / 2));
+        a.limit = std::max(1, std::min(knobs().t1_keys, (1 << T1_LOGC) / 2));
         auto kern = warp_engine_kernel<T1_LOGC, DIR, MODEL, TASK>;
         const size_t smem = (WE_THREADS / 32) * tab_bytes<T1_LOGC>();
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2428,8 +2450,8 @@ sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cuda
         // 4096-slot second stage for their 1-2 K-node tasks was slower than
         // sending those to tier 3); reverse tasks (about 1 K nodes on
         // average) run in 4096-slot tables, two per SM.
-        const int lim1 = std::max(1, std::min(g_tier_limit[0], (1 << T1_LOGC) / 2));
-        const int t2 = std::max(1, std::min(g_tier_limit[1], (1 << CO_LOGC) / 2));
+        const int lim1 = std::max(1, std::min(knobs().t1_keys, (1 << T1_LOGC) / 2));
+        const int t2 = std::max(1, std::min(knobs().t2_keys, (1 << CO_LOGC) / 2));
         Ctl *ctl = ws.ctl.p;
         const StageIO io{ws.list1.p, &ctl->l1_count, &ctl->l1_next, ws.list2.p, &ctl->l2_count, 1};
         if (TASK == TASK_INIT)
@@ -2469,7 +2491,7 @@ sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
 {
     EngineArgs a = engine_args(g, ws, co, heavy_on);
     a.ntasks = (long long)g->n * co.W;
-    const int K = std::min(std::min(g_landmarks, g->lmk_count), MAX_LMK);
+    const int K = std::min(std::min(knobs().landmarks, g->lmk_count), MAX_LMK);
     if (K > 0) {
         a.lmk_k = K;
         for (int i = 0; i < K; ++i) a.lmk_x[i] = g->lmk_nodes[i];
@@ -2562,6 +2584,8 @@ thread_local int g_launches = 0;
 long long g_wait_polls = WAIT_POLLS_DEFAULT;
 int g_bu_mode = 1;
 int g_bu_div = 4;
+int g_scc = 1;
+thread_local const Knobs *t_knobs = nullptr;
 int g_tier_limit[2] = {(1 << T1_LOGC) / 2, (1 << CO_LOGC) / 2};
 int g_landmarks = 8;
 
@@ -2630,8 +2654,8 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
     }
     EngineArgs a{};
     a.spin = g_wait_polls;
-    a.bu_mode = g_bu_mode;
-    a.bu_div = g_bu_div;
+    a.bu_mode = knobs().bu_mode;
+    a.bu_div = knobs().bu_div;
     a.g = view_of(g, g->ws, 0);
     a.g.lm_out = nullptr;  // caches belong to another query's snapshots
     a.g.lm_in = nullptr;

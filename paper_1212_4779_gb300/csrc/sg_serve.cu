@@ -63,6 +63,10 @@ sg_status check_batch(int32_t nq, sg_query *q, int32_t concurrency)
     std::vector<const sg_workspace *> used;
     for (int32_t i = 0; i < nq; ++i) {
         q[i].status = SG_OK;
+        if (check_query_tuning(q[i].tuning) != SG_OK) {
+            q[i].status = SG_EINVAL;
+            return SG_EINVAL;
+        }
         if (!q[i].graph || !q[i].out_seeds || !q[i].out_gains) {
             q[i].status = SG_EINVAL;
             set_error("batch: query %d has a NULL graph or output", i);
@@ -90,6 +94,7 @@ sg_status run_batch(int32_t nq, sg_query *q, const std::vector<cudaStream_t> &ps
 {
     sg_status first = SG_OK;
     for (int32_t i = 0; i < nq; ++i) {
+        KnobScope ks(q[i].tuning);
         const sg_status rc = select_impl(q[i].graph, *query_ws(q[i]), q[i].R, q[i].k, q[i].cascade, q[i].seed,
                                          origin, q[i].out_seeds, q[i].out_gains, nullptr, true);
         q[i].status = rc;
@@ -102,6 +107,7 @@ sg_status run_batch(int32_t nq, sg_query *q, const std::vector<cudaStream_t> &ps
     for (cudaStream_t s : ps) SG_CUDA_TRY(cudaStreamWaitEvent(s, fork, 0));
     for (int32_t i = 0; i < nq; ++i) {
         cudaStream_t s = ps[(size_t)i % ps.size()];
+        KnobScope ks(q[i].tuning);
         const sg_status rc = select_impl(q[i].graph, *query_ws(q[i]), q[i].R, q[i].k, q[i].cascade, q[i].seed, s,
                                          q[i].out_seeds, q[i].out_gains, nullptr, false);
         q[i].status = rc;
@@ -179,6 +185,11 @@ struct sg_server {
     std::unordered_map<int64_t, SrvRequest *> reqs;
     std::vector<SrvSlot> slots;
     std::vector<SrvWs> pool;
+    // workspaces are built and released on a stream of their own, so that
+    // admission never waits for a running request; a slot's stream waits
+    // on setup_ev before using a fresh workspace
+    cudaStream_t setup_st = nullptr;
+    cudaEvent_t setup_ev = nullptr;
     std::thread worker;
     bool stopping = false;
     int64_t next_id = 1;
@@ -219,9 +230,13 @@ void srv_retire(sg_server *s)
 
 // An idle workspace for (g, W), creating one within the memory budget
 // (releasing least recently used idle ones if needed).  -1: none now.
-int srv_workspace(sg_server *s, sg_graph *g, int32_t W, bool *impossible)
+// *fresh: the workspace was created now; its set-up (allocations and
+// clears) is queued on the setup stream and marked by setup_ev.  Nothing
+// here waits on the host.
+int srv_workspace(sg_server *s, sg_graph *g, int32_t W, bool *impossible, bool *fresh)
 {
     *impossible = false;
+    *fresh = false;
     for (size_t i = 0; i < s->pool.size(); ++i)
         if (!s->pool[i].busy && s->pool[i].g == g && s->pool[i].W >= W) return (int)i;
     const size_t need = workspace_bytes(g, W, s->cfg.k_cap);
@@ -230,9 +245,10 @@ int srv_workspace(sg_server *s, sg_graph *g, int32_t W, bool *impossible)
         for (size_t i = 0; i < s->pool.size(); ++i)
             if (!s->pool[i].busy && (lru < 0 || s->pool[i].last_use < s->pool[(size_t)lru].last_use)) lru = (int)i;
         if (lru < 0) break;
+        // idle: its last request has finished (its slot event completed), so
+        // the release is queued in stream order without waiting
         sg_workspace *w = s->pool[(size_t)lru].ws;
-        cudaDeviceSynchronize();
-        free_workspace(*w, (cudaStream_t)0);
+        free_workspace(*w, s->setup_st);
         delete w;
         s->used -= s->pool[(size_t)lru].bytes;
         s->pool.erase(s->pool.begin() + lru);
@@ -247,15 +263,16 @@ int srv_workspace(sg_server *s, sg_graph *g, int32_t W, bool *impossible)
     }
     sg_workspace *w = new (std::nothrow) sg_workspace();
     if (!w) return -1;
-    cudaStream_t st = s->slots[0].st;
+    cudaStream_t st = s->setup_st;
     if (ensure_workspace(g, *w, W, s->cfg.k_cap, st) != SG_OK ||
         (heavy_index_enabled(g, W) && ensure_heavy_index(g, *w, W, st) != SG_OK) ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaEventRecord(s->setup_ev, st) != cudaSuccess) {
         free_workspace(*w, st);
         delete w;
         *impossible = s->running == 0;
         return -1;
     }
+    *fresh = true;
     w->owner_n = g->n;
     w->device = g->device;
     s->pool.push_back(SrvWs{g, w, W, need, false, ++s->tick});
@@ -263,7 +280,11 @@ int srv_workspace(sg_server *s, sg_graph *g, int32_t W, bool *impossible)
     return (int)s->pool.size() - 1;
 }
 
-void srv_admit(sg_server *s)
+// Admits queued requests in arrival order while a slot and memory allow.
+// Called with the lock held; the lock is released while a request's
+// kernels are enqueued (submit and poll never wait behind a launch
+// sequence).  Only the worker touches slots and the workspace pool.
+void srv_admit(sg_server *s, std::unique_lock<std::mutex> &lock)
 {
     while (!s->queue.empty()) {
         SrvSlot *free_slot = nullptr;
@@ -275,8 +296,8 @@ void srv_admit(sg_server *s)
         if (!free_slot) return;
         SrvRequest *r = s->queue.front();
         const int32_t W = (r->R + 63) / 64;
-        bool impossible = false;
-        const int wi = srv_workspace(s, r->g, W, &impossible);
+        bool impossible = false, fresh = false;
+        const int wi = srv_workspace(s, r->g, W, &impossible, &fresh);
         if (wi < 0) {
             if (!impossible) return;  // wait for memory
             s->queue.pop_front();
@@ -288,20 +309,29 @@ void srv_admit(sg_server *s)
         }
         s->queue.pop_front();
         s->pool[(size_t)wi].busy = true;
-        const sg_status rc = select_impl(r->g, *s->pool[(size_t)wi].ws, r->R, r->k, r->c, r->seed, free_slot->st,
-                                         free_slot->h_seeds, free_slot->h_gains, nullptr, false);
-        if (rc != SG_OK || cudaEventRecord(free_slot->ev, free_slot->st) != cudaSuccess) {
-            s->pool[(size_t)wi].busy = false;
-            r->status = rc != SG_OK ? rc : SG_ECUDA;
-            r->t_done = now_ms();
-            r->state = 2;
-            ++s->finished;
-            continue;
-        }
         r->state = 1;
         free_slot->req = r;
         free_slot->ws_index = wi;
         ++s->running;
+        sg_workspace *ws = s->pool[(size_t)wi].ws;
+        lock.unlock();
+        sg_status rc = SG_OK;
+        if (fresh && cudaStreamWaitEvent(free_slot->st, s->setup_ev, 0) != cudaSuccess) rc = SG_ECUDA;
+        if (rc == SG_OK)
+            rc = select_impl(r->g, *ws, r->R, r->k, r->c, r->seed, free_slot->st, free_slot->h_seeds,
+                             free_slot->h_gains, nullptr, false);
+        if (rc == SG_OK && cudaEventRecord(free_slot->ev, free_slot->st) != cudaSuccess) rc = SG_ECUDA;
+        lock.lock();
+        if (rc != SG_OK) {
+            s->pool[(size_t)free_slot->ws_index].busy = false;
+            free_slot->req = nullptr;
+            free_slot->ws_index = -1;
+            --s->running;
+            r->status = rc;
+            r->t_done = now_ms();
+            r->state = 2;
+            ++s->finished;
+        }
     }
 }
 
@@ -312,7 +342,7 @@ void srv_loop(sg_server *s)
     std::unique_lock<std::mutex> lock(s->mu);
     while (true) {
         srv_retire(s);
-        srv_admit(s);
+        srv_admit(s, lock);
         if (s->stopping && s->queue.empty() && s->running == 0) break;
         // wake on a submission, or poll the running slots every 50 us
         s->cv.wait_for(lock, std::chrono::microseconds(s->running ? 50 : 2000));
@@ -361,6 +391,7 @@ sg_status sg_batch_capture(int32_t nq, sg_query *q, int32_t concurrency, void *s
     SG_TRY(pool_streams(std::max(1, std::min(concurrency, nq)), ps));
     // size every workspace (allocations) before recording
     for (int32_t i = 0; i < nq; ++i) {
+        KnobScope ks(q[i].tuning);
         const sg_status rc = select_impl(q[i].graph, *query_ws(q[i]), q[i].R, q[i].k, q[i].cascade, q[i].seed,
                                          origin, q[i].out_seeds, q[i].out_gains, nullptr, true);
         q[i].status = rc;
@@ -433,6 +464,13 @@ sg_status sg_server_create(const sg_server_cfg *cfg, sg_server **out)
     SG_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
     s->budget = cfg->memory_budget ? cfg->memory_budget : (size_t)(0.8 * (double)fr);
     s->slots.resize((size_t)cfg->max_running);
+    if (cudaStreamCreateWithFlags(&s->setup_st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->setup_ev, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("sg_server_create: stream/event creation failed");
+        cudaGetLastError();
+        sg_server_destroy(s);
+        return SG_ECUDA;
+    }
     for (auto &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -568,6 +606,8 @@ void sg_server_destroy(sg_server *s)
         if (sl.h_seeds) cudaFreeHost(sl.h_seeds);
         if (sl.h_gains) cudaFreeHost(sl.h_gains);
     }
+    if (s->setup_ev) cudaEventDestroy(s->setup_ev);
+    if (s->setup_st) cudaStreamDestroy(s->setup_st);
     for (auto &kv : s->reqs) delete kv.second;
     delete s;
 }

@@ -1,0 +1,321 @@
+// sg_tune.cu -- per-query tuning knobs and the autotuner.
+//
+// None of the knobs changes a result: they pick how the same exact counts
+// are computed (how many blocks share a walk, when a walk level runs
+// bottom-up, where a task moves to a larger table, how many landmarks
+// credit the initial gains, whether landmark components condense sources,
+// whether the forward per-snapshot lists are built).  The autotuner times
+// whole selections of the caller's query under candidate settings,
+// coordinate by coordinate, checks that every candidate returns the same
+// seeds and gains, and keeps the fastest; results are cached in a JSON-lines
+// file keyed by the graph's shape, the cascade and the word count.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "sg_internal.cuh"
+
+using namespace sgi;
+
+namespace {
+
+sg_status check_tuning(const sg_tuning &t)
+{
+    const int wg = t.walk_groups;
+    if ((wg != 8 && wg != 16 && wg != 32 && wg != 64) || t.direction_mode < 0 || t.direction_mode > 2 ||
+        t.direction_div < 1 || t.tier1_keys < 1 || t.tier2_keys < 1 || t.landmarks < 0 || t.landmarks > 8 ||
+        (t.scc != 0 && t.scc != 1) || (t.forward_lists != 0 && t.forward_lists != 1)) {
+        set_error("sg_tuning out of range (walk_groups 8/16/32/64, direction mode 0..2 and divisor >= 1, "
+                  "tier keys >= 1, landmarks 0..8, scc and forward_lists 0/1)");
+        return SG_EINVAL;
+    }
+    return SG_OK;
+}
+
+Knobs to_knobs(const sg_tuning &t)
+{
+    Knobs k;
+    k.walk_groups = t.walk_groups;
+    k.bu_mode = t.direction_mode;
+    k.bu_div = t.direction_div;
+    k.t1_keys = std::min(t.tier1_keys, 256);
+    k.t2_keys = std::min(t.tier2_keys, 2048);
+    k.landmarks = t.landmarks;
+    k.scc = t.scc;
+    k.fwd_lists = t.forward_lists;
+    return k;
+}
+
+sg_tuning from_knobs(const Knobs &k)
+{
+    sg_tuning t;
+    t.walk_groups = k.walk_groups;
+    t.direction_mode = k.bu_mode;
+    t.direction_div = k.bu_div;
+    t.tier1_keys = k.t1_keys;
+    t.tier2_keys = k.t2_keys;
+    t.landmarks = k.landmarks;
+    t.scc = k.scc;
+    t.forward_lists = k.fwd_lists;
+    return t;
+}
+
+// Cache key: the graph's shape (nodes, arcs, largest out-degree), the
+// cascade (model, UIC probability) and the 64-snapshot word count.
+sg_status tuning_key(sg_graph *g, const sg_cascade &c, int32_t W, cudaStream_t st, std::string *out)
+{
+    std::vector<int32_t> rp((size_t)g->n + 1);
+    SG_CUDA_TRY(cudaMemcpyAsync(rp.data(), g->rp.p, rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    int32_t dmax = 0;
+    for (int64_t v = 0; v < g->n; ++v) dmax = std::max(dmax, rp[(size_t)v + 1] - rp[(size_t)v]);
+    char buf[256];
+    snprintf(buf, sizeof buf, "n=%lld m=%lld dmax=%d model=%d p=%.6f W=%d", (long long)g->n, (long long)g->m, dmax,
+             (int)c.model, c.model == SG_WIC ? 0.0 : c.p, (int)W);
+    *out = buf;
+    return SG_OK;
+}
+
+int json_int(const char *line, const char *name, int *out)
+{
+    char pat[64];
+    snprintf(pat, sizeof pat, "\"%s\": ", name);
+    const char *p = strstr(line, pat);
+    if (!p) return 0;
+    return sscanf(p + strlen(pat), "%d", out) == 1;
+}
+
+// Last cached tuning of `key` in the JSON-lines file, if any.
+bool cache_lookup(const char *path, const std::string &key, sg_tuning *out, double *ms)
+{
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    const std::string want = "{\"key\": \"" + key + "\"";
+    char line[1024];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        if (strncmp(line, want.c_str(), want.size()) != 0) continue;
+        sg_tuning t;
+        if (json_int(line, "walk_groups", &t.walk_groups) && json_int(line, "direction_mode", &t.direction_mode) &&
+            json_int(line, "direction_div", &t.direction_div) && json_int(line, "tier1_keys", &t.tier1_keys) &&
+            json_int(line, "tier2_keys", &t.tier2_keys) && json_int(line, "landmarks", &t.landmarks) &&
+            json_int(line, "scc", &t.scc) && json_int(line, "forward_lists", &t.forward_lists) &&
+            check_tuning(t) == SG_OK) {
+            *out = t;
+            const char *p = strstr(line, "\"ms\": ");
+            *ms = p ? atof(p + 6) : 0.0;
+            found = true;
+        }
+    }
+    fclose(f);
+    clear_error();
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, const sg_tuning &t, double ms)
+{
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f,
+            "{\"key\": \"%s\", \"walk_groups\": %d, \"direction_mode\": %d, \"direction_div\": %d, "
+            "\"tier1_keys\": %d, \"tier2_keys\": %d, \"landmarks\": %d, \"scc\": %d, \"forward_lists\": %d, "
+            "\"ms\": %.3f}\n",
+            key.c_str(), t.walk_groups, t.direction_mode, t.direction_div, t.tier1_keys, t.tier2_keys, t.landmarks,
+            t.scc, t.forward_lists, ms);
+    fclose(f);
+}
+
+struct Trial {
+    sg_graph *g;
+    int32_t R, k;
+    sg_cascade c;
+    uint64_t seed;
+    cudaStream_t st;
+    DBuf<int32_t> seeds;
+    DBuf<long long> gains;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<int32_t> ref_s, got_s;
+    std::vector<long long> ref_g, got_g;
+    int reps = 2;
+};
+
+// Fastest of `reps` timed selections (after one untimed) under knobs kn;
+// the seeds and gains must equal the first trial's.
+sg_status time_knobs(Trial &T, const Knobs &kn, double *ms)
+{
+    t_knobs = &kn;
+    struct Reset {
+        ~Reset() { t_knobs = nullptr; }
+    } reset;
+    float best = 1e30f;
+    for (int i = 0; i <= T.reps; ++i) {
+        SG_CUDA_TRY(cudaEventRecord(T.e0, T.st));
+        SG_TRY(select_impl(T.g, T.g->ws, T.R, T.k, T.c, T.seed, T.st, T.seeds.p,
+                           reinterpret_cast<int64_t *>(T.gains.p), nullptr, false));
+        SG_CUDA_TRY(cudaEventRecord(T.e1, T.st));
+        SG_CUDA_TRY(cudaEventSynchronize(T.e1));
+        float t = 0;
+        SG_CUDA_TRY(cudaEventElapsedTime(&t, T.e0, T.e1));
+        if (i > 0) best = std::min(best, t);
+    }
+    T.got_s.resize((size_t)T.k);
+    T.got_g.resize((size_t)T.k);
+    SG_CUDA_TRY(cudaMemcpy(T.got_s.data(), T.seeds.p, (size_t)T.k * 4, cudaMemcpyDeviceToHost));
+    SG_CUDA_TRY(cudaMemcpy(T.got_g.data(), T.gains.p, (size_t)T.k * 8, cudaMemcpyDeviceToHost));
+    if (T.ref_s.empty()) {
+        T.ref_s = T.got_s;
+        T.ref_g = T.got_g;
+    } else if (T.got_s != T.ref_s || T.got_g != T.ref_g) {
+        set_error("sg_autotune: a candidate setting changed the result (the knobs must not)");
+        return SG_EINTERNAL;
+    }
+    *ms = best;
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sg_status sg_get_tuning(sg_tuning *out)
+{
+    clear_error();
+    if (!out) {
+        set_error("sg_get_tuning: NULL output");
+        return SG_EINVAL;
+    }
+    *out = from_knobs(knobs());
+    return SG_OK;
+}
+
+sg_status sg_set_tuning(const sg_tuning *t)
+{
+    clear_error();
+    if (!t) {
+        set_error("sg_set_tuning: NULL tuning");
+        return SG_EINVAL;
+    }
+    SG_TRY(check_tuning(*t));
+    SG_TRY(sg_set_walk_groups(t->walk_groups));
+    SG_TRY(sg_set_direction(t->direction_mode, t->direction_div));
+    SG_TRY(sg_set_engine_limits(t->tier1_keys, t->tier2_keys));
+    SG_TRY(sg_set_landmarks(t->landmarks));
+    SG_TRY(sg_set_scc_condensation(t->scc));
+    return sg_set_forward_lists(t->forward_lists);
+}
+
+sg_status sg_autotune(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                      const char *cache_path, sg_tuning *out, double *out_ms)
+{
+    clear_error();
+    if (!g || !out) {
+        set_error("sg_autotune: NULL graph or output");
+        return SG_EINVAL;
+    }
+    SG_TRY(check_query(g, R, k));
+    Coins co;
+    SG_TRY(make_coins(c, seed, R, &co));
+    if (c.model == SG_UIC_UNDIRECTED) {
+        // the undirected variant runs per-snapshot union-find: no knob applies
+        *out = from_knobs(knobs());
+        if (out_ms) *out_ms = 0.0;
+        return SG_OK;
+    }
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::string key;
+    SG_TRY(tuning_key(g, c, co.W, st, &key));
+    double cached_ms = 0.0;
+    if (cache_path && cache_lookup(cache_path, key, out, &cached_ms)) {
+        if (out_ms) *out_ms = cached_ms;
+        return SG_OK;
+    }
+    Trial T;
+    T.g = g;
+    T.R = R;
+    T.k = k;
+    T.c = c;
+    T.seed = seed;
+    T.st = st;
+    sg_status rc = SG_OK;
+    if ((rc = dbuf_alloc(T.seeds, (size_t)k, st)) != SG_OK || (rc = dbuf_alloc(T.gains, (size_t)k, st)) != SG_OK) {
+        dbuf_free(T.seeds, st);
+        dbuf_free(T.gains, st);
+        return rc;
+    }
+    // the graph's own workspace is sized again with queues for every split
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    free_workspace(g->ws, st);
+    Knobs best = knobs();
+    best.walk_groups = 64;
+    {
+        t_knobs = &best;
+        rc = ensure_workspace(g, g->ws, co.W, k, st);
+        t_knobs = nullptr;
+    }
+    best = knobs();
+    double best_ms = 0.0;
+    if (rc == SG_OK && (cudaEventCreate(&T.e0) != cudaSuccess || cudaEventCreate(&T.e1) != cudaSuccess)) {
+        set_error("sg_autotune: cudaEventCreate failed");
+        rc = SG_ECUDA;
+    }
+    if (rc == SG_OK) rc = time_knobs(T, best, &best_ms);
+    // coordinate descent: each knob over its candidates, others held
+    auto try_values = [&](auto setter, const std::vector<int> &vals) {
+        for (int v : vals) {
+            if (rc != SG_OK) return;
+            Knobs cand = best;
+            setter(cand, v);
+            if (memcmp(&cand, &best, sizeof cand) == 0) continue;
+            double ms = 0.0;
+            rc = time_knobs(T, cand, &ms);
+            if (rc == SG_OK && ms < 0.99 * best_ms) {
+                best = cand;
+                best_ms = ms;
+            }
+        }
+    };
+    try_values([](Knobs &kn, int v) { kn.walk_groups = v; }, {8, 16, 32, 64});
+    try_values([](Knobs &kn, int v) {
+        kn.bu_mode = v == 0 ? 0 : 1;
+        kn.bu_div = v == 0 ? kn.bu_div : v;
+    }, {0, 2, 4, 16});
+    try_values([](Knobs &kn, int v) { kn.landmarks = v; }, {0, 4, 8});
+    try_values([](Knobs &kn, int v) { kn.scc = v; }, {0, 1});
+    try_values([](Knobs &kn, int v) { kn.t1_keys = v; }, {64, 128, 256});
+    try_values([](Knobs &kn, int v) { kn.t2_keys = v; }, {512, 1024, 2048});
+    try_values([](Knobs &kn, int v) { kn.fwd_lists = v; }, {0, 1});
+    if (T.e0) cudaEventDestroy(T.e0);
+    if (T.e1) cudaEventDestroy(T.e1);
+    dbuf_free(T.seeds, st);
+    dbuf_free(T.gains, st);
+    if (rc != SG_OK) return rc;
+    *out = from_knobs(best);
+    if (out_ms) *out_ms = best_ms;
+    if (cache_path) cache_store(cache_path, key, *out, best_ms);
+    return SG_OK;
+}
+
+}  // extern "C"
+
+namespace sgi {
+
+KnobScope::KnobScope(const sg_tuning *t)
+{
+    prev_ = t_knobs;
+    if (t) {
+        own_ = to_knobs(*t);
+        t_knobs = &own_;
+    }
+}
+
+KnobScope::~KnobScope() { t_knobs = prev_; }
+
+sg_status check_query_tuning(const sg_tuning *t) { return t ? check_tuning(*t) : SG_OK; }
+
+}  // namespace sgi

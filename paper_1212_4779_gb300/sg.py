@@ -31,9 +31,9 @@ EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg
            "sg_batch_capture", "sg_batch_launch", "sg_batch_free", "sg_server_create", "sg_server_submit",
            "sg_server_poll", "sg_server_counts", "sg_server_destroy",
            "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-           "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_set_walk_groups", "sg_set_direction", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_graph_trim", "sg_select",
+           "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_set_walk_groups", "sg_set_direction", "sg_set_scc_condensation", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_graph_trim", "sg_select",
            "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version",
-           "sg_debug_inject_flags", "sg_debug_set_wait_limit")
+           "sg_debug_inject_flags", "sg_debug_set_wait_limit", "sg_get_tuning", "sg_set_tuning", "sg_autotune")
 
 
 class SGError(RuntimeError):
@@ -68,10 +68,20 @@ class sg_stats(ctypes.Structure):
         return out
 
 
+class sg_tuning(ctypes.Structure):
+    _fields_ = [("walk_groups", ctypes.c_int32), ("direction_mode", ctypes.c_int32),
+                ("direction_div", ctypes.c_int32), ("tier1_keys", ctypes.c_int32), ("tier2_keys", ctypes.c_int32),
+                ("landmarks", ctypes.c_int32), ("scc", ctypes.c_int32), ("forward_lists", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
 class sg_query(ctypes.Structure):
     _fields_ = [("graph", ctypes.c_void_p), ("ws", ctypes.c_void_p), ("R", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("cascade", sg_cascade), ("seed", ctypes.c_uint64), ("out_seeds", ctypes.c_void_p),
-                ("out_gains", ctypes.c_void_p), ("status", ctypes.c_int)]
+                ("out_gains", ctypes.c_void_p), ("status", ctypes.c_int),
+                ("tuning", ctypes.POINTER(sg_tuning))]
 
 
 class sg_server_cfg(ctypes.Structure):
@@ -110,9 +120,14 @@ def lib() -> ctypes.CDLL:
         L.sg_set_forward_lists.argtypes = [i32]
         L.sg_set_walk_groups.argtypes = [i32]
         L.sg_set_direction.argtypes = [i32, i32]
+        L.sg_set_scc_condensation.argtypes = [i32]
         L.sg_graph_trim.argtypes = [P]
         L.sg_debug_inject_flags.argtypes = [i32]
         L.sg_debug_set_wait_limit.argtypes = [i64]
+        L.sg_get_tuning.argtypes = [ctypes.POINTER(sg_tuning)]
+        L.sg_set_tuning.argtypes = [ctypes.POINTER(sg_tuning)]
+        L.sg_autotune.argtypes = [P, i32, i32, sg_cascade, u64, P, ctypes.c_char_p, ctypes.POINTER(sg_tuning),
+                                  ctypes.POINTER(ctypes.c_double)]
         L.sg_spread.argtypes = [P, i32, sg_cascade, u64, P, i32, P, ctypes.POINTER(i64), ctypes.POINTER(u64)]
         L.sg_select_celf.argtypes = [P, i32, i32, sg_cascade, u64, P, P, P, ctypes.POINTER(i64), P]
         L.sg_argmax_noalloc.argtypes = [P, i64, P, P, P]
@@ -146,9 +161,10 @@ def lib() -> ctypes.CDLL:
         for name in ("sg_workspace_create", "sg_workspace_bytes", "sg_select_ws", "sg_select_batch",
                      "sg_batch_capture", "sg_batch_launch", "sg_server_create", "sg_server_submit",
                      "sg_server_poll", "sg_server_counts", "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
-                     "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_set_walk_groups", "sg_set_direction", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
+                     "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_set_walk_groups", "sg_set_direction", "sg_set_scc_condensation", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
                      "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr",
-                     "sg_debug_inject_flags", "sg_debug_set_wait_limit"):
+                     "sg_debug_inject_flags", "sg_debug_set_wait_limit", "sg_get_tuning", "sg_set_tuning",
+                     "sg_autotune"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -280,6 +296,11 @@ def sg_set_direction(mode: int = 1, divisor: int = 4):
     _check(lib().sg_set_direction(int(mode), int(divisor)))
 
 
+def sg_set_scc_condensation(enable: int = 1):
+    """Initial-gain sources inside a landmark's SCC skip that snapshot's walk (0: off)."""
+    _check(lib().sg_set_scc_condensation(int(enable)))
+
+
 def sg_set_walk_groups(groups: int = 8):
     """Blocks per 64-snapshot word of the forward and landmark walks (8/16/32/64)."""
     _check(lib().sg_set_walk_groups(int(groups)))
@@ -333,6 +354,26 @@ def sg_load_graph_coo(n, m, src, dst, stream=None):
 def sg_debug_inject_flags(flags: int):
     """Testing hook: the next query plants `flags` into its device flags."""
     _check(lib().sg_debug_inject_flags(int(flags)))
+
+
+def sg_get_tuning():
+    t = sg_tuning()
+    _check(lib().sg_get_tuning(ctypes.byref(t)))
+    return t
+
+
+def sg_set_tuning(t):
+    _check(lib().sg_set_tuning(ctypes.byref(t)))
+
+
+def sg_autotune(h, R, k, model="uic", p=0.0, seed=0, stream=None, cache_path=None):
+    """Fastest knobs for one query (results unchanged); returns (sg_tuning, ms per select)."""
+    t = sg_tuning()
+    ms = ctypes.c_double(0.0)
+    _check(lib().sg_autotune(h, int(R), int(k), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                             _stream_ptr(stream), cache_path.encode() if cache_path else None, ctypes.byref(t),
+                             ctypes.byref(ms)))
+    return t, ms.value
 
 
 def sg_debug_set_wait_limit(polls: int):
@@ -436,11 +477,17 @@ def sg_select_ws(h, w, R, k, model, p, seed, out_seeds, out_gains, stream=None, 
 
 
 def _queries(items):
-    """items: (graph handle, workspace or None, R, k, model, p, seed, seeds_out, gains_out)."""
+    """items: (graph handle, workspace or None, R, k, model, p, seed, seeds_out, gains_out[, sg_tuning])."""
     arr = (sg_query * len(items))()
-    for i, (h, w, R, k, model, p, seed, so, go) in enumerate(items):
+    keep = []
+    for i, it in enumerate(items):
+        h, w, R, k, model, p, seed, so, go = it[:9]
+        tun = it[9] if len(it) > 9 else None
         arr[i] = sg_query(h, w, int(R), int(k), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
-                          ctypes.c_void_p(_addr(so)[0]), ctypes.c_void_p(_addr(go)[0]), 0)
+                          ctypes.c_void_p(_addr(so)[0]), ctypes.c_void_p(_addr(go)[0]), 0,
+                          ctypes.pointer(tun) if tun is not None else None)
+        keep.append(tun)
+    arr._tunings = keep  # alive as long as the array
     return arr
 
 

@@ -96,6 +96,18 @@ def test_setters_validate_without_gpu(libpath):
     assert L.sg_set_direction(3, 4) == sg.SG_EINVAL
     assert L.sg_set_direction(1, 0) == sg.SG_EINVAL
     assert L.sg_set_direction(1, 4) == sg.SG_OK
+    t0 = sg.sg_get_tuning()
+    bad = sg.sg_tuning(**dict(t0.as_dict(), walk_groups=12))
+    assert L.sg_set_tuning(ctypes.byref(bad)) == sg.SG_EINVAL
+    bad = sg.sg_tuning(**dict(t0.as_dict(), landmarks=9))
+    assert L.sg_set_tuning(ctypes.byref(bad)) == sg.SG_EINVAL
+    t1 = sg.sg_tuning(**dict(t0.as_dict(), walk_groups=32, direction_mode=0, scc=0))
+    sg.sg_set_tuning(t1)
+    assert sg.sg_get_tuning().as_dict() == t1.as_dict()
+    sg.sg_set_tuning(t0)
+    assert sg.sg_get_tuning().as_dict() == t0.as_dict()
+    assert L.sg_set_scc_condensation(2) == sg.SG_EINVAL
+    assert L.sg_set_scc_condensation(1) == sg.SG_OK
     assert L.sg_set_walk_groups(12) == sg.SG_EINVAL
     assert L.sg_set_walk_groups(8) == sg.SG_OK
     assert L.sg_debug_set_wait_limit(-1) == sg.SG_EINVAL

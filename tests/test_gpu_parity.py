@@ -129,6 +129,40 @@ def limits(sg):
     sg.sg_set_forward_lists(1)
     sg.sg_set_walk_groups(8)
     sg.sg_set_direction(1, 4)
+    sg.sg_set_scc_condensation(1)
+
+
+@pytest.mark.parametrize("t1,t2", [(256, 4096), (2, 16)])
+def test_scc_condensation_is_exact_and_skips_work(sg, limits, t1, t2):
+    """UIC 0.05 on a Chung-Lu graph with a giant strongly connected component
+    holding the hubs: sources inside a landmark's component skip those
+    snapshots' walks.  With condensation on and off the initial gains,
+    seeds, gains and counters equal the oracle's, and on expands fewer
+    elements; also on the named workloads."""
+    n, s, d = inputs.chung_lu_undirected(4000, 30000, 2.5, 15.0, 77)
+    g, o = _both(sg, n, s, d, "uic", 0.05)
+    ref = o.select(128, 8, 99, mode=oracle.DU, want_init=True)
+    limits(t1, t2)
+    elems = {}
+    for on in (0, 1):
+        sg.sg_set_scc_condensation(on)
+        s_gpu, ed = g.init_gains(128, "uic", 0.05, 99)
+        assert np.array_equal(s_gpu, ref["s_init"]) and ed == int(ref["counters"][0])
+        res = g.select(128, 8, "uic", 0.05, 99, stats=True)
+        assert np.array_equal(res.seeds, ref["seeds"]) and np.array_equal(res.gains, ref["gains"])
+        got = [res.stats["init_edges"], res.stats["fwd_edges"], res.stats["rev_edges"]]
+        assert got == [int(x) for x in ref["counters"]]
+        elems[on] = sum(res.stats["work_elems"][0])
+    assert elems[1] < elems[0], elems
+    for name in ("cl15k_wic", "cl15k_uic0.01"):
+        wl = inputs.workload(name)
+        n, s, d = wl.graph()
+        g, o = _both(sg, n, s, d, wl.model, wl.p)
+        ref = o.select(wl.R, 10, wl.seed, mode=oracle.DU, want_init=True)
+        for on in (0, 1):
+            sg.sg_set_scc_condensation(on)
+            s_gpu, ed = g.init_gains(wl.R, wl.model, wl.p, wl.seed)
+            assert np.array_equal(s_gpu, ref["s_init"]) and ed == int(ref["counters"][0])
 
 
 @pytest.mark.parametrize("mode,div", [(0, 4), (1, 4), (1, 64), (2, 1)])
