@@ -215,7 +215,7 @@ sg_status sg_set_direction(int32_t mode, int32_t divisor);
 /* Blocks per 64-snapshot word of the level-synchronous walks (the forward
  * dynamic update's walk from each new seed and the landmark walks of the
  * initial gains): each block owns 64/groups of the word's snapshot bits.
- * 8, 16, 32 or 64 (default 8); more blocks spread one walk over more SMs.
+ * 8, 16, 32 or 64 (default 32); more blocks spread one walk over more SMs.
  * Workspaces size their level queues for max(8, groups) at creation (4
  * bytes per node, word and block, twice); a query on an older workspace
  * uses at most what it was sized for.  Results do not depend on it.
@@ -332,6 +332,9 @@ sg_status sg_select_ws(sg_graph *g, sg_workspace *ws, int32_t R, int32_t k, sg_c
  *   landmarks       0..8 (sg_set_landmarks)
  *   scc             0/1 (sg_set_scc_condensation)
  *   forward_lists   0/1 (sg_set_forward_lists)
+ *   word_major      initial-gain task order: 1 (default) all of one 64-snapshot
+ *                   word's sources before the next word's, so the tasks in
+ *                   flight share that word's caches in L2; 0 source by source
  * The slice width is fixed at 64 snapshots (one 64-bit word per node and
  * task) and is not a knob. */
 typedef struct {
@@ -343,6 +346,7 @@ typedef struct {
     int32_t landmarks;
     int32_t scc;
     int32_t forward_lists;
+    int32_t word_major;
 } sg_tuning;
 
 /* The process-wide knobs (what the sg_set_* calls set) / set all of them.

@@ -87,7 +87,8 @@ sg_status run_poison(const sg_graph *g, sg_workspace &ws, int32_t *seeds, long l
 int g_snapshot_lists = 1;
 int g_mask_cache = 0;
 int g_fwd_lists = 1;
-int g_walk_groups = 8;
+int g_walk_groups = 32;
+int g_word_major = 1;
 
 Knobs knobs()
 {
@@ -101,6 +102,7 @@ Knobs knobs()
     k.landmarks = g_landmarks;
     k.scc = g_scc;
     k.fwd_lists = g_fwd_lists;
+    k.word_major = g_word_major;
     return k;
 }
 

@@ -309,6 +309,7 @@ extern int g_bu_div;
 // nonzero: initial-gain sources inside a landmark's strongly connected
 // component skip those snapshots' walks (the landmark credit counts them)
 extern int g_scc;
+extern int g_word_major;
 // The tunable knobs one query runs with (none changes a result).
 struct Knobs {
     int walk_groups;  // blocks per word of the forward and landmark walks
@@ -319,6 +320,7 @@ struct Knobs {
     int landmarks;    // landmarks for the initial gains (0 .. 8)
     int scc;          // SCC condensation of initial-gain sources
     int fwd_lists;    // forward per-snapshot live lists
+    int word_major;   // initial-gain tasks numbered word-major (1) or source-major (0)
 };
 // The calling thread's current query knobs: the per-query tuning it was
 // given (t_knobs, set for the duration of one query) or else the

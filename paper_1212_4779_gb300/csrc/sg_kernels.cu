@@ -320,6 +320,7 @@ struct EngineArgs {
     int bu_mode;            // level-synchronous walks: 0 top-down only, 1 switch by frontier size, 2 bottom-up after level 0
     int bu_div;             // mode 1: a level runs bottom-up when its frontier holds more than n / bu_div nodes
     int scc;                // initial gains: condense sources inside a landmark's strongly connected component
+    int word_major;         // initial-gain task t: 1 -> (source t mod n, word t / n), 0 -> (t / W, t mod W)
 };
 
 
@@ -414,6 +415,20 @@ __device__ __forceinline__ uint64_t lmk_scc_bits(const EngineArgs &a, int word, 
     return m;
 }
 
+// Source and word of initial-gain task t.  Word-major numbering runs all of
+// one word's tasks before the next word's, so the tasks in flight share
+// that word's row descriptors, lists and landmark records in L2.
+__device__ __forceinline__ void init_task(const EngineArgs &a, long long t, int &x0, int &word)
+{
+    if (a.word_major) {
+        word = (int)(t / a.g.n);
+        x0 = (int)(t - (long long)word * a.g.n);
+    } else {
+        x0 = (int)(t / a.co.W);
+        word = (int)(t - (long long)x0 * a.co.W);
+    }
+}
+
 // ============================================================ warp engine
 
 struct WTab {
@@ -497,8 +512,7 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
     int x0 = 0, word;
     uint32_t rs;
     if (TASK == TASK_INIT) {
-        x0 = (int)(t / co.W);
-        word = (int)(t - (long long)x0 * co.W);
+        init_task(a, t, x0, word);
         rs = (uint32_t)word * 64u;
         int own = -1;
 #pragma unroll
@@ -1516,8 +1530,7 @@ __global__ void __launch_bounds__(CoopShape<TAB, LOGC>::T, CoopShape<TAB, LOGC>:
         }
         __syncthreads();
         if (TASK == TASK_INIT) {
-            x0 = (int)(t / a.co.W);
-            word = (int)(t - (long long)x0 * a.co.W);
+            init_task(a, t, x0, word);
             rs = (uint32_t)word * 64u;
             if (tid < MAX_LMK)
                 c.xbits[tid] = tid < a.lmk_k ? lmk_reaches(a, word, x0, tid) & word_mask(word, a.co.R) : 0ull;
@@ -2396,6 +2409,7 @@ EngineArgs engine_args(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
     a.bu_mode = kn.bu_mode;
     a.bu_div = kn.bu_div;
     a.scc = kn.scc;
+    a.word_major = kn.word_major;
     return a;
 }
 

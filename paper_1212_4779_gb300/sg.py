@@ -71,7 +71,8 @@ class sg_stats(ctypes.Structure):
 class sg_tuning(ctypes.Structure):
     _fields_ = [("walk_groups", ctypes.c_int32), ("direction_mode", ctypes.c_int32),
                 ("direction_div", ctypes.c_int32), ("tier1_keys", ctypes.c_int32), ("tier2_keys", ctypes.c_int32),
-                ("landmarks", ctypes.c_int32), ("scc", ctypes.c_int32), ("forward_lists", ctypes.c_int32)]
+                ("landmarks", ctypes.c_int32), ("scc", ctypes.c_int32), ("forward_lists", ctypes.c_int32),
+                ("word_major", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
@@ -301,7 +302,7 @@ def sg_set_scc_condensation(enable: int = 1):
     _check(lib().sg_set_scc_condensation(int(enable)))
 
 
-def sg_set_walk_groups(groups: int = 8):
+def sg_set_walk_groups(groups: int = 32):
     """Blocks per 64-snapshot word of the forward and landmark walks (8/16/32/64)."""
     _check(lib().sg_set_walk_groups(int(groups)))
 

@@ -109,7 +109,7 @@ def test_setters_validate_without_gpu(libpath):
     assert L.sg_set_scc_condensation(2) == sg.SG_EINVAL
     assert L.sg_set_scc_condensation(1) == sg.SG_OK
     assert L.sg_set_walk_groups(12) == sg.SG_EINVAL
-    assert L.sg_set_walk_groups(8) == sg.SG_OK
+    assert L.sg_set_walk_groups(32) == sg.SG_OK
     assert L.sg_debug_set_wait_limit(-1) == sg.SG_EINVAL
     assert L.sg_debug_set_wait_limit(0) == sg.SG_OK  # restores the default; no query runs here
 
