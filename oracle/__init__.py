@@ -61,15 +61,19 @@ def _load():
         lib.or_thresholds.restype = cint
         lib.or_thresholds.argtypes = [cint, dbl, i64, P, P, P]
         lib.or_select.restype = cint
-        lib.or_select.argtypes = [cint, i64, P, P, P, i32, i32, u64, cint, P, P, P, P, P, P]
+        lib.or_select.argtypes = [cint, i64, P, P, P, i32, i32, u64, cint, P, P, P, P, P, P, P]
         lib.or_init_gains.restype = cint
-        lib.or_init_gains.argtypes = [i64, P, P, P, i32, i32, u64, cint, P, P, P]
+        lib.or_init_gains.argtypes = [i64, P, P, P, i32, i32, u64, cint, P, P, P, P]
         lib.or_spread.restype = i64
-        lib.or_spread.argtypes = [i64, P, P, P, i32, u64, i32, P, cint, P, P]
+        lib.or_spread.argtypes = [i64, P, P, P, i32, u64, i32, P, cint, P, P, P]
         lib.or_reach_sums.restype = cint
-        lib.or_reach_sums.argtypes = [i64, P, P, P, i32, u64, i32, P, cint, P, P, P]
+        lib.or_reach_sums.argtypes = [i64, P, P, P, i32, u64, i32, P, cint, P, P, P, P]
         lib.or_live_masks.restype = cint
-        lib.or_live_masks.argtypes = [i64, P, i32, u64, P, P]
+        lib.or_live_masks.argtypes = [i64, P, i32, u64, P, P, P]
+        lib.or_live_range.restype = cint
+        lib.or_live_range.argtypes = [u64, ctypes.c_uint32, u64, u64, u64]
+        lib.or_lt_intervals.restype = cint
+        lib.or_lt_intervals.argtypes = [i64, P, P, P, P, P]
         lib.or_coupled_ids.restype = cint
         lib.or_coupled_ids.argtypes = [i64, P, P, P]
         _lib = lib
@@ -101,13 +105,19 @@ def live(seed: int, r: int, e: int, thr: int) -> bool:
     return bool(_load().or_live(seed, r, e, thr))
 
 
+def live_range(seed: int, r: int, key: int, lo: int, hi: int) -> bool:
+    return bool(_load().or_live_range(seed, r, key, lo, hi))
+
+
 class Graph:
     """Canonical graph (CSR) with per-arc thresholds for one cascade model."""
 
     def __init__(self, n, src, dst, model="uic", p=0.0):
-        """model: "uic", "wic", or "uic_undirected" (uniform cascade on a
+        """model: "uic", "wic", "uic_undirected" (uniform cascade on a
         symmetric graph with one coin per undirected edge: both arcs hash the
-        lower of their two canonical arc ids)."""
+        lower of their two canonical arc ids), or "lt" (the linear threshold
+        model's live-edge form with weights 1/d_v: each node keeps at most one
+        in-arc, chosen by one draw per node and snapshot)."""
         lib = _load()
         src = np.ascontiguousarray(src, dtype=np.int32)
         dst = np.ascontiguousarray(dst, dtype=np.int32)
@@ -128,6 +138,12 @@ class Graph:
         _check(lib.or_thresholds(WIC if model == "wic" else UIC, self.p, self.n, _ptr(self.rp),
                                  _ptr(self.col), _ptr(self.thr)), "thresholds")
         self.cid = None
+        self.lo = None
+        if model == "lt":
+            self.cid = np.zeros(max(1, self.m), dtype=np.int64)
+            self.lo = np.zeros(max(1, self.m), dtype=np.uint64)
+            _check(lib.or_lt_intervals(self.n, _ptr(self.rp), _ptr(self.col), _ptr(self.cid), _ptr(self.lo),
+                                       _ptr(self.thr)), "lt_intervals")
         if model == "uic_undirected":
             self.cid = np.zeros(max(1, self.m), dtype=np.int64)
             if lib.or_coupled_ids(self.n, _ptr(self.rp), _ptr(self.col), _ptr(self.cid)) != 0:
@@ -135,6 +151,9 @@ class Graph:
 
     def _cid(self):
         return _ptr(self.cid) if self.cid is not None else None
+
+    def _lo(self):
+        return _ptr(self.lo) if self.lo is not None else None
 
     def select(self, R, k, seed, mode=DU, nthreads=None, want_init=False, want_hist=False):
         """Greedy seeds by Algorithm 1 (LITERAL/COVER) or Algorithm 2 (DU).
@@ -148,7 +167,7 @@ class Graph:
         rc = lib.or_select(mode, self.n, _ptr(self.rp), _ptr(self.col), _ptr(self.thr), R, k,
                            ctypes.c_uint64(seed), _threads(nthreads), _ptr(seeds), _ptr(gains),
                            _ptr(s_init) if want_init else None, _ptr(s_hist) if want_hist else None,
-                           _ptr(cnt), self._cid())
+                           _ptr(cnt), self._cid(), self._lo())
         _check(rc, "select")
         out = dict(seeds=seeds, gains=gains, counters=cnt[:3], evals=int(cnt[3]))
         if want_init:
@@ -164,7 +183,8 @@ class Graph:
         s = np.zeros(self.n, dtype=np.int64)
         ed = ctypes.c_uint64(0)
         _check(lib.or_init_gains(self.n, _ptr(self.rp), _ptr(self.col), _ptr(self.thr), r0, r1,
-                                 ctypes.c_uint64(seed), _threads(nthreads), _ptr(s), ctypes.byref(ed), self._cid()),
+                                 ctypes.c_uint64(seed), _threads(nthreads), _ptr(s), ctypes.byref(ed), self._cid(),
+                                 self._lo()),
                "init_gains")
         return s, int(ed.value)
 
@@ -175,7 +195,7 @@ class Graph:
         ed = ctypes.c_uint64(0)
         v = _load().or_spread(self.n, _ptr(self.rp), _ptr(self.col), _ptr(self.thr), R,
                               ctypes.c_uint64(seed), S.size, _ptr(S), _threads(nthreads), ctypes.byref(ed),
-                              self._cid())
+                              self._cid(), self._lo())
         if v < 0:
             raise OracleError(f"spread: oracle status {v}")
         return (int(v), int(ed.value)) if want_edges else int(v)
@@ -187,7 +207,7 @@ class Graph:
         ed = ctypes.c_uint64(0)
         _check(_load().or_reach_sums(self.n, _ptr(self.rp), _ptr(self.col), _ptr(self.thr), R,
                                      ctypes.c_uint64(seed), vs.size, _ptr(vs), _threads(nthreads),
-                                     _ptr(out), ctypes.byref(ed), self._cid()), "reach_sums")
+                                     _ptr(out), ctypes.byref(ed), self._cid(), self._lo()), "reach_sums")
         return out, int(ed.value)
 
     def live_masks(self, R, seed):
@@ -195,5 +215,5 @@ class Graph:
         W = (R + 63) // 64
         masks = np.zeros((max(1, self.m), W), dtype=np.uint64)
         _check(_load().or_live_masks(self.m, _ptr(self.thr), R, ctypes.c_uint64(seed), _ptr(masks),
-                                     self._cid()), "live_masks")
+                                     self._cid(), self._lo()), "live_masks")
         return masks[: self.m]

@@ -36,8 +36,12 @@ def canonical_arcs(src, dst):
 
 
 def coin_ids(arcs, model):
-    """The id each arc's coin hashes: its own index, or for the undirected
-    variant ("uic_undirected") the smaller index of the arc and its reverse."""
+    """The value each arc's coin hashes: its own index; for the undirected
+    variant ("uic_undirected") the smaller index of the arc and its reverse;
+    for the linear threshold model ("lt") the arc's destination (one draw
+    per node decides which in-arc it keeps)."""
+    if model == "lt":
+        return [v for _, v in arcs]
     if model != "uic_undirected":
         return list(range(len(arcs)))
     index = {a: i for i, a in enumerate(arcs)}
@@ -46,6 +50,25 @@ def coin_ids(arcs, model):
         if (v, u) not in index:
             raise ValueError("uic_undirected needs a symmetric graph")
         out.append(min(i, index[(v, u)]))
+    return out
+
+
+def intervals(n, arcs, model, p=0.0):
+    """Kept interval [lo, hi) of each arc's 32-bit draw: [0, thr) for the
+    cascades; for "lt", node v's in-arcs in order of source own consecutive
+    intervals of width floor(2^32 / indeg(v)) (Kempe et al.'s live-edge
+    linear threshold model with weights 1/indeg)."""
+    if model != "lt":
+        return [(0, t) for t in thresholds(n, arcs, model, p)]
+    indeg = [0] * n
+    for _, v in arcs:
+        indeg[v] += 1
+    seen = [0] * n
+    out = []
+    for _, v in arcs:  # canonical order: sources ascending
+        w = (1 << 32) // indeg[v]
+        out.append((seen[v] * w, (seen[v] + 1) * w))
+        seen[v] += 1
     return out
 
 
@@ -62,6 +85,11 @@ def thresholds(n, arcs, model, p=0.0):
 
 def coin(seed, r, e, thr) -> bool:
     return (splitmix64((seed ^ (r << 40) ^ e) & MASK64) >> 32) < thr
+
+
+def coin_range(seed, r, key, lo, hi) -> bool:
+    h = splitmix64((seed ^ (r << 40) ^ key) & MASK64) >> 32
+    return lo <= h < hi
 
 
 def closure(n, live_arcs):
@@ -84,12 +112,12 @@ class Brute:
     def __init__(self, n, src, dst, model, p, R, seed):
         self.n = n
         self.arcs = canonical_arcs(src, dst)
-        self.thr = thresholds(n, self.arcs, model, p)
+        iv = intervals(n, self.arcs, model, p)
         cid = coin_ids(self.arcs, model)
         self.R = R
         self.reach = []
         for r in range(R):
-            live = [a for e, a in enumerate(self.arcs) if coin(seed, r, cid[e], self.thr[e])]
+            live = [a for e, a in enumerate(self.arcs) if coin_range(seed, r, cid[e], *iv[e])]
             self.reach.append(closure(n, live))
 
     def f(self, S) -> int:
@@ -141,6 +169,47 @@ def exact_spread(n, src, dst, model, p, S):
         live = [a for e, a in enumerate(arcs) if world >> slot[cid[e]] & 1]
         if prob == 0:
             continue
+        reach = closure(n, live)
+        cov = 0
+        for v in S:
+            cov |= reach[v]
+        c = bin(cov).count("1")
+        mean += prob * c
+        second += prob * c * c
+    return mean, second - mean * mean
+
+
+def exact_spread_lt(n, src, dst, S):
+    """Exact I(S) and Var(|R(S)|) under the live-edge linear threshold model
+    with weights 1/indeg: every node independently keeps one of its d in-arcs,
+    each with probability w/2^32 (w = floor(2^32/d), the discretised weight
+    the hash realises), or none with the remaining probability; enumerates
+    every combination of choices with exact rationals."""
+    arcs = canonical_arcs(src, dst)
+    ins = [[] for _ in range(n)]
+    for u, v in arcs:
+        ins[v].append(u)
+    options = []
+    for v in range(n):
+        d = len(ins[v])
+        if d == 0:
+            options.append([(None, Fraction(1))])
+            continue
+        w = Fraction((1 << 32) // d, 1 << 32)
+        opts = [(u, w) for u in ins[v]]
+        rest = 1 - d * w
+        if rest:
+            opts.append((None, rest))
+        options.append(opts)
+    mean = Fraction(0)
+    second = Fraction(0)
+    for choice in itertools.product(*options):
+        prob = Fraction(1)
+        live = []
+        for v, (u, q) in enumerate(choice):
+            prob *= q
+            if u is not None:
+                live.append((u, v))
         reach = closure(n, live)
         cov = 0
         for v in S:

@@ -76,6 +76,16 @@ int or_live(uint64_t seed, uint32_t r, uint64_t e, uint64_t thr)
     return hi < thr;
 }
 
+/* The general form: the hash of `key` in snapshot r keeps the arc iff its
+ * high 32 bits fall in [lo, hi).  The cascade models take lo = 0 and
+ * key = the arc id (or_live); the linear threshold model hashes the arc's
+ * destination and gives each of its in-arcs an interval of its own. */
+int or_live_range(uint64_t seed, uint32_t r, uint64_t key, uint64_t lo, uint64_t hi)
+{
+    uint64_t h = or_splitmix64(seed ^ ((uint64_t)r << 40) ^ key) >> 32;
+    return lo <= h && h < hi;
+}
+
 /* ------------------------------------------------------------- the graph */
 
 static int cmp_u64(const void *a, const void *b)
@@ -195,8 +205,47 @@ int or_coupled_ids(int64_t n, const int64_t *rp, const int32_t *col, int64_t *ci
  * undirected snapshot). */
 static uint64_t coin_of(const int64_t *cid, int64_t e) { return cid ? (uint64_t)cid[e] : (uint64_t)e; }
 
+/* Arc e kept in snapshot r: key coin_of(cid, e), interval [lo[e], thr[e])
+ * (lo NULL: [0, thr[e])). */
+static int arc_live(uint64_t seed, uint32_t r, int64_t e, const uint64_t *thr, const int64_t *cid,
+                    const uint64_t *lo)
+{
+    return or_live_range(seed, r, coin_of(cid, e), lo ? lo[e] : 0, thr[e]);
+}
+
+/* Linear threshold model in its live-edge form (Kempe, Kleinberg and Tardos,
+ * KDD 2003): every node v keeps at most one of its in-arcs, arc (u, v) with
+ * probability b(u, v), none with probability 1 - sum_u b(u, v); here
+ * b(u, v) = 1/d_v with d_v the in-degree, the weights of the weighted
+ * cascade (Section 3.4.1).  Discretised like the cascade coins: v's draw in
+ * snapshot r is the high 32 bits of splitmix64(seed XOR (r << 40) XOR v);
+ * v's in-arcs, in order of source (canonical arc order), own the intervals
+ * [j w, (j + 1) w), w = floor(2^32 / d_v), j = 0 .. d_v - 1; the arc whose
+ * interval holds the draw is kept (none when the draw is >= d_v w).  Writes
+ * key[e] = destination, lo[e] = j w, hi[e] = (j + 1) w. */
+int or_lt_intervals(int64_t n, const int64_t *rp, const int32_t *col, int64_t *key, uint64_t *lo, uint64_t *hi)
+{
+    int64_t m = rp[n];
+    int64_t *indeg = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *seen = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    if (!indeg || !seen) { free(indeg); free(seen); return OR_ENOMEM; }
+    for (int64_t e = 0; e < m; e++) indeg[col[e]]++;
+    for (int64_t u = 0; u < n; u++)
+        for (int64_t e = rp[u]; e < rp[u + 1]; e++) {  /* sources in increasing order */
+            int32_t v = col[e];
+            uint64_t w = (1ULL << 32) / (uint64_t)indeg[v];
+            int64_t j = seen[v]++;
+            key[e] = v;
+            lo[e] = (uint64_t)j * w;
+            hi[e] = (uint64_t)(j + 1) * w;
+        }
+    free(indeg); free(seen);
+    return OR_OK;
+}
+
 static or_snaps *snaps_build(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
-                             int32_t r0, int32_t R, uint64_t seed, int nthreads, const int64_t *cid)
+                             int32_t r0, int32_t R, uint64_t seed, int nthreads, const int64_t *cid,
+                             const uint64_t *lo)
 {
     or_snaps *S = (or_snaps *)calloc(1, sizeof(or_snaps));
     if (!S) return NULL;
@@ -219,7 +268,7 @@ static or_snaps *snaps_build(int64_t n, const int64_t *rp, const int32_t *col, c
         int64_t kept = 0;
         for (int64_t u = 0; u < n; u++)
             for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
-                keep[e] = (uint8_t)or_live(seed, (uint32_t)(r0 + r), coin_of(cid, e), thr[e]);
+                keep[e] = (uint8_t)arc_live(seed, (uint32_t)(r0 + r), e, thr, cid, lo);
                 if (keep[e]) { orp[u + 1]++; irp[col[e] + 1]++; kept++; }
             }
         for (int64_t v = 0; v < n; v++) { orp[v + 1] += orp[v]; irp[v + 1] += irp[v]; }
@@ -449,10 +498,10 @@ static void heap_pop(or_heap *h, int64_t *b, int32_t *v, int32_t *stamp)
  * number of marginal-gain evaluations after the initial gains. */
 int or_select(int mode, int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
               int32_t R, int32_t k, uint64_t seed, int nthreads, int32_t *seeds, int64_t *gains,
-              int64_t *s_init, int64_t *s_hist, uint64_t *counters, const int64_t *cid)
+              int64_t *s_init, int64_t *s_hist, uint64_t *counters, const int64_t *cid, const uint64_t *lo)
 {
     if (n < 1 || R < 1 || k < 1 || k > n) return OR_EINVAL;
-    or_snaps *S = snaps_build(n, rp, col, thr, 0, R, seed, nthreads, cid);
+    or_snaps *S = snaps_build(n, rp, col, thr, 0, R, seed, nthreads, cid, lo);
     if (!S) return OR_ENOMEM;
     int rc = OR_OK;
     int64_t *s = (int64_t *)calloc((size_t)n, sizeof(int64_t));
@@ -589,10 +638,10 @@ done:
  * initial gains. */
 int or_init_gains(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
                   int32_t r0, int32_t r1, uint64_t seed, int nthreads, int64_t *s,
-                  uint64_t *init_edges, const int64_t *cid)
+                  uint64_t *init_edges, const int64_t *cid, const uint64_t *lo)
 {
     if (n < 1 || r0 < 0 || r1 <= r0) return OR_EINVAL;
-    or_snaps *S = snaps_build(n, rp, col, thr, r0, r1 - r0, seed, nthreads, cid);
+    or_snaps *S = snaps_build(n, rp, col, thr, r0, r1 - r0, seed, nthreads, cid, lo);
     if (!S) return OR_ENOMEM;
     int rc = init_gains(S, rp, nthreads, s, init_edges);
     snaps_free(S);
@@ -608,7 +657,8 @@ int or_init_gains(int64_t n, const int64_t *rp, const int32_t *col, const uint64
  * mark/queue: n-entry scratch, mark zeroed by the caller. */
 static int64_t reach_fly(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
                          uint64_t seed, uint32_t r, int32_t nsrc, const int32_t *src,
-                         uint8_t *mark, int32_t *queue, uint64_t *edges, const int64_t *cid)
+                         uint8_t *mark, int32_t *queue, uint64_t *edges, const int64_t *cid,
+                         const uint64_t *lo)
 {
     int64_t head = 0, tail = 0;
     for (int32_t i = 0; i < nsrc; i++)
@@ -619,7 +669,7 @@ static int64_t reach_fly(int64_t n, const int64_t *rp, const int32_t *col, const
         for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
             int32_t x = col[e];
             if (mark[x]) continue;
-            if (!or_live(seed, r, coin_of(cid, e), thr[e])) continue;
+            if (!arc_live(seed, r, e, thr, cid, lo)) continue;
             mark[x] = 1;
             queue[tail++] = x;
         }
@@ -634,7 +684,7 @@ static int64_t reach_fly(int64_t n, const int64_t *rp, const int32_t *col, const
  * NULL) gets the snapshot-edge count sum_r sum_{u in R(G'_r, S)} outdeg(u). */
 int64_t or_spread(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
                   int32_t R, uint64_t seed, int32_t nS, const int32_t *Sset, int nthreads,
-                  uint64_t *edges, const int64_t *cid)
+                  uint64_t *edges, const int64_t *cid, const uint64_t *lo)
 {
     int64_t total = 0;
     uint64_t ed = 0;
@@ -652,7 +702,7 @@ int64_t or_spread(int64_t n, const int64_t *rp, const int32_t *col, const uint64
 #pragma omp for schedule(dynamic, 1)
 #endif
             for (int32_t r = 0; r < R; r++)
-                total += reach_fly(n, rp, col, thr, seed, (uint32_t)r, nS, Sset, mark, queue, &ed, cid);
+                total += reach_fly(n, rp, col, thr, seed, (uint32_t)r, nS, Sset, mark, queue, &ed, cid, lo);
         }
         free(mark); free(queue);
     }
@@ -665,7 +715,7 @@ int64_t or_spread(int64_t n, const int64_t *rp, const int32_t *col, const uint64
  * of those sources. */
 int or_reach_sums(int64_t n, const int64_t *rp, const int32_t *col, const uint64_t *thr,
                   int32_t R, uint64_t seed, int32_t nv, const int32_t *v, int nthreads,
-                  int64_t *out, uint64_t *edges, const int64_t *cid)
+                  int64_t *out, uint64_t *edges, const int64_t *cid, const uint64_t *lo)
 {
     uint64_t ed = 0;
     int failed = 0;
@@ -684,7 +734,7 @@ int or_reach_sums(int64_t n, const int64_t *rp, const int32_t *col, const uint64
             for (int32_t i = 0; i < nv; i++) {
                 int64_t acc = 0;
                 for (int32_t r = 0; r < R; r++)
-                    acc += reach_fly(n, rp, col, thr, seed, (uint32_t)r, 1, v + i, mark, queue, &ed, cid);
+                    acc += reach_fly(n, rp, col, thr, seed, (uint32_t)r, 1, v + i, mark, queue, &ed, cid, lo);
                 out[i] = acc;
             }
         }
@@ -697,7 +747,7 @@ int or_reach_sums(int64_t n, const int64_t *rp, const int32_t *col, const uint64
 /* Coins as 64-snapshot words: bit b of masks[e*W + w] is the coin of arc e
  * in snapshot 64w+b, for snapshots < R (higher bits of the last word 0). */
 int or_live_masks(int64_t m, const uint64_t *thr, int32_t R, uint64_t seed, uint64_t *masks,
-                  const int64_t *cid)
+                  const int64_t *cid, const uint64_t *lo)
 {
     int32_t W = (R + 63) / 64;
     for (int64_t e = 0; e < m; e++)
@@ -705,7 +755,7 @@ int or_live_masks(int64_t m, const uint64_t *thr, int32_t R, uint64_t seed, uint
             uint64_t word = 0;
             for (int32_t b = 0; b < 64; b++) {
                 int32_t r = 64 * w + b;
-                if (r < R && or_live(seed, (uint32_t)r, coin_of(cid, e), thr[e])) word |= 1ULL << b;
+                if (r < R && arc_live(seed, (uint32_t)r, e, thr, cid, lo)) word |= 1ULL << b;
             }
             masks[e * W + w] = word;
         }

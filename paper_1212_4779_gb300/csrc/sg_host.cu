@@ -565,13 +565,14 @@ sg_status ensure_wic(sg_graph *g, cudaStream_t st)
     return SG_OK;
 }
 
-// Tier-3 slot memory: 12 KB per node, between 64 MB and 16 GiB.
+// Tier-3 slot memory: 4 KB per node per resident dense block per SM (12 KB
+// at three), between 64 MB and 16 GiB.
 size_t tier3_budget(int64_t n)
 {
     // about 24 bytes per node per slot: 12 KB per node gives every graph up
     // to 1.1 M nodes its three slots per SM (tier-3 tasks are latency-bound,
     // so the number of resident blocks sets their throughput)
-    const size_t b = (size_t)n * 12288;
+    const size_t b = (size_t)n * 4096 * SG_DENSE_BLOCKS;
     return std::min<size_t>((size_t)16 << 30, std::max<size_t>((size_t)64 << 20, b));
 }
 
@@ -592,7 +593,7 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
     int qcap = 1;
     while ((size_t)qcap < n) qcap <<= 1;
     const size_t per_slot = n * 20 + (size_t)qcap * 4;
-    const size_t slots = std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms * 3, tier3_budget(g->n) / per_slot));
+    const size_t slots = std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms * SG_DENSE_BLOCKS, tier3_budget(g->n) / per_slot));
     b += slots * per_slot;
     b += (size_t)g->num_sms * 2 * 12 + (size_t)k * 12 + 4096;
     if (heavy_index_enabled(g, W)) {
@@ -655,7 +656,7 @@ sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, 
         while (qcap < n) qcap <<= 1;
         const size_t per_slot = (size_t)n * (2 * sizeof(unsigned long long) + sizeof(int32_t)) + (size_t)qcap * 4;
         const size_t budget = tier3_budget(n);
-        int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms * 3, budget / per_slot));
+        int slots = (int)std::max<size_t>(1, std::min<size_t>((size_t)g->num_sms * SG_DENSE_BLOCKS, budget / per_slot));
         const size_t ns = (size_t)slots * (size_t)n;
         SG_TRY(dbuf_alloc(ws.slot_vis, 2 * ns, st));  // per node: visited and pending words side by side
         SG_TRY(dbuf_alloc(ws.slot_qa, (size_t)slots * (size_t)qcap, st));

@@ -36,6 +36,12 @@
 
 #include "sg.h"
 
+// Resident 512-thread blocks per SM of the dense (tier-3) traversal engine;
+// the tier-3 slot count is this many per SM.
+#ifndef SG_DENSE_BLOCKS
+#define SG_DENSE_BLOCKS 3
+#endif
+
 namespace sgi {
 
 // ------------------------------------------------------------------ errors

@@ -1175,7 +1175,7 @@ struct CoopShape {
 };
 template <int LOGC>
 struct CoopShape<TAB_DENSE, LOGC> {
-    static constexpr int T = 512, MINB = 3;
+    static constexpr int T = 512, MINB = SG_DENSE_BLOCKS;
 };
 
 struct CoopCtl {

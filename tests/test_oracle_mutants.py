@@ -38,10 +38,12 @@ MUTANTS = {
     "celf_accepts_stale_bound": ("if (stamp == i) { s[v] = b; vs = v; break; }",
                                  "if (stamp <= i) { s[v] = b; vs = v; break; }"),
     "coupled_higher_arc_id": ("cid[e] = e < lo ? e : lo;", "cid[e] = e > lo ? e : lo;"),
-    "masks_last_word_unmasked": ("if (r < R && or_live(seed, (uint32_t)r, coin_of(cid, e), thr[e])) word |= 1ULL << b;",
-                                 "if (or_live(seed, (uint32_t)r, coin_of(cid, e), thr[e])) word |= 1ULL << b;"),
-    "masks_bit_reversed": ("if (r < R && or_live(seed, (uint32_t)r, coin_of(cid, e), thr[e])) word |= 1ULL << b;",
-                           "if (r < R && or_live(seed, (uint32_t)r, coin_of(cid, e), thr[e])) word |= 1ULL << (63 - b);"),
+    "masks_last_word_unmasked": ("if (r < R && arc_live(seed, (uint32_t)r, e, thr, cid, lo)) word |= 1ULL << b;",
+                                 "if (arc_live(seed, (uint32_t)r, e, thr, cid, lo)) word |= 1ULL << b;"),
+    "masks_bit_reversed": ("if (r < R && arc_live(seed, (uint32_t)r, e, thr, cid, lo)) word |= 1ULL << b;",
+                           "if (r < R && arc_live(seed, (uint32_t)r, e, thr, cid, lo)) word |= 1ULL << (63 - b);"),
+    "lt_hashes_source": ("            key[e] = v;\n", "            key[e] = u;\n"),
+    "lt_overlapping_intervals": ("hi[e] = (uint64_t)(j + 1) * w;", "hi[e] = (uint64_t)(j + 2) * w;"),
     "celf_ties_to_highest_id": ("return h->b[x] > h->b[y] || (h->b[x] == h->b[y] && h->v[x] < h->v[y]);",
                                 "return h->b[x] > h->b[y] || (h->b[x] == h->b[y] && h->v[x] > h->v[y]);"),
 }

@@ -62,7 +62,7 @@ def test_coin_word_layout(oracle_mod):
 
 
 @pytest.mark.parametrize("R", [1, 63, 64, 65, 130])
-@pytest.mark.parametrize("model,p", [("uic", 0.3), ("wic", 0.0), ("uic_undirected", 0.4)])
+@pytest.mark.parametrize("model,p", [("uic", 0.3), ("wic", 0.0), ("uic_undirected", 0.4), ("lt", 0.0)])
 def test_live_masks_bit_by_bit(oracle_mod, R, model, p):
     """or_live_masks against the pure-Python coin, bit by bit: bit b of word
     w of arc e is the coin of snapshot 64w + b (Section 3.1 snapshot; reading
@@ -79,14 +79,14 @@ def test_live_masks_bit_by_bit(oracle_mod, R, model, p):
     assert masks.shape == (g.m, W)
     arcs = brute.canonical_arcs(s, d)
     assert len(arcs) == g.m
-    thr = brute.thresholds(n, arcs, model, p)
+    iv = brute.intervals(n, arcs, model, p)
     cid = brute.coin_ids(arcs, model)
     for e in range(g.m):
         for w in range(W):
             want = 0
             for b in range(64):
                 r = 64 * w + b
-                if r < R and brute.coin(seed, r, cid[e], thr[e]):
+                if r < R and brute.coin_range(seed, r, cid[e], *iv[e]):
                     want |= 1 << b
             assert int(masks[e, w]) == want, (e, w)
 
@@ -339,6 +339,80 @@ def test_snapshot_mean_matches_exact_expectation(oracle_mod, model, p):
         assert abs(float(est - mean)) <= 5 * math.sqrt(float(var)) / math.sqrt(R) + 1e-12
 
 
+# ------------------------------------- linear threshold model (live-edge form)
+
+
+LT_CASES = [(9, 20, 1), (10, 24, 2), (11, 18, 3), (12, 26, 4)]
+
+
+@pytest.mark.parametrize("n,m,gseed", LT_CASES)
+def test_lt_greedy_matches_brute_force(oracle_mod, n, m, gseed):
+    """Live-edge linear threshold snapshots (one kept in-arc per node at
+    most): every route of the oracle gives the brute-force greedy (own
+    intervals, Warshall closure), within the Nemhauser bound."""
+    _, s, d = inputs.random_small(n, m, gseed, loops_and_dups=True)
+    R, k, seed = 24, 4, 700 + gseed
+    b = brute.Brute(n, s, d, "lt", 0.0, R, seed)
+    bs, bg = b.greedy(k)
+    g = oracle.Graph(n, s, d, "lt")
+    for mode in MODES:
+        out = g.select(R=R, k=k, seed=seed, mode=mode)
+        assert list(out["seeds"]) == bs, mode
+        assert list(out["gains"]) == bg, mode
+    assert sum(bg) >= (1 - 1 / math.e) * b.optimum(k)
+    s_init = g.select(R=R, k=1, seed=seed, mode=oracle.DU, want_init=True)["s_init"]
+    assert list(s_init) == [b.f([v]) for v in range(n)]
+
+
+def test_lt_keeps_at_most_one_in_arc(oracle_mod):
+    """Per snapshot every node keeps at most one in-arc, exactly one when its
+    in-degree is a power of two (the intervals then tile 2^32), and each arc
+    is kept with probability floor(2^32/d)/2^32 (within 6 sigma)."""
+    n, s, d = inputs.chung_lu_undirected(2000, 8000, 2.5, 8.0, 5)
+    g = oracle.Graph(n, s, d, "lt")
+    R = 192
+    masks = g.live_masks(R, seed=404)
+    bits = np.unpackbits(masks.view(np.uint8), axis=1, bitorder="little")[:, :R]  # (m, R)
+    col = g.col[: g.m]
+    indeg = np.bincount(col, minlength=n)
+    per_node = np.zeros((n, R), dtype=np.int64)
+    np.add.at(per_node, col, bits.astype(np.int64))
+    assert per_node.max() <= 1
+    pow2 = (indeg > 0) & ((indeg & (indeg - 1)) == 0)
+    assert np.all(per_node[pow2] == 1)
+    q = ((1 << 32) // indeg[col]).astype(np.float64) / 2**32
+    kept = bits.sum(axis=1)
+    _sigma_check(int(kept.sum()), float(q.sum()) * R, float((q * (1 - q)).sum()) * R)
+
+
+def test_lt_closed_forms(oracle_mod):
+    """A directed path: every node has one in-arc, kept always, so
+    s_i = R (n - i).  An in-star of 4 sources into c (in-degree 4, a power of
+    two): in each snapshot exactly one source reaches c, so the sources'
+    initial gains sum to 4R + R and c's is R."""
+    n, s, d = inputs.path_graph(7)
+    g = oracle.Graph(n, s, d, "lt")
+    s_init = g.select(R=50, k=1, seed=3, mode=oracle.DU, want_init=True)["s_init"]
+    assert list(s_init) == [50 * (n - i) for i in range(n)]
+    g = oracle.Graph(5, [0, 1, 2, 3], [4, 4, 4, 4], "lt")
+    for R, seed in ((64, 1), (100, 9), (333, 12345)):
+        s_init, _ = g.init_gains(R, seed)
+        assert int(s_init[:4].sum()) == 5 * R and int(s_init[4]) == R
+
+
+def test_lt_snapshot_mean_matches_exact_expectation(oracle_mod):
+    """R = 2^16 snapshots: the mean of |R(G'_r, S)| lies within 5 sigma/sqrt(R)
+    of the exact linear-threshold spread, enumerated over every combination
+    of per-node in-arc choices (Kempe et al.'s live-edge equivalence)."""
+    n, s, d = inputs.random_small(6, 11, 17, loops_and_dups=False)
+    g = oracle.Graph(n, s, d, "lt")
+    R = 1 << 16
+    for S in ([0], [1, 3], [2, 4, 5]):
+        mean, var = brute.exact_spread_lt(n, s, d, S)
+        est = Fraction(g.spread(R, seed=55, S=S), R)
+        assert abs(float(est - mean)) <= 5 * math.sqrt(float(var)) / math.sqrt(R) + 1e-12
+
+
 # ------------------------------------------- undirected variant (coupled coins)
 
 
@@ -415,10 +489,11 @@ def medium_graphs(oracle_mod):
     return {
         "wic": oracle.Graph(n, s, d, "wic"),
         "uic": oracle.Graph(n, s, d, "uic", 0.05),
+        "lt": oracle.Graph(n, s, d, "lt"),
     }
 
 
-@pytest.mark.parametrize("model", ["wic", "uic"])
+@pytest.mark.parametrize("model", ["wic", "uic", "lt"])
 def test_du_matches_recompute_and_invariants(medium_graphs, model):
     g = medium_graphs[model]
     R, k, seed = 64, 15, 31
