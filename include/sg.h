@@ -64,8 +64,19 @@ typedef enum {
  *   is undirected and reach sets are connected components.  sg_select,
  *   sg_init_gains, sg_spread, sg_live_masks, batches and the server accept
  *   it (sg_select runs it by per-snapshot union-find); sg_select_celf does
- *   not.  A graph that is not symmetric gives SG_EINVAL. */
-typedef enum { SG_UIC = 0, SG_WIC = 1, SG_UIC_UNDIRECTED = 2 } sg_model;
+ *   not.  A graph that is not symmetric gives SG_EINVAL.
+ * SG_LT: the linear threshold model in its live-edge form (Kempe, Kleinberg
+ *   and Tardos 2003; the paper's Section 3.4.2 and Section 7 name the LT
+ *   generalisation), weights 1/indeg(v): in each snapshot every node v
+ *   keeps at most one in-arc.  v's draw in snapshot r is
+ *   hi32(splitmix64(seed ^ (r << 40) ^ v)); its in-arcs, sources ascending,
+ *   own the intervals [j w, (j+1) w), w = floor(2^32 / indeg(v)), and the
+ *   arc whose interval holds the draw is live (none when the draw is past
+ *   indeg(v) w).  p is ignored.  Every entry point accepts it; the coins are
+ *   materialised once per query into the live-mask cache (2 x W x m x 8
+ *   bytes, at most 16 GiB, else SG_ENOMEM) and the heavy-row index is not
+ *   used. */
+typedef enum { SG_UIC = 0, SG_WIC = 1, SG_UIC_UNDIRECTED = 2, SG_LT = 3 } sg_model;
 
 /* Cascade model: UIC uses p in [0, 1] for every arc; WIC ignores p and uses
  * 1/indeg(v) for every arc u -> v (Section 3.4.1 and Section 5.1). */

@@ -62,13 +62,14 @@ sg_status celf_impl(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     sg_workspace &ws = g->ws;
     const size_t n = (size_t)g->n, nw = n * (size_t)co.W;
     SG_TRY(ensure_workspace(g, ws, co.W, k, st));
-    const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
+    // the linear threshold model reads every coin from the live-mask cache
+    const int heavy_on = (!co.lt && heavy_index_enabled(g, co.W)) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
     ws.slists_on = 0;
     // every per-query cache is rebuilt for this query's coins
     ws.fl_on = 0;
     if (heavy_on) SG_TRY(ensure_fwd_lists(g, ws, co, c.p, model, st));
-    SG_TRY(ensure_mask_cache(g, ws, co.W, st));
+    SG_TRY(ensure_mask_cache(g, ws, co.W, st, co.lt != 0));
 
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     struct EvGuard {

@@ -475,6 +475,7 @@ GraphView view_of(const sg_graph *g, const sg_workspace &ws, int heavy_on)
     v.heavy_on = heavy_on;
     v.lm_out = ws.lm_on ? ws.lm_out.p : nullptr;
     v.lm_in = ws.lm_on ? ws.lm_in.p : nullptr;
+    v.lm_w0 = 0;
     v.rdesc = (heavy_on && ws.rd_on) ? ws.rdesc.p : nullptr;
     const bool fl = heavy_on && ws.fl_on;
     v.fsoff = fl ? ws.fsoff.p : nullptr;
@@ -495,10 +496,16 @@ static bool mask_cache_fits(const sg_graph *g, int32_t W)
     return g_mask_cache && g->m > 0 && mask_cache_bytes(g, W) <= ((size_t)16 << 30);
 }
 
-sg_status ensure_mask_cache(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st)
+sg_status ensure_mask_cache(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st, bool required)
 {
     ws.lm_on = 0;
-    if (!mask_cache_fits(g, W)) return SG_OK;
+    if (required && g->m > 0 && mask_cache_bytes(g, W) > ((size_t)16 << 30)) {
+        set_error("the linear threshold model needs the live-mask cache (2 x W x m x 8 = %zu bytes > 16 GiB)",
+                  mask_cache_bytes(g, W));
+        return SG_ENOMEM;
+    }
+    if (!required && !mask_cache_fits(g, W)) return SG_OK;
+    if (g->m == 0) return SG_OK;
     if (ws.lm_cap < W) {
         dbuf_free(ws.lm_out, st);
         dbuf_free(ws.lm_in, st);
@@ -760,6 +767,7 @@ sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out)
     co.W = (R + 63) / 64;
     co.none_live = 0;
     co.uic_tm1 = 0xffffffffu;
+    co.lt = 0;
     if (c.model == SG_UIC || c.model == SG_UIC_UNDIRECTED) {
         if (!(c.p >= 0.0 && c.p <= 1.0)) {
             set_error("UIC probability must lie in [0, 1]");
@@ -769,6 +777,8 @@ sg_status make_coins(const sg_cascade &c, uint64_t seed, int32_t R, Coins *out)
         const uint64_t thr = (uint64_t)std::floor(c.p * 4294967296.0);
         if (thr == 0) co.none_live = 1;
         else co.uic_tm1 = (uint32_t)(thr - 1);
+    } else if (c.model == SG_LT) {
+        co.lt = 1;  // per-node draws, materialised into the live-mask cache
     } else if (c.model != SG_WIC) {
         set_error("unknown cascade model %d", c.model);
         return SG_EINVAL;
@@ -1136,13 +1146,14 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     const int model = c.model == SG_WIC ? MODEL_WIC : MODEL_UIC;
     const int launches0 = g_launches;
     SG_TRY(ensure_workspace(g, ws, co.W, k, st));
-    const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
+    // the linear threshold model reads every coin from the live-mask cache
+    const int heavy_on = (!co.lt && heavy_index_enabled(g, co.W)) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
     ws.slists_on = 0;
     if (heavy_on && g_snapshot_lists) SG_TRY(ensure_snapshot_lists(g, ws, co, c.p, model, st));
     ws.fl_on = 0;
     if (heavy_on) SG_TRY(ensure_fwd_lists(g, ws, co, c.p, model, st));
-    SG_TRY(ensure_mask_cache(g, ws, co.W, st));
+    SG_TRY(ensure_mask_cache(g, ws, co.W, st, co.lt != 0));
     ws.walk_groups = std::min(knobs().walk_groups, ws.fq_groups);
     if (prepare_only) return SG_OK;
     // events: 0 start, 1 after index, 2 after init tier 1, 3 after init,
@@ -1408,7 +1419,7 @@ sg_status sg_spread(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, const i
                                st);
         } else {
             rc = run_spread(g, co, model, dS.p, s_count, dc.p, reinterpret_cast<unsigned long long *>(dc.p + 1),
-                            st);
+                                st);
         }
     }
     long long hc[2] = {0, 0};
@@ -1454,12 +1465,12 @@ sg_status sg_init_gains(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, voi
         if (init_edges) *init_edges = h.init_edges;
         return flags_status(h.flags);
     }
-    const int heavy_on = heavy_index_enabled(g, co.W) ? 1 : 0;
+    const int heavy_on = (!co.lt && heavy_index_enabled(g, co.W)) ? 1 : 0;
     if (heavy_on) SG_TRY(ensure_heavy_index(g, ws, co.W, st));
     ws.slists_on = 0;
     ws.fl_on = 0;
     if (heavy_on) SG_TRY(ensure_fwd_lists(g, ws, co, c.p, model, st));
-    SG_TRY(ensure_mask_cache(g, ws, co.W, st));
+    SG_TRY(ensure_mask_cache(g, ws, co.W, st, co.lt != 0));
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) {

@@ -108,6 +108,7 @@ struct Coins {
     int32_t none_live; // UIC with thr = 0: no arc is ever live
     int32_t R;
     int32_t W;         // ceil(R / 64)
+    int32_t lt;        // linear threshold model: coins come from the live-mask cache (per-node draws)
 };
 
 // High 32 bits of splitmix64(base ^ (r << 40)) (Steele, Lea, Flood 2014,
@@ -154,6 +155,7 @@ struct GraphView {
     // the arc at CSC position j
     const unsigned long long *lm_out;
     const unsigned long long *lm_in;
+    int32_t lm_w0;  // word of the cache's first block (a cache may hold a range of words)
     // forward row descriptors (null when the heavy-row index is off), two
     // int4 (one 32-byte sector) per (w, x):
     // rdesc[2(w*n + x)]     = {segment base (lo, hi), elements to expand for
@@ -384,7 +386,7 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
 sg_status run_walk(sg_graph *g, const sg_workspace &ws, const Coins &co, int model, int heavy_on,
                    const int32_t *d_S, int32_t ns, unsigned long long *vis, unsigned long long *pend, int32_t *qa,
                    int32_t *qb, long long *d_total, unsigned long long *d_edges, cudaStream_t st);
-sg_status ensure_mask_cache(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st);
+sg_status ensure_mask_cache(sg_graph *g, sg_workspace &ws, int32_t W, cudaStream_t st, bool required = false);
 size_t mask_cache_bytes(const sg_graph *g, int32_t W);
 sg_status ensure_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, double p_uic, int model,
                                 cudaStream_t st);

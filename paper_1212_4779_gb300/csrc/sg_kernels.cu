@@ -220,7 +220,7 @@ __device__ __forceinline__ uint64_t elem(const GraphView &g, const Coins &co, lo
         // cached live bits of the arc at this CSR / CSC position
         const long long q = base + j;
         y = DIR == DIR_FWD ? __ldg(g.col + q) : __ldg(&g.cin[q].x);
-        const uint64_t mk = __ldg(lm + (long long)(rs >> 6) * g.m + q);
+        const uint64_t mk = __ldg(lm + (long long)((int)(rs >> 6) - g.lm_w0) * g.m + q);
         if (SLICE == SLICE_SNAP) return mk & F;
         return ((mk >> (rs & 63u)) & 1ull) ? F : 0ull;
     }
@@ -878,7 +878,7 @@ __device__ void bu_level(const EngineArgs &a, const CtaState &w, int word, uint3
                 mk = __ldg(hv.hmask + q);
             } else if (lm) {
                 x = BDIR == DIR_FWD ? __ldg(g.col + q) : __ldg(&g.cin[q].x);
-                mk = __ldg(lm + (long long)(rs >> 6) * g.m + q);
+                mk = __ldg(lm + (long long)((int)(rs >> 6) - g.lm_w0) * g.m + q);
             } else {
                 arc_at<BDIR, MODEL>(g, (int)q, rr.rtm1, x, eid, tm1);
                 hashed = true;
@@ -2309,6 +2309,56 @@ __global__ void live_masks_kernel(Coins co, long long m, const uint2 *fw, uint32
 // One warp per (word, node).  With the forward lists, the word's 65 list
 // offsets of an indexed row give its live mask (nonempty lists), its list
 // base and whether every nonempty list holds one arc.
+// Live-edge linear threshold coins (Kempe, Kleinberg and Tardos 2003, weights
+// 1/indeg): node v's draw in snapshot r is coin_hi32(seed ^ v, r); its
+// in-arcs, in CSC order (sources ascending), own consecutive intervals of
+// width w_v = floor(2^32 / indeg(v)) = tmi[v] + 1, and the arc whose
+// interval holds the draw is live in r (none when the draw is past d_v w_v).
+// One thread per (node, word) of words [w0, w0 + words): it alone writes the
+// masks of v's in-arcs for that word (zero on entry), so no atomics.
+// Outputs (each may be NULL): lm_in / lm_out [word - w0][m] in CSC / CSR
+// order, arc-major [e][aW] (sg_live_masks' layout).
+__global__ void __launch_bounds__(256) lt_masks_kernel(Coins co, int n, long long m, int w0, int words,
+                                                       const int32_t *crp, const int2 *cin, const uint32_t *tmi,
+                                                       unsigned long long *lm_in, unsigned long long *lm_out,
+                                                       unsigned long long *arc_major, int aW)
+{
+    const long long total = (long long)words * n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int wi = (int)(t / n);
+        const int v = (int)(t - (long long)wi * n);
+        const int word = w0 + wi;
+        const int beg = __ldg(crp + v), d = __ldg(crp + v + 1) - beg;
+        if (d == 0) continue;
+        const uint64_t w = (uint64_t)__ldg(tmi + v) + 1ull;
+        const uint64_t base = co.seed ^ (uint64_t)(uint32_t)v;
+        const uint64_t wm = word_mask(word, co.R);
+        int cj = -1;
+        uint64_t cm = 0;
+        auto flush = [&]() {
+            if (cj < 0) return;
+            const long long q = beg + cj;
+            const long long e = __ldg(&cin[q].y);
+            if (lm_in) lm_in[(long long)wi * m + q] |= cm;
+            if (lm_out) lm_out[(long long)wi * m + e] |= cm;
+            if (arc_major) arc_major[e * aW + word] |= cm;
+        };
+        for (int b = 0; b < 64; ++b) {
+            if (!((wm >> b) & 1ull)) break;
+            const uint64_t j = (uint64_t)coin_hi32(base, (uint32_t)word * 64u + (uint32_t)b) / w;
+            if (j >= (uint64_t)d) continue;
+            if ((int)j != cj) {
+                flush();
+                cj = (int)j;
+                cm = 0;
+            }
+            cm |= 1ull << b;
+        }
+        flush();
+    }
+}
+
 __global__ void __launch_bounds__(256) row_desc_kernel(GraphView g, int W, const long long *fsoff, int4 *out)
 {
     const int lane = threadIdx.x & 31;
@@ -2613,10 +2663,29 @@ sg_status run_heavy_index(sg_graph *g, sg_workspace &ws, const Coins &co, int mo
     return launch_index<DIR_REV, MODEL_UIC>(g, ws, co, st);
 }
 
+sg_status run_lt_masks(sg_graph *g, const Coins &co, int w0, int words, unsigned long long *lm_in,
+                       unsigned long long *lm_out, unsigned long long *arc_major, int aW, cudaStream_t st)
+{
+    const long long total = (long long)words * g->n;
+    if (total == 0 || g->m == 0) return SG_OK;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)g->num_sms * 16);
+    lt_masks_kernel<<<blocks, 256, 0, st>>>(co, (int)g->n, g->m, w0, words, g->crp.p, g->cin.p, g->tmi.p, lm_in,
+                                            lm_out, arc_major, aW);
+    SG_CUDA_TRY(cudaGetLastError());
+    ++g_launches;
+    return SG_OK;
+}
+
 sg_status run_mask_cache(sg_graph *g, sg_workspace &ws, const Coins &co, int model, cudaStream_t st)
 {
     const long long total = g->m * co.W;
     if (total == 0) return SG_OK;
+    if (co.lt) {
+        // per-node draws: every word's masks in both arc orders
+        SG_CUDA_TRY(cudaMemsetAsync(ws.lm_in.p, 0, (size_t)total * 8, st));
+        SG_CUDA_TRY(cudaMemsetAsync(ws.lm_out.p, 0, (size_t)total * 8, st));
+        return run_lt_masks(g, co, 0, co.W, ws.lm_in.p, ws.lm_out.p, nullptr, 0, st);
+    }
     const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)g->num_sms * 16);
     if (model == MODEL_WIC)
         mask_cache_kernel<MODEL_WIC><<<blocks, 256, 0, st>>>(co, g->m, g->fw.p, ws.lm_out.p);
@@ -2647,11 +2716,13 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
     const size_t n = (size_t)g->n;
     // words per launch: dense vis/pend (8 B each) and two level queues (4 B
     // each) per node and word, within 4 GiB
-    const size_t per_word = n * 32;
+    // LT: both orders of the chunk's live-mask cache as well
+    const size_t per_word = n * 32 + (co.lt ? (size_t)g->m * 16 : 0);
     const int wc = (int)std::max<size_t>(1, std::min<size_t>((size_t)co.W, ((size_t)4 << 30) / per_word));
-    DBuf<unsigned long long> vis, pend, fr;
+    DBuf<unsigned long long> vis, pend, fr, lmc;
     DBuf<int32_t> qa, qb;
     sg_status rc = SG_OK;
+    if (co.lt && (rc = dbuf_alloc(lmc, (size_t)wc * (size_t)g->m * 2, st)) != SG_OK) return rc;
     if ((rc = dbuf_alloc(vis, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(pend, (size_t)wc * n, st)) != SG_OK ||
         (rc = dbuf_alloc(qa, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(qb, (size_t)wc * n, st)) != SG_OK ||
         (rc = dbuf_alloc(fr, (size_t)wc * n, st)) != SG_OK) {
@@ -2660,6 +2731,7 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
         dbuf_free(qa, st);
         dbuf_free(qb, st);
         dbuf_free(fr, st);
+        dbuf_free(lmc, st);
         return rc;
     }
     if (cudaMemsetAsync(fr.p, 0, (size_t)wc * n * 8, st) != cudaSuccess) {
@@ -2684,6 +2756,18 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
             rc = SG_ECUDA;
             break;
         }
+        if (co.lt) {
+            const size_t cm = (size_t)words * (size_t)g->m;
+            if (cudaMemsetAsync(lmc.p, 0, cm * 16, st) != cudaSuccess) {
+                set_error("sg_spread: memset failed");
+                rc = SG_ECUDA;
+                break;
+            }
+            if ((rc = run_lt_masks(g, co, w0, words, lmc.p + cm, lmc.p, nullptr, 0, st)) != SG_OK) break;
+            a.g.lm_out = lmc.p;
+            a.g.lm_in = lmc.p + cm;
+            a.g.lm_w0 = w0;
+        }
         SpreadArgs sp{vis.p, pend.p, qa.p, qb.p, d_S, ns, w0, 1, d_total, d_edges, fr.p};
         if (model == MODEL_WIC) spread_kernel<MODEL_WIC><<<words, BT, 0, st>>>(a, sp);
         else spread_kernel<MODEL_UIC><<<words, BT, 0, st>>>(a, sp);
@@ -2698,6 +2782,7 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
     dbuf_free(qa, st);
     dbuf_free(qb, st);
     dbuf_free(fr, st);
+    dbuf_free(lmc, st);
     return rc;
 }
 
@@ -2798,6 +2883,10 @@ sg_status run_live_masks(sg_graph *g, const Coins &co, int model, uint64_t *out,
 {
     const long long total = g->m * co.W;
     if (total == 0) return SG_OK;
+    if (co.lt) {
+        SG_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)total * 8, st));
+        return run_lt_masks(g, co, 0, co.W, nullptr, nullptr, reinterpret_cast<unsigned long long *>(out), co.W, st);
+    }
     const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)g->num_sms * 16);
     live_masks_kernel<<<blocks, 256, 0, st>>>(co, g->m, g->fw.p, co.uic_tm1, model == MODEL_WIC, cid,
                                               reinterpret_cast<unsigned long long *>(out));

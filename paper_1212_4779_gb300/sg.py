@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libsg.so")
 
 SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ETIMEOUT, SG_EBUSY, SG_EINTERNAL = range(7)
-SG_UIC, SG_WIC, SG_UIC_UNDIRECTED = 0, 1, 2
+SG_UIC, SG_WIC, SG_UIC_UNDIRECTED, SG_LT = 0, 1, 2, 3
 _STATUS = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA", 4: "SG_ETIMEOUT", 5: "SG_EBUSY",
            6: "SG_EINTERNAL"}
 
@@ -241,8 +241,8 @@ def _addr(a):
 
 
 def _cascade(model, p):
-    m = {"uic": SG_UIC, "wic": SG_WIC, "uic_undirected": SG_UIC_UNDIRECTED, SG_UIC: SG_UIC, SG_WIC: SG_WIC,
-         SG_UIC_UNDIRECTED: SG_UIC_UNDIRECTED}[model]
+    m = {"uic": SG_UIC, "wic": SG_WIC, "uic_undirected": SG_UIC_UNDIRECTED, "lt": SG_LT, SG_UIC: SG_UIC,
+         SG_WIC: SG_WIC, SG_UIC_UNDIRECTED: SG_UIC_UNDIRECTED, SG_LT: SG_LT}[model]
     return sg_cascade(m, float(p))
 
 

@@ -118,7 +118,7 @@ def test_cascade_models_map_to_the_header_enum():
     from paper_1212_4779_gb300 import sg
 
     hdr = open(os.path.join(ROOT, "include", "sg.h")).read()
-    assert "SG_UIC = 0, SG_WIC = 1, SG_UIC_UNDIRECTED = 2" in hdr
-    for name, val in (("uic", 0), ("wic", 1), ("uic_undirected", 2)):
+    assert "SG_UIC = 0, SG_WIC = 1, SG_UIC_UNDIRECTED = 2, SG_LT = 3" in hdr
+    for name, val in (("uic", 0), ("wic", 1), ("uic_undirected", 2), ("lt", 3)):
         c = sg._cascade(name, 0.25)
         assert c.model == val and c.p == 0.25
