@@ -2135,8 +2135,8 @@ __global__ void __launch_bounds__(AM_T) argmax_kernel(long long *s, int n, Ctl *
 // (h, w) segment.  hcnt must be zero on entry.
 template <int DIR, int MODEL>
 __global__ void __launch_bounds__(256) heavy_index_kernel(GraphView g, Coins co, const int32_t *hrow,
-                                                          const int32_t *hcpref, int nh, int32_t *hcnt,
-                                                          int32_t *hnbr, unsigned long long *hmask,
+                                                          const int32_t *hcpref, const int32_t *hbrow, int nh,
+                                                          int32_t *hcnt, int32_t *hnbr, unsigned long long *hmask,
                                                           const long long *hpref)
 {
     const int lane = threadIdx.x & 31;
@@ -2146,13 +2146,7 @@ __global__ void __launch_bounds__(256) heavy_index_kernel(GraphView g, Coins co,
     for (long long it = gw0; it < items; it += nwarps) {
         const int word = (int)(it % co.W);
         const long long k = it / co.W;
-        int lo = 0, hi = nh - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(hcpref + mid) <= k) lo = mid;
-            else hi = mid - 1;
-        }
-        const int h = lo;
+        const int h = __ldg(hbrow + k);  // the block's row (one load; no search over the rows)
         const int blk = (int)(k - __ldg(hcpref + h));
         const int x = __ldg(hrow + h);
         int beg, end;
@@ -2195,8 +2189,8 @@ __global__ void __launch_bounds__(256) heavy_index_kernel(GraphView g, Coins co,
 
 // ------------------------------------------- per-snapshot heavy in-lists
 // From the per-word index of heavy in-rows: count the live in-arcs of every
-// (heavy row, snapshot), scan, and fill.  mode 0 counts into scnt, mode 1
-// fills snbr using scnt as cursors (reset to zero in between).
+// (heavy row, snapshot), scan, and fill.  mode 0 writes the counts into
+// scnt, mode 1 fills snbr from the offsets soff (scnt unused).
 // by_node 0: lists indexed by heavy-row ordinal h (q = h*64W + r), nq =
 // nh*64W; by_node 1: indexed by the row's node (q = x*64W + r), nq = n*64W.
 // rp holds the row offsets of the index's direction (for the degree).
@@ -2208,7 +2202,11 @@ __global__ void __launch_bounds__(256) snapshot_lists_kernel(Coins co, int nh, c
                                                              long long cap, int32_t *svalid, int mode,
                                                              int by_node, long long nq)
 {
+    // One warp owns each (row, word) segment and so its 64 (row, snapshot)
+    // lists: counts and ranks come from warp ballots, no atomics; lane l
+    // keeps the counters (or cursors) of snapshot bits l and l + 32.
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const long long nseg = (long long)nh * co.W;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int R64 = 64 * co.W;
@@ -2219,20 +2217,37 @@ __global__ void __launch_bounds__(256) snapshot_lists_kernel(Coins co, int nh, c
         const int deg = crp[x + 1] - crp[x];
         const long long seg = hpref[h] * co.W + (long long)w * deg;
         const int cnt = hcnt[sg];
-        for (int j = lane; j < cnt; j += 32) {
-            uint64_t M = hmask[seg + j];
-            const int y = hnbr[seg + j];
-            while (M) {
-                const int b = __ffsll((long long)M) - 1;
-                M &= M - 1;
-                const long long q = (long long)(by_node ? x : h) * R64 + 64 * w + b;
-                if (mode == 0) {
-                    atomicAdd((unsigned long long *)&scnt[q], 1ull);
-                } else {
-                    const long long pos = soff[q] + (long long)atomicAdd((unsigned long long *)&scnt[q], 1ull);
-                    if (pos < cap) snbr[pos] = y;
+        const long long q0 = (long long)(by_node ? x : h) * R64 + 64 * w;  // list of snapshot 64w + b at q0 + b
+        long long acc0 = 0, acc1 = 0;  // counts (mode 0) or list cursors (mode 1) of bits lane, lane + 32
+        if (mode == 1) {
+            acc0 = soff[q0 + lane];
+            acc1 = soff[q0 + 32 + lane];
+        }
+        for (int j0 = 0; j0 < cnt; j0 += 32) {
+            const int j = j0 + lane;
+            const uint64_t M = j < cnt ? hmask[seg + j] : 0ull;
+            const int y = j < cnt ? hnbr[seg + j] : 0;
+#pragma unroll 4
+            for (int b = 0; b < 64; ++b) {
+                const bool has = (M >> b) & 1ull;
+                const unsigned bal = __ballot_sync(FULL, has);
+                if (!bal) continue;
+                if (mode == 1) {
+                    const long long cur = __shfl_sync(FULL, b < 32 ? acc0 : acc1, b & 31);
+                    if (has) {
+                        const long long pos = cur + __popc(bal & lt);
+                        if (pos < cap) snbr[pos] = y;
+                    }
+                }
+                if (lane == (b & 31)) {
+                    if (b < 32) acc0 += __popc(bal);
+                    else acc1 += __popc(bal);
                 }
             }
+        }
+        if (mode == 0) {
+            scnt[q0 + lane] = acc0;
+            scnt[q0 + 32 + lane] = acc1;
         }
     }
     if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) *svalid = soff[nq] <= cap ? 1 : 0;
@@ -2541,7 +2556,8 @@ sg_status launch_index(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStrea
     int32_t *hcnt = fwd ? ws.hcnt_out.p : ws.hcnt_in.p;
     SG_CUDA_TRY(cudaMemsetAsync(hcnt, 0, (size_t)nh * co.W * sizeof(int32_t), st));
     heavy_index_kernel<DIR, MODEL><<<g->num_sms * 8, 256, 0, st>>>(
-        view_of(g, ws, 1), co, fwd ? g->hrow_out.p : g->hrow_in.p, fwd ? g->hcpref_out.p : g->hcpref_in.p, nh, hcnt,
+        view_of(g, ws, 1), co, fwd ? g->hrow_out.p : g->hrow_in.p, fwd ? g->hcpref_out.p : g->hcpref_in.p,
+        fwd ? g->hbrow_out.p : g->hbrow_in.p, nh, hcnt,
         fwd ? ws.hnbr_out.p : ws.hnbr_in.p, fwd ? ws.hmask_out.p : ws.hmask_in.p,
         fwd ? g->hpref_out.p : g->hpref_in.p);
     SG_CUDA_TRY(cudaGetLastError());
@@ -2821,7 +2837,7 @@ sg_status run_fwd_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cudaStre
     scan_sums_kernel<<<1, SC_T, 0, st>>>(sums, nb, sums + nb);
     scan_add_kernel<<<(unsigned)nb, SC_T, 0, st>>>(ws.fsoff.p, n1, sums);
     SG_CUDA_TRY(cudaGetLastError());
-    SG_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)nq * 8, st));
+    // the fill keeps its list cursors in registers (no counters to clear)
     snapshot_lists_kernel<<<grid, 256, 0, st>>>(co, nh, ws.hcnt_out.p, ws.hnbr_out.p, ws.hmask_out.p, g->hpref_out.p,
                                                 g->rp.p, g->hrow_out.p, cnt, ws.fsoff.p, ws.fsnbr.p,
                                                 (long long)ws.fsnbr_cap, ws.fsvalid.p, 1, 1, nq);
@@ -2849,8 +2865,7 @@ sg_status run_snapshot_lists(sg_graph *g, sg_workspace &ws, const Coins &co, cud
     scan_sums_kernel<<<1, SC_T, 0, st>>>(sums, nb, sums + nb);
     scan_add_kernel<<<(unsigned)nb, SC_T, 0, st>>>(ws.soff.p, n1, sums);
     SG_CUDA_TRY(cudaGetLastError());
-    // fill, counts reused as cursors
-    SG_CUDA_TRY(cudaMemsetAsync(ws.scan_tmp.p, 0, (size_t)nq * 8, st));
+    // fill (list cursors in registers)
     snapshot_lists_kernel<<<grid, 256, 0, st>>>(co, nh, ws.hcnt_in.p, ws.hnbr_in.p, ws.hmask_in.p, g->hpref_in.p,
                                                 g->crp.p, g->hrow_in.p, ws.scan_tmp.p, ws.soff.p, ws.snbr.p,
                                                 (long long)ws.snbr_cap, ws.svalid.p, 1, 0, nq);
