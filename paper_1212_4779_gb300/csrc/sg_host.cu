@@ -600,7 +600,7 @@ size_t workspace_bytes(const sg_graph *g, int32_t W, int32_t k)
     b += 4 * (nw + W64 + 64) * 2;                      // task lists
     b += 4 * nw * 64;                                  // per-snapshot targets
     b += (8 + 8 + 4) * W64 + 4 * (size_t)W;            // offsets, counts
-    b += 8 * nw + (4 * nw + 4 * (size_t)W) * 8;        // ancestors, per (word, group) lists
+    b += 8 * nw + (4 * nw + 4 * (size_t)W) * (size_t)std::max(8, knobs().walk_groups);  // ancestors, lists
     b += 2 * 8 * nw * 8 + (W64 << 8) * (4 + 4 + 8 + 8);  // landmarks
     int qcap = 1;
     while ((size_t)qcap < n) qcap <<= 1;
@@ -650,8 +650,9 @@ sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, 
         SG_TRY(dbuf_alloc(ws.du_cnt, (size_t)W, st));
         SG_TRY(dbuf_alloc(ws.anc, nw, st));
         SG_TRY(dbuf_alloc(ws.frw, nw, st));
-        SG_TRY(dbuf_alloc(ws.anc_list, nw * 8, st));  // one list per (word, forward group)
-        SG_TRY(dbuf_alloc(ws.anc_cnt, (size_t)W * 8, st));
+        // one list of marked ancestors per (word, walk group)
+        SG_TRY(dbuf_alloc(ws.anc_list, nw * (size_t)ws.fq_groups, st));
+        SG_TRY(dbuf_alloc(ws.anc_cnt, (size_t)W * (size_t)ws.fq_groups, st));
         SG_TRY(dbuf_alloc(ws.lmk_rx, nw * 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_ux, nw * 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_U, ((size_t)64 * W) << 8, st));
@@ -1193,7 +1194,7 @@ sg_status select_impl(sg_graph *g, sg_workspace &ws, int32_t R, int32_t k, sg_ca
     SG_CUDA_TRY(cudaMemsetAsync(ws.s.p, 0, (size_t)g->n * sizeof(long long), st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.cov.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.anc.p, 0, (size_t)g->n * (size_t)co.W * 8, st));
-    SG_CUDA_TRY(cudaMemsetAsync(ws.anc_cnt.p, 0, (size_t)co.W * 8 * 4, st));
+    SG_CUDA_TRY(cudaMemsetAsync(ws.anc_cnt.p, 0, (size_t)co.W * (size_t)ws.fq_groups * 4, st));
     SG_CUDA_TRY(cudaMemsetAsync(ws.ctl.p, 0, sizeof(Ctl), st));
     if (heavy_on) {
         SG_TRY(run_heavy_index(g, ws, co, model, st));

@@ -216,8 +216,8 @@ struct sg_workspace {
     sgi::DBuf<int32_t> du_cnt;           // [W] entries per word
     sgi::DBuf<unsigned long long> anc;   // [W][n] ancestors of the round's seed, per snapshot bit
     sgi::DBuf<unsigned long long> frw;   // [W][n] bottom-up frontier bits of the walks (zero between levels)
-    sgi::DBuf<int32_t> anc_list;         // [W][8][n] nodes given ancestor bits, per (word, 8-bit group)
-    sgi::DBuf<int32_t> anc_cnt;          // [W][8]
+    sgi::DBuf<int32_t> anc_list;         // [W][G][n] nodes given ancestor bits, per (word, walk group)
+    sgi::DBuf<int32_t> anc_cnt;          // [W][G]
     sgi::DBuf<unsigned long long> lmk_rx;    // [W][n][8] landmark reach bits (R(x_i) membership)
     sgi::DBuf<unsigned long long> lmk_ux;    // [W][n][8] ... and which landmarks the node reaches
     sgi::DBuf<int32_t> lmk_U, lmk_H;         // [64W << K] union sizes / membership histogram

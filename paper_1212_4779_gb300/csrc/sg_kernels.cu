@@ -1683,27 +1683,29 @@ __global__ void __launch_bounds__(BT) fwd_walk_kernel(EngineArgs a, FwdArgs f)
                                       nullptr, S);
 }
 
-// Forward DU after the walk, in three launches over (word, group) blocks,
-// group g owning snapshot bits 8g..8g+7 of the word (bit-disjoint atomics on
-// the shared words, as in the walk):
-//  fwd_anc_kernel    clears the group's bits of the previous round's
+// Forward DU after the walk, in three launches:
+//  fwd_anc_kernel    per (word, group) -- the walk's groups, 64/G snapshot
+//                    bits each (bit-disjoint atomics on the shared words):
+//                    clears the group's bits of the previous round's
 //                    ancestor marks; |N_r| for its snapshots; then walks back
 //                    from v* over live in-arcs: every u reaching v* in
 //                    snapshot r reaches all of N_r (N_r lies inside
 //                    R(G'_r, v*)), so s_u drops by |N_r| at once, and u is
 //                    marked an ancestor;
-//  fwd_lists_kernel  per-snapshot lists of the remaining targets (N_r minus
-//                    the ancestors), one fixed region of n entries per
-//                    snapshot, for the target-sliced reverse tasks, which
-//                    never enter a marked node (a path through one would make
-//                    its start an ancestor); the last block turns the counts
-//                    into the reverse tasks' offsets;
+//  fwd_lists_kernel  per (word, 8-bit group, slice of the word's new
+//                    entries): per-snapshot lists of the remaining targets
+//                    (N_r minus the ancestors), one fixed region of n
+//                    entries per snapshot, for the target-sliced reverse
+//                    tasks, which never enter a marked node (a path through
+//                    one would make its start an ancestor); the last block
+//                    turns the counts into the reverse tasks' offsets;
 //  fwd_clear_kernel  clears the round's new-bit words.
-constexpr int FPB = 64 / FWD_GROUPS;  // snapshot bits per group
+constexpr int FPB = 64 / FWD_GROUPS;  // snapshot bits per list group
+constexpr int LIST_SLICES = 4;       // blocks per (word, list group)
 
-__device__ __forceinline__ uint64_t group_mask(int grp)
+__device__ __forceinline__ uint64_t group_mask(int grp, int gb)
 {
-    return (FPB == 64 ? ~0ull : ((1ull << FPB) - 1ull)) << (grp * FPB);
+    return (gb == 64 ? ~0ull : ((1ull << gb) - 1ull)) << (grp * gb);
 }
 
 template <int MODEL>
@@ -1711,10 +1713,11 @@ __global__ void __launch_bounds__(BT) fwd_anc_kernel(EngineArgs a, FwdArgs f)
 {
     __shared__ CtaShared S;
     const int n = a.g.n;
-    const int word = blockIdx.x / FWD_GROUPS;
-    const int grp = blockIdx.x - word * FWD_GROUPS;
+    const int word = blockIdx.x / f.groups;
+    const int grp = blockIdx.x - word * f.groups;
+    const int gb = 64 / f.groups;  // at most 8
     const int tid = threadIdx.x, lane = tid & 31;
-    const uint64_t gm = group_mask(grp);
+    const uint64_t gm = group_mask(grp, gb);
     const int vstar = *(volatile int32_t *)&a.ctl->vstar;
     const size_t so = (size_t)word * (size_t)n;
     unsigned long long *ancw = f.anc + so;
@@ -1726,24 +1729,26 @@ __global__ void __launch_bounds__(BT) fwd_anc_kernel(EngineArgs a, FwdArgs f)
         for (int i = tid; i < na; i += BT) atomicAnd(&ancw[anclw[i]], ~gm);
     }
     if (tid < 64) S.boff[tid] = 0;
+    if (tid < gb) f.tcnt[64 * word + grp * gb + tid] = 0;  // the target lists' counters (fwd_lists_kernel)
     __syncthreads();
     const int nd = vstar >= 0 ? *(volatile int32_t *)&f.du_cnt[word] : 0;
     const int32_t *dux = f.du_x + so;
     const unsigned long long *nb = f.nbits + so;
     // |N_r| for the group's snapshots: ballots over 32 entries at a time
-    int c[FPB];
+    int c[8];
 #pragma unroll
-    for (int j = 0; j < FPB; ++j) c[j] = 0;
+    for (int j = 0; j < 8; ++j) c[j] = 0;
     for (int base = (tid >> 5) * 32; base < nd; base += BT) {
         const int i = base + lane;
-        const uint64_t M = i < nd ? (__ldg(nb + dux[i]) & gm) >> (grp * FPB) : 0ull;
+        const uint64_t M = i < nd ? (__ldg(nb + dux[i]) & gm) >> (grp * gb) : 0ull;
 #pragma unroll
-        for (int j = 0; j < FPB; ++j) c[j] += __popc(__ballot_sync(FULL, (M >> j) & 1ull));
+        for (int j = 0; j < 8; ++j)
+            if (j < gb) c[j] += __popc(__ballot_sync(FULL, (M >> j) & 1ull));
     }
     if (lane == 0)
 #pragma unroll
-        for (int j = 0; j < FPB; ++j)
-            if (c[j]) atomicAdd(&S.boff[grp * FPB + j], c[j]);
+        for (int j = 0; j < 8; ++j)
+            if (j < gb && c[j]) atomicAdd(&S.boff[grp * gb + j], c[j]);
     __syncthreads();
     const uint64_t mv = vstar >= 0 ? nb[vstar] & gm : 0ull;  // bits v* newly covers
     int nanc = 0;
@@ -1769,22 +1774,23 @@ __global__ void __launch_bounds__(BT) fwd_lists_kernel(FwdArgs f, Ctl *ctl, int 
 {
     __shared__ CtaShared S;
     __shared__ int sh_last;
-    __shared__ int cnt[FPB];
-    const int word = blockIdx.x / FWD_GROUPS;
-    const int grp = blockIdx.x - word * FWD_GROUPS;
+    constexpr int PER_WORD = FWD_GROUPS * LIST_SLICES;
+    const int word = blockIdx.x / PER_WORD;
+    const int rem = blockIdx.x - word * PER_WORD;
+    const int grp = rem / LIST_SLICES, slice = rem - grp * LIST_SLICES;
     const int tid = threadIdx.x, lane = tid & 31;
-    const uint64_t gm = group_mask(grp);
+    const uint64_t gm = group_mask(grp, FPB);
     const int vstar = *(volatile int32_t *)&ctl->vstar;
     const size_t so = (size_t)word * (size_t)n;
-    if (tid < FPB) cnt[tid] = 0;
-    __syncthreads();
     const int nd = vstar >= 0 ? *(volatile int32_t *)&f.du_cnt[word] : 0;
     const int32_t *dux = f.du_x + so;
     const unsigned long long *nb = f.nbits + so, *ancw = f.anc + so;
     int32_t *tlw = f.tl + (size_t)word * (size_t)f.tcap;
+    int32_t *cnt = f.tcnt + 64 * word + grp * FPB;  // zeroed by fwd_anc_kernel
     const unsigned lt = (1u << lane) - 1u;
-    // whole warps take 32 entries at a time (every lane joins the ballots)
-    for (int base = (tid >> 5) * 32; base < nd; base += BT) {
+    // whole warps take 32 entries at a time (every lane joins the ballots);
+    // the slices of one (word, group) share its counters
+    for (int base = ((tid >> 5) + BW * slice) * 32; base < nd; base += BT * LIST_SLICES) {
         const int i = base + lane;
         int y = 0;
         uint64_t T = 0;
@@ -1802,12 +1808,11 @@ __global__ void __launch_bounds__(BT) fwd_lists_kernel(FwdArgs f, Ctl *ctl, int 
             if ((T >> j) & 1ull) tlw[(size_t)(grp * FPB + j) * (size_t)n + pos + __popc(bal & lt)] = y;
         }
     }
-    __syncthreads();
-    if (tid < FPB) {
+    if (slice == 0 && tid < FPB) {
         const int b = grp * FPB + tid;
         f.toff[64 * word + b] = (long long)word * f.tcap + (long long)b * n;
-        f.tcnt[64 * word + b] = cnt[tid];
     }
+    __syncthreads();
     if (tid == 0) {
         __threadfence();
         const unsigned prev = atomicAdd(&ctl->fwd_arrivals, 1u);
@@ -1817,7 +1822,7 @@ __global__ void __launch_bounds__(BT) fwd_lists_kernel(FwdArgs f, Ctl *ctl, int 
     if (!sh_last) return;
     __threadfence();
     // last block: chunk-task offsets over every snapshot
-    const int W = gridDim.x / FWD_GROUPS;
+    const int W = gridDim.x / PER_WORD;
     const int NS = 64 * W;
     long long carry = 0;
     for (int base = 0; base < NS; base += BT) {
@@ -2647,9 +2652,9 @@ sg_status round_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy_on, 
     f.frw = ws.frw.p;
     fwd_walk_kernel<MODEL><<<co.W * f.groups, BT, 0, st>>>(a, f);
     SG_CUDA_TRY(cudaGetLastError());
-    fwd_anc_kernel<MODEL><<<co.W * FWD_GROUPS, BT, 0, st>>>(a, f);
+    fwd_anc_kernel<MODEL><<<co.W * f.groups, BT, 0, st>>>(a, f);
     SG_CUDA_TRY(cudaGetLastError());
-    fwd_lists_kernel<<<co.W * FWD_GROUPS, BT, 0, st>>>(f, ws.ctl.p, (int)g->n);
+    fwd_lists_kernel<<<co.W * FWD_GROUPS * LIST_SLICES, BT, 0, st>>>(f, ws.ctl.p, (int)g->n);
     SG_CUDA_TRY(cudaGetLastError());
     fwd_clear_kernel<<<g->num_sms * 2, 256, 0, st>>>(f, ws.ctl.p, (int)g->n, co.W);
     SG_CUDA_TRY(cudaGetLastError());
