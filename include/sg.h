@@ -346,6 +346,10 @@ sg_status sg_select_ws(sg_graph *g, sg_workspace *ws, int32_t R, int32_t k, sg_c
  *   word_major      initial-gain task order: 1 (default) all of one 64-snapshot
  *                   word's sources before the next word's, so the tasks in
  *                   flight share that word's caches in L2; 0 source by source
+ *   tier1_direct    an initial-gain task that outgrows its warp's table with
+ *                   at least this many frontier entries still to expand goes
+ *                   straight to the dense tier, skipping the block-shared
+ *                   tables it would outgrow too (default 16; 0: never)
  * The slice width is fixed at 64 snapshots (one 64-bit word per node and
  * task) and is not a knob. */
 typedef struct {
@@ -358,6 +362,7 @@ typedef struct {
     int32_t scc;
     int32_t forward_lists;
     int32_t word_major;
+    int32_t tier1_direct;
 } sg_tuning;
 
 /* The process-wide knobs (what the sg_set_* calls set) / set all of them.

@@ -89,6 +89,7 @@ int g_mask_cache = 0;
 int g_fwd_lists = 1;
 int g_walk_groups = 32;
 int g_word_major = 1;
+int g_t1_direct = 16;
 
 Knobs knobs()
 {
@@ -103,6 +104,7 @@ Knobs knobs()
     k.scc = g_scc;
     k.fwd_lists = g_fwd_lists;
     k.word_major = g_word_major;
+    k.t1_direct = g_t1_direct;
     return k;
 }
 

@@ -42,6 +42,7 @@
 #define SG_DENSE_BLOCKS 3
 #endif
 
+
 namespace sgi {
 
 // ------------------------------------------------------------------ errors
@@ -319,6 +320,7 @@ extern int g_bu_div;
 // component skip those snapshots' walks (the landmark credit counts them)
 extern int g_scc;
 extern int g_word_major;
+extern int g_t1_direct;
 // The tunable knobs one query runs with (none changes a result).
 struct Knobs {
     int walk_groups;  // blocks per word of the forward and landmark walks
@@ -330,6 +332,7 @@ struct Knobs {
     int scc;          // SCC condensation of initial-gain sources
     int fwd_lists;    // forward per-snapshot live lists
     int word_major;   // initial-gain tasks numbered word-major (1) or source-major (0)
+    int t1_direct;    // initial-gain warp-tier overflows with this many frontier entries left skip tier 2 (0: never)
 };
 // The calling thread's current query knobs: the per-query tuning it was
 // given (t_knobs, set for the duration of one query) or else the

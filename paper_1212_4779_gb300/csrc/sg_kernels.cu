@@ -321,6 +321,7 @@ struct EngineArgs {
     int bu_div;             // mode 1: a level runs bottom-up when its frontier holds more than n / bu_div nodes
     int scc;                // initial gains: condense sources inside a landmark's strongly connected component
     int word_major;         // initial-gain task t: 1 -> (source t mod n, word t / n), 0 -> (t / W, t mod W)
+    int t1_direct;          // initial gains: a warp-tier overflow with this many frontier entries left skips tier 2 (0: never)
 };
 
 
@@ -497,10 +498,11 @@ __device__ __forceinline__ int table_slot(const WTab &T, int y, int limit)
     return -1;
 }
 
-// One task by one warp.  Returns true if the table overflowed (nothing of
-// the task was applied; the table is clean again either way).
+// One task by one warp.  Returns 0 when it completed, else (nothing of the
+// task applied; the table is clean again either way) 1 to move it to the
+// block-shared tier, 2 straight to the dense tier.
 template <int LOGC, int DIR, int MODEL, int TASK>
-__device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, long long t, int lane,
+__device__ __forceinline__ int warp_task(const EngineArgs &a, const WTab &T, long long t, int lane,
                                           unsigned long long &edges_acc, unsigned long long &wk,
                                           unsigned long long &lel)
 {
@@ -566,11 +568,14 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         for (int i = 0; i < a.lmk_k; ++i) xany |= T.xbits[i];
     const bool flists = TASK == TASK_INIT && g.fsoff && __ldg(g.fsvalid);
     unsigned long long tedges = 0;
-    int qhead = 0;
+    int qhead = 0, left = 0;
     while (true) {
         const int qtail = *(volatile int *)&T.ctr[0];
         const int ovf = *(volatile int *)&T.ctr[2];
-        if (ovf || qhead >= qtail) break;
+        if (ovf || qhead >= qtail) {
+            left = qtail - qhead;  // frontier entries not yet expanded (on overflow)
+            break;
+        }
         const int nb = min(32, qtail - qhead);
         long long base = 0;
         int vdeg = 0, heavy = 0;
@@ -705,7 +710,10 @@ __device__ __forceinline__ bool warp_task(const EngineArgs &a, const WTab &T, lo
         T.ctr[2] = 0;
     }
     __syncwarp();
-    return ovf != 0;
+    if (!ovf) return 0;
+    // an initial-gain task that overflowed with a large frontier still to
+    // expand is sent straight to the dense tier
+    return (TASK == TASK_INIT && a.t1_direct > 0 && left >= a.t1_direct) ? 2 : 1;
 }
 
 // Tier 1: tasks [0, ntasks) by dynamic chunks, one warp per task with a
@@ -739,8 +747,9 @@ __global__ void __launch_bounds__(WE_THREADS) warp_engine_kernel(EngineArgs a, i
         if (base >= ntasks) break;
         const long long tend = min(base + (long long)chunk, ntasks);
         for (long long t = base; t < tend; ++t) {
-            const bool ovf = warp_task<LOGC, DIR, MODEL, TASK>(a, T, t, lane, edges, wk, lel);
-            if (ovf && lane == 0) a.list1[atomicAdd(&ctl->l1_count, 1ull)] = (int32_t)t;
+            const int ovf = warp_task<LOGC, DIR, MODEL, TASK>(a, T, t, lane, edges, wk, lel);
+            if (ovf == 1 && lane == 0) a.list1[atomicAdd(&ctl->l1_count, 1ull)] = (int32_t)t;
+            if (ovf == 2 && lane == 0) a.list2[atomicAdd(&ctl->l2_count, 1ull)] = (int32_t)t;
         }
     }
     edges = warp_sum(edges);
@@ -2480,6 +2489,7 @@ EngineArgs engine_args(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
     a.bu_div = kn.bu_div;
     a.scc = kn.scc;
     a.word_major = kn.word_major;
+    a.t1_direct = kn.t1_direct;
     return a;
 }
 

@@ -30,9 +30,9 @@ sg_status check_tuning(const sg_tuning &t)
     if ((wg != 8 && wg != 16 && wg != 32 && wg != 64) || t.direction_mode < 0 || t.direction_mode > 2 ||
         t.direction_div < 1 || t.tier1_keys < 1 || t.tier2_keys < 1 || t.landmarks < 0 || t.landmarks > 8 ||
         (t.scc != 0 && t.scc != 1) || (t.forward_lists != 0 && t.forward_lists != 1) ||
-        (t.word_major != 0 && t.word_major != 1)) {
+        (t.word_major != 0 && t.word_major != 1) || t.tier1_direct < 0) {
         set_error("sg_tuning out of range (walk_groups 8/16/32/64, direction mode 0..2 and divisor >= 1, "
-                  "tier keys >= 1, landmarks 0..8, scc, forward_lists and word_major 0/1)");
+                  "tier keys >= 1, landmarks 0..8, scc, forward_lists and word_major 0/1, tier1_direct >= 0)");
         return SG_EINVAL;
     }
     return SG_OK;
@@ -50,6 +50,7 @@ Knobs to_knobs(const sg_tuning &t)
     k.scc = t.scc;
     k.fwd_lists = t.forward_lists;
     k.word_major = t.word_major;
+    k.t1_direct = t.tier1_direct;
     return k;
 }
 
@@ -65,6 +66,7 @@ sg_tuning from_knobs(const Knobs &k)
     t.scc = k.scc;
     t.forward_lists = k.fwd_lists;
     t.word_major = k.word_major;
+    t.tier1_direct = k.t1_direct;
     return t;
 }
 
@@ -108,7 +110,8 @@ bool cache_lookup(const char *path, const std::string &key, sg_tuning *out, doub
             json_int(line, "direction_div", &t.direction_div) && json_int(line, "tier1_keys", &t.tier1_keys) &&
             json_int(line, "tier2_keys", &t.tier2_keys) && json_int(line, "landmarks", &t.landmarks) &&
             json_int(line, "scc", &t.scc) && json_int(line, "forward_lists", &t.forward_lists) &&
-            json_int(line, "word_major", &t.word_major) && check_tuning(t) == SG_OK) {
+            json_int(line, "word_major", &t.word_major) && json_int(line, "tier1_direct", &t.tier1_direct) &&
+            check_tuning(t) == SG_OK) {
             *out = t;
             const char *p = strstr(line, "\"ms\": ");
             *ms = p ? atof(p + 6) : 0.0;
@@ -127,9 +130,9 @@ void cache_store(const char *path, const std::string &key, const sg_tuning &t, d
     fprintf(f,
             "{\"key\": \"%s\", \"walk_groups\": %d, \"direction_mode\": %d, \"direction_div\": %d, "
             "\"tier1_keys\": %d, \"tier2_keys\": %d, \"landmarks\": %d, \"scc\": %d, \"forward_lists\": %d, "
-            "\"word_major\": %d, \"ms\": %.3f}\n",
+            "\"word_major\": %d, \"tier1_direct\": %d, \"ms\": %.3f}\n",
             key.c_str(), t.walk_groups, t.direction_mode, t.direction_div, t.tier1_keys, t.tier2_keys, t.landmarks,
-            t.scc, t.forward_lists, t.word_major, ms);
+            t.scc, t.forward_lists, t.word_major, t.tier1_direct, ms);
     fclose(f);
 }
 
@@ -210,6 +213,7 @@ sg_status sg_set_tuning(const sg_tuning *t)
     SG_TRY(sg_set_landmarks(t->landmarks));
     SG_TRY(sg_set_scc_condensation(t->scc));
     g_word_major = t->word_major;
+    g_t1_direct = t->tier1_direct;
     return sg_set_forward_lists(t->forward_lists);
 }
 
@@ -295,6 +299,7 @@ sg_status sg_autotune(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t 
     try_values([](Knobs &kn, int v) { kn.t2_keys = v; }, {512, 1024, 2048});
     try_values([](Knobs &kn, int v) { kn.fwd_lists = v; }, {0, 1});
     try_values([](Knobs &kn, int v) { kn.word_major = v; }, {0, 1});
+    try_values([](Knobs &kn, int v) { kn.t1_direct = v; }, {0, 16, 64});
     if (T.e0) cudaEventDestroy(T.e0);
     if (T.e1) cudaEventDestroy(T.e1);
     dbuf_free(T.seeds, st);

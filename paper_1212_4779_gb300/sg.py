@@ -72,7 +72,7 @@ class sg_tuning(ctypes.Structure):
     _fields_ = [("walk_groups", ctypes.c_int32), ("direction_mode", ctypes.c_int32),
                 ("direction_div", ctypes.c_int32), ("tier1_keys", ctypes.c_int32), ("tier2_keys", ctypes.c_int32),
                 ("landmarks", ctypes.c_int32), ("scc", ctypes.c_int32), ("forward_lists", ctypes.c_int32),
-                ("word_major", ctypes.c_int32)]
+                ("word_major", ctypes.c_int32), ("tier1_direct", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

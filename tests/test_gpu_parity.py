@@ -109,6 +109,7 @@ def test_big_tasks_take_the_upper_tiers_and_agree(sg, limits, lmk):
     n, s, d = inputs.chung_lu_undirected(3000, 12000, 2.5, 8.0, 31)
     g, o = _both(sg, n, s, d, "uic", 0.3)
     sg.sg_set_landmarks(lmk)
+    _set_tier1_direct(sg, 0)  # every overflow passes through the block-shared tier
     res = g.select(96, 8, "uic", 0.3, 4, stats=True)
     ref = o.select(96, 8, 4, mode=oracle.DU)
     if lmk == 0:
@@ -130,6 +131,15 @@ def limits(sg):
     sg.sg_set_walk_groups(32)
     sg.sg_set_direction(1, 4)
     sg.sg_set_scc_condensation(1)
+    _set_tier1_direct(sg, 16)
+
+
+def _set_tier1_direct(sg, v):
+    """Initial-gain warp-tier overflows with >= v frontier entries left skip
+    the block-shared tier (0: never); set through the tuning struct."""
+    t = sg.sg_get_tuning()
+    t.tier1_direct = v
+    sg.sg_set_tuning(t)
 
 
 @pytest.mark.parametrize("t1,t2", [(256, 4096), (2, 16)])
@@ -313,15 +323,19 @@ def test_landmark_gives_identical_results(sg, limits, name, lmk):
         assert got == [int(x) for x in ref["counters"]]
 
 
+@pytest.mark.parametrize("direct", [0, 1, 16])
 @pytest.mark.parametrize("t1,t2", [(1, 1), (4, 32), (16, 300), (256, 4096)])
 @pytest.mark.parametrize("name", ["cl15k_wic", "cl15k_uic0.01"])
-def test_every_tier_gives_identical_results(sg, limits, name, t1, t2):
-    """Tiny table limits push tasks through all three engine tiers; the
-    seeds, gains and counters must not change."""
+def test_every_tier_gives_identical_results(sg, limits, name, t1, t2, direct):
+    """Tiny table limits push tasks through all three engine tiers, with the
+    warp tier's overflows routed through the block-shared tier (direct 0) or
+    straight to the dense tier past 1 or 16 frontier entries; the seeds,
+    gains and counters must not change."""
     wl = inputs.workload(name)
     n, s, d = wl.graph()
     g, o = _both(sg, n, s, d, wl.model, wl.p)
     limits(t1, t2)
+    _set_tier1_direct(sg, direct)
     k = 12
     res = g.select(wl.R, k, wl.model, wl.p, wl.seed, stats=True)
     ref = o.select(wl.R, k, wl.seed, mode=oracle.DU)
@@ -332,7 +346,9 @@ def test_every_tier_gives_identical_results(sg, limits, name, t1, t2):
     if t2 <= 32:
         assert res.stats["init_tier3_tasks"] > 0 and res.stats["rev_tier3_tasks"] > 0
     if t1 <= 4:
-        assert res.stats["init_tier2_tasks"] > 0 and res.stats["rev_tier2_tasks"] > 0
+        assert res.stats["rev_tier2_tasks"] > 0
+        if direct == 0:
+            assert res.stats["init_tier2_tasks"] > 0
 
 
 @pytest.mark.parametrize("heavy", [0, 2, 8, 64])

@@ -61,11 +61,11 @@ def test_batch_with_per_query_tunings_equals_oracle(sg):
     qs = [q for q in inputs.batch_queries(12) if q["n"] <= 60000][:6]
     graphs, wss, items, outs, refs = [], [], [], [], []
     variants = [dict(walk_groups=8, direction_mode=0, direction_div=4, tier1_keys=256, tier2_keys=2048,
-                     landmarks=8, scc=1, forward_lists=1, word_major=1),
+                     landmarks=8, scc=1, forward_lists=1, word_major=1, tier1_direct=16),
                 dict(walk_groups=32, direction_mode=2, direction_div=1, tier1_keys=16, tier2_keys=300,
-                     landmarks=0, scc=0, forward_lists=0, word_major=0),
+                     landmarks=0, scc=0, forward_lists=0, word_major=0, tier1_direct=0),
                 dict(walk_groups=64, direction_mode=1, direction_div=16, tier1_keys=64, tier2_keys=1024,
-                     landmarks=4, scc=1, forward_lists=1, word_major=1)]
+                     landmarks=4, scc=1, forward_lists=1, word_major=1, tier1_direct=1)]
     sg.sg_set_walk_groups(64)  # workspaces sized for every split
     try:
         for i, q in enumerate(qs):
