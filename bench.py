@@ -51,6 +51,9 @@ UNIT = "GTEPS"
 BYTES_PER_ELEMENT = 16  # hashed arc: 8-byte arc record (destination, threshold) + 8-byte state word
 BYTES_PER_ELEMENT_INDEXED = 20  # index entry: 4-byte neighbour + 8-byte live mask + 8-byte state word
 BYTES_PER_LIST_ELEMENT = 12  # per-snapshot list entry: 4-byte neighbour + 8-byte state word
+# and per expanded (node, 64-snapshot word) of a task: its 8-byte row
+# offsets and its 8-byte state word (the per-node term of the same model)
+BYTES_PER_EXPANDED_NODE = 16
 LANES_PER_SM = 128  # INT32 lanes per SM per clock (4 SMSP x 32)
 
 
@@ -647,14 +650,17 @@ def main():
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     # dominant kernel: the initial-gain tier-3 launch (cooperative engine over
-    # dense per-block arrays).  Algorithmic bytes per element: an index entry
+    # dense per-block arrays).  Algorithmic bytes: per expanded (node, word)
+    # its row offsets and state word (16 B); per element an index entry
     # (4-byte neighbour + 8-byte live mask) or arc record, plus the
     # neighbour's 8-byte state word; a per-snapshot list entry is a 4-byte
     # neighbour plus the state word.
     t3_ms = float(np.mean(t_t3))
     bpe = BYTES_PER_ELEMENT_INDEXED if (st_last["mask_cache"] or st_last["heavy_index"]) else BYTES_PER_ELEMENT
     t3_list = st_last["list_elems"][2]
-    t3_bytes = (st_last["work_elems"][0][2] - t3_list) * bpe + t3_list * BYTES_PER_LIST_ELEMENT
+    t3_keys = st_last["work_keys"][0][2]
+    t3_bytes = (t3_keys * BYTES_PER_EXPANDED_NODE + (st_last["work_elems"][0][2] - t3_list) * bpe +
+                t3_list * BYTES_PER_LIST_ELEMENT)
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = t3_bytes / (t3_ms / 1e3) / 1e9 if t3_ms > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": "coop_engine_kernel<dense> (initial gains, tier 3)",
@@ -663,8 +669,9 @@ def main():
                 "traffic_source": "profiles/coop_engine_tier3_init_rmat20_traffic.md (full-size ncu capture)",
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
                 "kernel_ms": t3_ms, "elements_per_launch": st_last["work_elems"][0][2],
-                "list_elements_per_launch": t3_list, "bytes_per_element": bpe,
-                "bytes_per_list_element": BYTES_PER_LIST_ELEMENT, "algorithmic_bytes_per_launch": t3_bytes}
+                "list_elements_per_launch": t3_list, "expanded_nodes_per_launch": t3_keys,
+                "bytes_per_element": bpe, "bytes_per_list_element": BYTES_PER_LIST_ELEMENT,
+                "bytes_per_expanded_node": BYTES_PER_EXPANDED_NODE, "algorithmic_bytes_per_launch": t3_bytes}
     t1_ms = float(np.mean(t_t1))
     alu_view = {"kernel": "warp_engine_kernel (initial gains, tier 1)", "kernel_ms": t1_ms,
                 "elements_per_launch": st_last["work_elems"][0][0],

@@ -587,7 +587,8 @@ size_t tier3_budget(int64_t n)
     // to 1.1 M nodes its three slots per SM (tier-3 tasks are latency-bound,
     // so the number of resident blocks sets their throughput)
     const size_t b = (size_t)n * 4096 * SG_DENSE_BLOCKS;
-    return std::min<size_t>((size_t)16 << 30, std::max<size_t>((size_t)64 << 20, b));
+    const size_t cap = ((size_t)16 << 30) * (size_t)std::max(1, SG_DENSE_BLOCKS / 3);
+    return std::min<size_t>(cap, std::max<size_t>((size_t)64 << 20, b));
 }
 
 // Device bytes a workspace for (W, k) takes, as ensure_workspace /

@@ -36,11 +36,22 @@
 
 #include "sg.h"
 
-// Resident 512-thread blocks per SM of the dense (tier-3) traversal engine;
-// the tier-3 slot count is this many per SM.
-#ifndef SG_DENSE_BLOCKS
-#define SG_DENSE_BLOCKS 3
+// Dense (tier-3) engine block shapes: threads per block (the warps sharing
+// one task) and resident blocks per SM, for initial-gain and for reverse
+// tasks; the workspace holds slots for the larger count per SM.
+#ifndef SG_DENSE_INIT_THREADS
+#define SG_DENSE_INIT_THREADS 384
 #endif
+#ifndef SG_DENSE_INIT_BLOCKS
+#define SG_DENSE_INIT_BLOCKS 4
+#endif
+#ifndef SG_DENSE_REV_THREADS
+#define SG_DENSE_REV_THREADS 256
+#endif
+#ifndef SG_DENSE_REV_BLOCKS
+#define SG_DENSE_REV_BLOCKS 6
+#endif
+#define SG_DENSE_BLOCKS (SG_DENSE_INIT_BLOCKS > SG_DENSE_REV_BLOCKS ? SG_DENSE_INIT_BLOCKS : SG_DENSE_REV_BLOCKS)
 
 
 namespace sgi {

@@ -1173,7 +1173,9 @@ struct SlotArgs {
 // tables run in four 256-thread blocks per SM, 4096-slot tables in two
 // 512-thread blocks.  Tasks are deep and narrow walks, so tasks in flight
 // per SM set the throughput more than threads per task.  The dense tier
-// runs three 512-thread blocks per SM (40 registers).
+// (LOGC selects its shape: 0 initial gains, 1 reverse tasks) runs four
+// 384-thread blocks per SM for initial gains and six 256-thread blocks for
+// the smaller reverse tasks (40 registers either way).
 constexpr int CO_LOGC = 12;  // the largest shared-memory table
 constexpr unsigned short QE16 = 0xFFFF;
 enum { TAB_HASH = 0, TAB_DENSE = 1 };
@@ -1184,7 +1186,8 @@ struct CoopShape {
 };
 template <int LOGC>
 struct CoopShape<TAB_DENSE, LOGC> {
-    static constexpr int T = 512, MINB = SG_DENSE_BLOCKS;
+    static constexpr int T = LOGC == 0 ? SG_DENSE_INIT_THREADS : SG_DENSE_REV_THREADS;
+    static constexpr int MINB = LOGC == 0 ? SG_DENSE_INIT_BLOCKS : SG_DENSE_REV_BLOCKS;
 };
 
 struct CoopCtl {
@@ -2554,8 +2557,12 @@ sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cuda
             SG_TRY((launch_stage<DIR, MODEL, TASK, 12>(g, ws, a, std::max(lim1, t2), io, st)));
     }
     if (ev && ev->t2) SG_CUDA_TRY(cudaEventRecord(ev->t2, st));
-    coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK, 0><<<ws.nslots, CoopShape<TAB_DENSE, 0>::T, 0, st>>>(
-        a, slot_args(ws), StageIO{ws.list2.p, &ws.ctl.p->l2_count, &ws.ctl.p->l2_next, nullptr, nullptr, 2});
+    {
+        constexpr int DV = TASK == TASK_INIT ? 0 : 1;  // dense shape by task kind
+        const int blocks = std::min(ws.nslots, g->num_sms * CoopShape<TAB_DENSE, DV>::MINB);
+        coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK, DV><<<blocks, CoopShape<TAB_DENSE, DV>::T, 0, st>>>(
+            a, slot_args(ws), StageIO{ws.list2.p, &ws.ctl.p->l2_count, &ws.ctl.p->l2_next, nullptr, nullptr, 2});
+    }
     SG_CUDA_TRY(cudaGetLastError());
     ++g_launches;
     if (ev && ev->t3) SG_CUDA_TRY(cudaEventRecord(ev->t3, st));
