@@ -158,11 +158,12 @@ sg_status sg_load_graph(int64_t n, int64_t m, const int64_t *row_ptr, const int3
 sg_status sg_set_heavy_threshold(int32_t min_degree);
 
 /* Traversal-engine limits: a task whose visited set grows past tier1_keys
- * nodes leaves its warp's shared-memory table (tier 1) for block-shared
- * shared-memory tables (tier 2: first 2048-slot tables holding up to
- * min(1024, tier2_keys / 2) nodes, four blocks per SM, then 4096-slot
- * tables, two blocks per SM), and past tier2_keys nodes for the engine
- * with dense per-slot arrays in global memory (tier 3).  Values are
+ * nodes leaves its warp's shared-memory table (tier 1) for a block-shared
+ * shared-memory table (tier 2: 2048-slot tables, four blocks per SM,
+ * holding up to min(1024, tier2_keys / 2) nodes), and past that for the
+ * engine with dense per-slot arrays in global memory (tier 3).  An
+ * initial-gain task that leaves tier 1 with a large frontier still to
+ * expand may go straight to tier 3 (sg_tuning.tier1_direct).  Values are
  * clamped to 256 and 2048 (the defaults).  A tuning and testing knob:
  * results do not depend on it.  Applies to later calls.
  * Errors: SG_EINVAL if either is < 1. */

@@ -52,6 +52,12 @@
 #define SG_DENSE_REV_BLOCKS 6
 #endif
 #define SG_DENSE_BLOCKS (SG_DENSE_INIT_BLOCKS > SG_DENSE_REV_BLOCKS ? SG_DENSE_INIT_BLOCKS : SG_DENSE_REV_BLOCKS)
+// log2 of the shared-memory table slots of the reverse tasks' block-shared
+// tier (11: 2048-slot tables, four 256-thread blocks per SM, tasks past 1024
+// keys go on to the dense tier; 12: 4096-slot tables, two 512-thread blocks)
+#ifndef SG_REV_T2_LOGC
+#define SG_REV_T2_LOGC 11
+#endif
 
 
 namespace sgi {

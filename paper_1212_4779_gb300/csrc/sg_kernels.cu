@@ -2542,11 +2542,12 @@ sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cuda
     }
     if (ev && ev->t1) SG_CUDA_TRY(cudaEventRecord(ev->t1, st));
     {
-        // Tier 2: one shared-memory stage, chosen by the kind of task.
-        // Initial-gain tasks run in 2048-slot tables, four per SM (a
-        // 4096-slot second stage for their 1-2 K-node tasks was slower than
-        // sending those to tier 3); reverse tasks (about 1 K nodes on
-        // average) run in 4096-slot tables, two per SM.
+        // Tier 2: one shared-memory stage.  Initial-gain tasks run in
+        // 2048-slot tables, four per SM (a 4096-slot second stage for their
+        // 1-2 K-node tasks was slower than sending those to tier 3); so do
+        // reverse tasks by default (4096-slot tables, two per SM, measured
+        // 34 ms slower per select once the dense tier ran six reverse blocks
+        // per SM).
         const int lim1 = std::max(1, std::min(knobs().t1_keys, (1 << T1_LOGC) / 2));
         const int t2 = std::max(1, std::min(knobs().t2_keys, (1 << CO_LOGC) / 2));
         Ctl *ctl = ws.ctl.p;
@@ -2554,7 +2555,8 @@ sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cuda
         if (TASK == TASK_INIT)
             SG_TRY((launch_stage<DIR, MODEL, TASK, 11>(g, ws, a, std::max(lim1, std::min(1 << 10, t2)), io, st)));
         else
-            SG_TRY((launch_stage<DIR, MODEL, TASK, 12>(g, ws, a, std::max(lim1, t2), io, st)));
+            SG_TRY((launch_stage<DIR, MODEL, TASK, SG_REV_T2_LOGC>(
+                g, ws, a, std::max(lim1, std::min((1 << SG_REV_T2_LOGC) / 2, t2)), io, st)));
     }
     if (ev && ev->t2) SG_CUDA_TRY(cudaEventRecord(ev->t2, st));
     {
