@@ -161,9 +161,9 @@ sg_status sg_set_heavy_threshold(int32_t min_degree);
  * nodes leaves its warp's shared-memory table (tier 1) for a block-shared
  * shared-memory table (tier 2: 2048-slot tables, four blocks per SM,
  * holding up to min(1024, tier2_keys / 2) nodes), and past that for the
- * engine with dense per-slot arrays in global memory (tier 3).  An
- * initial-gain task that leaves tier 1 with a large frontier still to
- * expand may go straight to tier 3 (sg_tuning.tier1_direct).  Values are
+ * engine with dense per-slot arrays in global memory (tier 3).  A task
+ * that leaves tier 1 with a large frontier still to expand may go straight
+ * to tier 3 (sg_tuning.tier1_direct).  Values are
  * clamped to 256 and 2048 (the defaults).  A tuning and testing knob:
  * results do not depend on it.  Applies to later calls.
  * Errors: SG_EINVAL if either is < 1. */
@@ -347,10 +347,11 @@ sg_status sg_select_ws(sg_graph *g, sg_workspace *ws, int32_t R, int32_t k, sg_c
  *   word_major      initial-gain task order: 1 (default) all of one 64-snapshot
  *                   word's sources before the next word's, so the tasks in
  *                   flight share that word's caches in L2; 0 source by source
- *   tier1_direct    an initial-gain task that outgrows its warp's table with
- *                   at least this many frontier entries still to expand goes
- *                   straight to the dense tier, skipping the block-shared
- *                   tables it would outgrow too (default 16; 0: never)
+ *   tier1_direct    a task (initial gains or reverse update) that outgrows
+ *                   its warp's table with at least this many frontier
+ *                   entries still to expand goes straight to the dense tier,
+ *                   skipping the block-shared table it would likely outgrow
+ *                   too (default 16; 0: never)
  * The slice width is fixed at 64 snapshots (one 64-bit word per node and
  * task) and is not a knob. */
 typedef struct {

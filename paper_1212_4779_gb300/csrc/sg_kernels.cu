@@ -321,7 +321,7 @@ struct EngineArgs {
     int bu_div;             // mode 1: a level runs bottom-up when its frontier holds more than n / bu_div nodes
     int scc;                // initial gains: condense sources inside a landmark's strongly connected component
     int word_major;         // initial-gain task t: 1 -> (source t mod n, word t / n), 0 -> (t / W, t mod W)
-    int t1_direct;          // initial gains: a warp-tier overflow with this many frontier entries left skips tier 2 (0: never)
+    int t1_direct;          // a warp-tier overflow with this many frontier entries left skips tier 2 (0: never)
 };
 
 
@@ -711,9 +711,9 @@ __device__ __forceinline__ int warp_task(const EngineArgs &a, const WTab &T, lon
     }
     __syncwarp();
     if (!ovf) return 0;
-    // an initial-gain task that overflowed with a large frontier still to
-    // expand is sent straight to the dense tier
-    return (TASK == TASK_INIT && a.t1_direct > 0 && left >= a.t1_direct) ? 2 : 1;
+    // a task that overflowed with a large frontier still to expand is sent
+    // straight to the dense tier
+    return (a.t1_direct > 0 && left >= a.t1_direct) ? 2 : 1;
 }
 
 // Tier 1: tasks [0, ntasks) by dynamic chunks, one warp per task with a
@@ -2595,10 +2595,12 @@ sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
 {
     EngineArgs a = engine_args(g, ws, co, heavy_on);
     a.ntasks = (long long)g->n * co.W;
-    const int K = std::min(std::min(knobs().landmarks, g->lmk_count), MAX_LMK);
+    const bool weighted = SG_LMK_WEIGHTED && (MODEL == MODEL_WIC || co.lt);
+    const int32_t *lmk = weighted ? g->lmk_nodes_w : g->lmk_nodes;
+    const int K = std::min(std::min(knobs().landmarks, weighted ? g->lmk_count_w : g->lmk_count), MAX_LMK);
     if (K > 0) {
         a.lmk_k = K;
-        for (int i = 0; i < K; ++i) a.lmk_x[i] = g->lmk_nodes[i];
+        for (int i = 0; i < K; ++i) a.lmk_x[i] = lmk[i];
         const size_t nw = (size_t)g->n * co.W;
         SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_rx.p, 0, nw * 8 * MAX_LMK, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_ux.p, 0, nw * 8 * MAX_LMK, st));
