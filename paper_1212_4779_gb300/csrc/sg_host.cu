@@ -328,29 +328,6 @@ sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> 
         }
         g->lmk_count = (int32_t)top.size();
         for (size_t i = 0; i < top.size(); ++i) g->lmk_nodes[i] = top[i].second;
-        // for the weighted cascade (and the linear threshold model, same
-        // weights): the 8 largest expected live out-degrees,
-        // sum over out-arcs u -> v of 1 / indeg(v), among the same rows
-        std::vector<double> live((size_t)n, 0.0);
-        for (int64_t u = 0; u < n; ++u) {
-            if (rp[(size_t)u + 1] - rp[(size_t)u] < 32) continue;
-            double acc = 0.0;
-            for (int32_t e = rp[(size_t)u]; e < rp[(size_t)u + 1]; ++e) {
-                const int32_t v = col[(size_t)e];
-                acc += 1.0 / (double)(crp[(size_t)v + 1] - crp[(size_t)v]);
-            }
-            live[(size_t)u] = acc;
-        }
-        std::vector<std::pair<double, int32_t>> topw;
-        for (int64_t v = 0; v < n; ++v)
-            if (live[(size_t)v] > 0.0) topw.emplace_back(live[(size_t)v], (int32_t)v);
-        std::stable_sort(topw.begin(), topw.end(),
-                         [](const std::pair<double, int32_t> &x, const std::pair<double, int32_t> &y) {
-                             return x.first > y.first;
-                         });
-        if (topw.size() > 8) topw.resize(8);
-        g->lmk_count_w = (int32_t)topw.size();
-        for (size_t i = 0; i < topw.size(); ++i) g->lmk_nodes_w[i] = topw[i].second;
     }
     g->nh_out = (int32_t)ho.hrow.size();
     g->nh_in = (int32_t)hi.hrow.size();

@@ -55,11 +55,6 @@
 // log2 of the shared-memory table slots of the reverse tasks' block-shared
 // tier (11: 2048-slot tables, four 256-thread blocks per SM, tasks past 1024
 // keys go on to the dense tier; 12: 4096-slot tables, two 512-thread blocks)
-// Landmarks of weighted-cascade and linear-threshold queries: 1 by expected
-// live out-degree, 0 by out-degree (as for the uniform cascade).
-#ifndef SG_LMK_WEIGHTED
-#define SG_LMK_WEIGHTED 0
-#endif
 #ifndef SG_REV_T2_LOGC
 #define SG_REV_T2_LOGC 11
 #endif
@@ -297,8 +292,6 @@ struct sg_graph {
     sgi::DBuf<uint2> fw;      // built on first WIC query
     int32_t lmk_nodes[8] = {-1, -1, -1, -1, -1, -1, -1, -1};  // landmarks: largest out-degrees (>= 32)
     int32_t lmk_count = 0;
-    int32_t lmk_nodes_w[8] = {-1, -1, -1, -1, -1, -1, -1, -1};  // ... by expected live out-degree under 1/indeg weights
-    int32_t lmk_count_w = 0;
     // heavy rows (static)
     int32_t heavy_min_deg = 0;
     int32_t nh_out = 0, nh_in = 0;

@@ -2595,12 +2595,10 @@ sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
 {
     EngineArgs a = engine_args(g, ws, co, heavy_on);
     a.ntasks = (long long)g->n * co.W;
-    const bool weighted = SG_LMK_WEIGHTED && (MODEL == MODEL_WIC || co.lt);
-    const int32_t *lmk = weighted ? g->lmk_nodes_w : g->lmk_nodes;
-    const int K = std::min(std::min(knobs().landmarks, weighted ? g->lmk_count_w : g->lmk_count), MAX_LMK);
+    const int K = std::min(std::min(knobs().landmarks, g->lmk_count), MAX_LMK);
     if (K > 0) {
         a.lmk_k = K;
-        for (int i = 0; i < K; ++i) a.lmk_x[i] = lmk[i];
+        for (int i = 0; i < K; ++i) a.lmk_x[i] = g->lmk_nodes[i];
         const size_t nw = (size_t)g->n * co.W;
         SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_rx.p, 0, nw * 8 * MAX_LMK, st));
         SG_CUDA_TRY(cudaMemsetAsync(ws.lmk_ux.p, 0, nw * 8 * MAX_LMK, st));
