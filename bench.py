@@ -16,7 +16,9 @@ by the library; ms_per_step is the k-seed select time.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With --impl reference the CPU oracle (the plain StaticGreedyDU of oracle/)
-is timed on the host cores on a bounded sample of the same workload.
+is timed on the host cores on a bounded sample of the same workload;
+--workload oracle_select times the oracle's whole selection at full R
+(CPU only, about 40 s on 16 cores for the default query).
 Under torchrun each rank runs an independent replica (the path has no
 cross-GPU exchange); value is the sum over ranks.
 """
@@ -231,6 +233,31 @@ def run_reference(args, wl):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_oracle_select(args, wl):
+    """The oracle's whole k-seed selection of the workload, at full R, on
+    the host cores: lazy forward evaluation (StaticGreedyCELF, which the
+    pins prove equal to Algorithm 2; the oracle's Algorithm 2 route itself
+    walks every (w, r, u) of the reverse update, about 2.2 T snapshot-edges
+    here, out of reach), timed once per step.  The select time to compare
+    with the GPU's ms_per_step."""
+    import oracle
+
+    n, s, d = wl.graph()
+    cores = os.cpu_count() or 1
+    g = oracle.Graph(n, s, d, wl.model, wl.p)
+    times, out = [], None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = g.select(wl.R, wl.k, wl.seed, mode=oracle.CELF, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    line = {"impl": "oracle", "metric": "k-seed select time, oracle StaticGreedyCELF (full R)",
+            "value": float(np.mean(times)) * 1e3, "unit": "ms", "steps": args.steps, "higher_is_better": False,
+            "config": {"workload": wl_desc(wl)}, "cores": cores, "celf_evaluations": int(out["evals"]),
+            "init_and_forward_snapshot_edges": [int(x) for x in out["counters"][:2]]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -564,6 +591,7 @@ def main():
     ap.add_argument("--served-scale", type=int, default=22, help="served: R-MAT scale of the large graph")
     ap.add_argument("--spread-R", type=int, default=20000, help="spread: snapshots of the evaluation")
     ap.add_argument("--celf-workload", default="rmat20_wic", help="celf: the query compared with the dynamic update")
+    ap.add_argument("--oracle-workload", default="rmat20_wic", help="oracle_select: the query the oracle selects on")
     ap.add_argument("--mask-cache", type=int, default=0, choices=[0, 1],
                     help="1: evaluate every arc's coins once per query into the live-mask cache")
     ap.add_argument("--no-summary", action="store_true",
@@ -584,6 +612,8 @@ def main():
         return run_spread_bench(args)
     if args.workload == "celf" and args.impl == "ours":
         return run_celf_bench(args)
+    if args.workload == "oracle_select":
+        return run_oracle_select(args, inputs.workload(args.oracle_workload))
     wl = inputs.workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, wl)
