@@ -298,6 +298,8 @@ def run_batched(args):
     __graft_entry__.build()
     from paper_1212_4779_gb300 import sg
 
+    apply_knobs(sg, args)
+
     sg.sg_set_mask_cache(args.mask_cache)
     qs = inputs.batch_queries(args.queries)
     coo = _batch_graphs(qs)
@@ -444,6 +446,8 @@ def run_served(args):
     __graft_entry__.build()
     from paper_1212_4779_gb300 import serve, sg
 
+    apply_knobs(sg, args)
+
     sg.sg_set_mask_cache(args.mask_cache)
     qs = inputs.batch_queries(64)
     coo = _batch_graphs(qs)
@@ -480,6 +484,8 @@ def run_spread_bench(args):
 
     __graft_entry__.build()
     from paper_1212_4779_gb300 import sg
+
+    apply_knobs(sg, args)
 
     wl = inputs.workload("rmat20_wic")
     n, s, d = wl.graph()
@@ -527,7 +533,7 @@ def run_spread_bench(args):
                                    f"on {R_eval} fresh snapshots (hash seed {seed_eval})",
                        "l2": "inputs larger than L2 (graph 100 MB + 2-4 GB of per-word state per launch)"},
             "spread_estimate": total / R_eval, "snapshot_edges_per_step": edges,
-            "gpu_launches": args.steps * -(-W_eval // max(1, min(W_eval, (4 << 30) // (n * 24)))),
+            "gpu_launches": args.steps * -(-W_eval // max(1, min(W_eval, (8 << 30) // (n * 24)))),
             "cpu_baseline": cpu, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
@@ -544,6 +550,8 @@ def run_celf_bench(args):
 
     __graft_entry__.build()
     from paper_1212_4779_gb300 import sg
+
+    apply_knobs(sg, args)
 
     wl = inputs.workload(args.celf_workload)
     n, s, d = wl.graph()

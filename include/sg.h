@@ -211,7 +211,8 @@ sg_status sg_set_scc_condensation(int32_t enable);
 
 /* Direction-optimising switch of the level-synchronous walks (the forward
  * dynamic update's walk from each new seed, its walk back over the seed's
- * ancestors, the landmark walks of the initial gains, and sg_spread).  A
+ * ancestors, and the landmark walks of the initial gains; sg_spread's
+ * walks, which hash their coins in registers, stay top-down).  A
  * top-down level expands every frontier node's arcs; a bottom-up level
  * instead lets every node still missing some snapshot bits scan its arcs
  * from the other side (in-arcs of a forward walk) for frontier nodes with
@@ -271,7 +272,7 @@ sg_status sg_select_celf(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64
  * A multi-source bit-sliced traversal, one 64-snapshot word per block, with
  * the coins hashed in registers (no per-query cache is used).  S: host or
  * device int32[s_count]; out_total: host or device int64; out_edges: host.
- * Synchronises `stream` before returning; uses up to ~4 GiB of scratch.
+ * Synchronises `stream` before returning; uses up to ~8 GiB of scratch.
  * Errors: SG_EINVAL for a NULL graph/output, s_count < 0, a seed outside
  * [0, n), R outside [1, 2^24) or an invalid cascade; SG_ENOMEM; SG_ECUDA. */
 sg_status sg_spread(sg_graph *g, int32_t R, sg_cascade c, uint64_t seed, const int32_t *S, int32_t s_count,

@@ -2755,28 +2755,28 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
 {
     const size_t n = (size_t)g->n;
     // words per launch: dense vis/pend (8 B each) and two level queues (4 B
-    // each) per node and word, within 4 GiB
-    // LT: both orders of the chunk's live-mask cache as well
-    const size_t per_word = n * 32 + (co.lt ? (size_t)g->m * 16 : 0);
-    const int wc = (int)std::max<size_t>(1, std::min<size_t>((size_t)co.W, ((size_t)4 << 30) / per_word));
-    DBuf<unsigned long long> vis, pend, fr, lmc;
+    // each) per node and word (LT: both orders of the chunk's live-mask
+    // cache as well), within 8 GiB, split into launches of equal size (one
+    // block per word: a short last launch would leave SMs idle).  The spread
+    // walks stay top-down: they hash coins in registers, and a bottom-up
+    // level would hash every in-arc of every node not yet reached (measured
+    // on R-MAT 20, 20,000 snapshots: 7.97 s against 0.69 s top-down).
+    const size_t per_word = n * 24 + (co.lt ? (size_t)g->m * 16 : 0);
+    const int cap = (int)std::max<size_t>(1, std::min<size_t>((size_t)co.W, ((size_t)8 << 30) / per_word));
+    const int nl = (co.W + cap - 1) / cap;
+    const int wc = (co.W + nl - 1) / nl;
+    DBuf<unsigned long long> vis, pend, lmc;
     DBuf<int32_t> qa, qb;
     sg_status rc = SG_OK;
     if (co.lt && (rc = dbuf_alloc(lmc, (size_t)wc * (size_t)g->m * 2, st)) != SG_OK) return rc;
     if ((rc = dbuf_alloc(vis, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(pend, (size_t)wc * n, st)) != SG_OK ||
-        (rc = dbuf_alloc(qa, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(qb, (size_t)wc * n, st)) != SG_OK ||
-        (rc = dbuf_alloc(fr, (size_t)wc * n, st)) != SG_OK) {
+        (rc = dbuf_alloc(qa, (size_t)wc * n, st)) != SG_OK || (rc = dbuf_alloc(qb, (size_t)wc * n, st)) != SG_OK) {
         dbuf_free(vis, st);
         dbuf_free(pend, st);
         dbuf_free(qa, st);
         dbuf_free(qb, st);
-        dbuf_free(fr, st);
         dbuf_free(lmc, st);
         return rc;
-    }
-    if (cudaMemsetAsync(fr.p, 0, (size_t)wc * n * 8, st) != cudaSuccess) {
-        set_error("sg_spread: memset failed");
-        rc = SG_ECUDA;
     }
     EngineArgs a{};
     a.spin = g_wait_polls;
@@ -2808,7 +2808,7 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
             a.g.lm_in = lmc.p + cm;
             a.g.lm_w0 = w0;
         }
-        SpreadArgs sp{vis.p, pend.p, qa.p, qb.p, d_S, ns, w0, 1, d_total, d_edges, fr.p};
+        SpreadArgs sp{vis.p, pend.p, qa.p, qb.p, d_S, ns, w0, 1, d_total, d_edges, nullptr};
         if (model == MODEL_WIC) spread_kernel<MODEL_WIC><<<words, BT, 0, st>>>(a, sp);
         else spread_kernel<MODEL_UIC><<<words, BT, 0, st>>>(a, sp);
         if (cudaGetLastError() != cudaSuccess) {
@@ -2821,7 +2821,6 @@ sg_status run_spread(sg_graph *g, const Coins &co, int model, const int32_t *d_S
     dbuf_free(pend, st);
     dbuf_free(qa, st);
     dbuf_free(qb, st);
-    dbuf_free(fr, st);
     dbuf_free(lmc, st);
     return rc;
 }
