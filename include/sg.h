@@ -163,8 +163,8 @@ sg_status sg_set_heavy_threshold(int32_t min_degree);
  * holding up to min(1024, tier2_keys / 2) nodes), and past that for the
  * engine with dense per-slot arrays in global memory (tier 3).  A task
  * that leaves tier 1 with a large frontier still to expand may go straight
- * to tier 3 (sg_tuning.tier1_direct).  Values are
- * clamped to 256 and 2048 (the defaults).  A tuning and testing knob:
+ * to tier 3 (sg_tuning.tier1_direct).  Values are clamped to 256 and
+ * 2048; the defaults are 64 and 2048.  A tuning and testing knob:
  * results do not depend on it.  Applies to later calls.
  * Errors: SG_EINVAL if either is < 1. */
 sg_status sg_set_engine_limits(int32_t tier1_keys, int32_t tier2_keys);

@@ -185,7 +185,7 @@ def test_real_bounded_wait_runs_out_and_reports_timeout(sg):
         assert r.stats["status_flags"] == 0
         assert np.array_equal(r.seeds, want["seeds"]) and np.array_equal(r.gains, want["gains"])
     finally:
-        sg.sg_set_engine_limits(256, 2048)
+        sg.sg_set_engine_limits(64, 2048)
     r = g.select(100, 10, "wic", 0.0, 7)
     assert np.array_equal(r.seeds, want["seeds"]) and np.array_equal(r.gains, want["gains"])
     g.close()

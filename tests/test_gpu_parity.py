@@ -122,7 +122,7 @@ def test_big_tasks_take_the_upper_tiers_and_agree(sg, limits, lmk):
 @pytest.fixture
 def limits(sg):
     yield sg.sg_set_engine_limits
-    sg.sg_set_engine_limits(256, 4096)
+    sg.sg_set_engine_limits(64, 2048)
     sg.sg_set_heavy_threshold(2)
     sg.sg_set_landmarks(8)
     sg.sg_set_snapshot_lists(1)
