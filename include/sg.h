@@ -516,11 +516,12 @@ sg_status sg_debug_inject_flags(int32_t flags);
 /* Testing hook: the number of polls a bounded device-side wait of the
  * traversal engines makes before it gives up (an idle warp waiting for work
  * in a block-shared queue, a warp waiting for a claimed queue entry to
- * land; each poll sleeps 32-64 ns).  A wait that runs out sets flag 2 in
+ * land; a claimed entry's poll sleeps 32 ns, an idle warp's poll sleeps
+ * 64 ns doubling up to 1 us).  A wait that runs out sets flag 2 in
  * the query's device flags and returns, and the query reports SG_ETIMEOUT
  * as described in the conventions above; the engine's per-block state is
  * cleaned up so the next query is exact.  0 restores the default (2^22
- * polls, about a second).  Applies to queries started later, on every
+ * polls: a few seconds at most).  Applies to queries started later, on every
  * thread.  Errors: SG_EINVAL if polls < 0. */
 sg_status sg_debug_set_wait_limit(int64_t polls);
 

@@ -412,6 +412,7 @@ void free_workspace(sg_workspace &ws, cudaStream_t st)
     dbuf_free(ws.anc_cnt, st);
     dbuf_free(ws.lmk_rx, st);
     dbuf_free(ws.lmk_ux, st);
+    dbuf_free(ws.lmk_any, st);
     dbuf_free(ws.lmk_U, st);
     dbuf_free(ws.lmk_H, st);
     dbuf_free(ws.lmk_E, st);
@@ -658,6 +659,7 @@ sg_status ensure_workspace(sg_graph *g, sg_workspace &ws, int32_t W, int32_t k, 
         SG_TRY(dbuf_alloc(ws.anc_cnt, (size_t)W * (size_t)ws.fq_groups, st));
         SG_TRY(dbuf_alloc(ws.lmk_rx, nw * 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_ux, nw * 8, st));
+        SG_TRY(dbuf_alloc(ws.lmk_any, nw, st));
         SG_TRY(dbuf_alloc(ws.lmk_U, ((size_t)64 * W) << 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_H, ((size_t)64 * W) << 8, st));
         SG_TRY(dbuf_alloc(ws.lmk_E, ((size_t)64 * W) << 8, st));

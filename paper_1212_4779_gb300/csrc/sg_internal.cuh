@@ -58,6 +58,9 @@
 #ifndef SG_REV_T2_LOGC
 #define SG_REV_T2_LOGC 11
 #endif
+#ifndef SG_IDLE_NS_MAX
+#define SG_IDLE_NS_MAX 1024
+#endif
 
 
 namespace sgi {
@@ -238,6 +241,7 @@ struct sg_workspace {
     sgi::DBuf<int32_t> anc_cnt;          // [W][G]
     sgi::DBuf<unsigned long long> lmk_rx;    // [W][n][8] landmark reach bits (R(x_i) membership)
     sgi::DBuf<unsigned long long> lmk_ux;    // [W][n][8] ... and which landmarks the node reaches
+    sgi::DBuf<unsigned long long> lmk_any;   // [W][n] OR over the landmarks of the R(x_i) bits
     sgi::DBuf<int32_t> lmk_U, lmk_H;         // [64W << K] union sizes / membership histogram
     sgi::DBuf<unsigned long long> lmk_E, lmk_HE;  // ... their out-degree sums
     sgi::DBuf<unsigned long long> slot_vis;  // tier-3 slots: [slot][n][2] visited / pending words

@@ -312,6 +312,7 @@ struct EngineArgs {
     int lmk_x[MAX_LMK];
     const unsigned long long *lmk_rx;
     const unsigned long long *lmk_ux;
+    const unsigned long long *lmk_any;  // [W][n]: OR over i of the lmk_rx words
     const int32_t *lmk_U;
     const unsigned long long *lmk_E;
     long long ntasks;       // TASK_INIT: n * W
@@ -340,10 +341,18 @@ __device__ __forceinline__ const unsigned long long *lmk_bits(const unsigned lon
     return base + (((size_t)word * (size_t)a.g.n + (size_t)y) << 3);
 }
 
+// PRE: first test the union word lmk_any (8 bytes) and read the eight
+// per-landmark words only where y lies in some landmark's set in a snapshot
+// the task credits.  It pays in the shared-memory tiers; in the dense tier,
+// whose arrivals mostly need the per-landmark words anyway, the extra
+// dependent load made the launch slower (269.0 against 263.4 ms on R-MAT
+// 20, while the block-shared tier went from 9.7 to 5.1 ms).
+template <bool PRE>
 __device__ __forceinline__ uint64_t lmk_filter(const EngineArgs &a, int word, int y, uint64_t ml,
                                                const unsigned long long *xbits, uint64_t xany)
 {
     if (!(ml & xany)) return ml;
+    if (PRE && !(ml & xany & __ldg(a.lmk_any + (size_t)word * (size_t)a.g.n + (size_t)y))) return ml;
     const unsigned long long *p = lmk_bits(a.lmk_rx, a, word, y);
     uint64_t drop = 0;
 #pragma unroll
@@ -638,7 +647,7 @@ __device__ __forceinline__ int warp_task(const EngineArgs &a, const WTab &T, lon
                 // nodes reaching v* in this snapshot were settled by the ancestor pass
                 if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
                     ml = 0;
-                if (TASK == TASK_INIT) ml = lmk_filter(a, word, y, ml, T.xbits, xany);
+                if (TASK == TASK_INIT) ml = lmk_filter<true>(a, word, y, ml, T.xbits, xany);
                 if (ml) {
                     const int h = table_slot<LOGC>(T, y, LIMIT);
                     if (h >= 0) {
@@ -1383,7 +1392,8 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                 if (lane == 0) c.err = 1;
                 break;
             }
-            __nanosleep(64);
+            // idle warps back off: 64 ns doubling up to SG_IDLE_NS_MAX (1 us)
+            __nanosleep((unsigned)min((long long)SG_IDLE_NS_MAX, 64ll << min(idle - 1, 10ll)));
             continue;
         }
         idle = 0;
@@ -1395,9 +1405,9 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
             const int idx = T.take(qb + lane, c, a.spin);
             if (idx >= 0) {
                 F = atomicExch(&T.pendr(idx), 0ull);
+                Row rr = row_ref<DIR, MODEL, SLICE>(g, co, T.node(idx), word, rs);
                 const uint64_t Fp = F;
                 uint64_t rest = 0;
-                Row rr = row_ref<DIR, MODEL, SLICE>(g, co, T.node(idx), word, rs);
                 if (TASK == TASK_INIT && flists) {
                     rest = pick_rows<DIR, SLICE>(g, co, T.node(idx), word, F, rr);
                     // the other bits go back to pending; re-queue unless an
@@ -1415,6 +1425,25 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
                     tedges += (unsigned long long)__popcll(Fp & ~rest) * (unsigned long long)rr.deg;
             }
         }
+        // The arrival filters: ancestors already credited (reverse tasks),
+        // landmark sets (initial gains).
+        auto keep = [&](int y, uint64_t ml) -> uint64_t {
+            if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
+                return 0ull;
+            if (TASK == TASK_INIT) ml = lmk_filter<TAB == TAB_HASH>(a, word, y, ml, c.xbits, xany);
+            return ml;
+        };
+        // After the visited-word atomic at idx returned old: record the new
+        // bits, count them (initial gains count (node, snapshot) pairs as
+        // they are first reached) and queue the node unless it is pending.
+        auto settle = [&](int y, int idx, uint64_t ml, uint64_t old) {
+            const uint64_t nw = ml & ~old;
+            if (!nw) return;
+            if (TASK == TASK_INIT) acnt += __popcll(nw);
+            if (TAB == TAB_DENSE && old == 0) T.note_new(y, c);
+            const uint64_t oldp = atomicOr(&T.pendr(idx), (unsigned long long)nw);
+            if (oldp == 0) T.put(atomicAdd(&c.tail, 1), idx);
+        };
         int incl = vdeg;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1424,8 +1453,10 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
         const int total = __shfl_sync(FULL, incl, 31);
         const int excl = incl - vdeg;
         if (lane == 0) elems += (unsigned long long)total;
-        for (int abase = 0; abase < total; abase += 32) {
-            const int j = abase + lane;
+        // Element j of the batch: its neighbour y and the state bits it
+        // carries there (0 when j is past the end or nothing is live).
+        // Warp-collective (shuffles): every lane calls it with its own j.
+        auto fetch = [&](int j, int &y) -> uint64_t {
             int lo = 0;
 #pragma unroll
             for (int step = 16; step >= 1; step >>= 1) {
@@ -1441,26 +1472,17 @@ __device__ __forceinline__ unsigned long long coop_expand(const EngineArgs &a, C
             const uint32_t itm1 = DIR == DIR_FWD ? co.uic_tm1 : __shfl_sync(FULL, rtm1, lo);
             const uint64_t iF = __shfl_sync(FULL, F, lo);
             const uint64_t ilive = TASK == TASK_INIT ? __shfl_sync(FULL, live, lo) : 0ull;
-            if (j < total) {
-                int y;
-                uint64_t ml = elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y, ilive);
-                if (TASK == TASK_REVT && ml && ((__ldg(a.anc + (size_t)word * g.n + y) >> (rs & 63u)) & 1ull))
-                    ml = 0;
-                if (TASK == TASK_INIT) ml = lmk_filter(a, word, y, ml, c.xbits, xany);
-                if (ml) {
-                    const int idx = T.slot(y, limit, c);
-                    if (idx >= 0) {
-                        const uint64_t old = atomicOr(&T.visr(idx), (unsigned long long)ml);
-                        const uint64_t nw = ml & ~old;
-                        if (nw) {
-                            // initial gains count (node, snapshot) pairs as they are first reached
-                            if (TASK == TASK_INIT) acnt += __popcll(nw);
-                            if (TAB == TAB_DENSE && old == 0) T.note_new(y, c);
-                            const uint64_t oldp = atomicOr(&T.pendr(idx), (unsigned long long)nw);
-                            if (oldp == 0) T.put(atomicAdd(&c.tail, 1), idx);
-                        }
-                    }
-                }
+            y = 0;
+            if (j >= total) return 0ull;
+            return elem<DIR, MODEL, SLICE>(g, co, ib, ih, itm1, j - iex, iF, rs, y, ilive);
+        };
+        for (int abase = 0; abase < total; abase += 32) {
+            int y;
+            const uint64_t raw = fetch(abase + lane, y);
+            const uint64_t ml = keep(y, raw);
+            if (ml) {
+                const int idx = T.slot(y, limit, c);
+                if (idx >= 0) settle(y, idx, ml, atomicOr(&T.visr(idx), (unsigned long long)ml));
             }
         }
         __syncwarp();
@@ -1879,7 +1901,7 @@ __global__ void __launch_bounds__(256) fwd_clear_kernel(FwdArgs f, Ctl *ctl, int
 // every node's landmark record (zero on entry): R(G'_r, x_i) into rx,
 // U(G'_r, x_i) into ux.
 struct LmkArgs {
-    unsigned long long *rx, *ux, *pendf, *E, *HE;
+    unsigned long long *rx, *ux, *any, *pendf, *E, *HE;
     int32_t *fq_a, *fq_b, *U, *H;
     int groups;  // blocks per word (8, 16, 32 or 64)
     unsigned long long *frw;  // [W][n] bottom-up frontier bits (zero between levels)
@@ -1970,7 +1992,8 @@ __global__ void __launch_bounds__(BT) spread_kernel(EngineArgs a, SpreadArgs sp)
 
 // Histogram, per snapshot r, of the landmark-membership mask
 // m_r(y) = {i : y in R(G'_r, x_i)} over the nodes with m_r(y) nonempty
-// (count and out-degree sum), in H / HE [(r << K) + m].
+// (count and out-degree sum), in H / HE [(r << K) + m]; any[w][y] = the
+// OR of y's eight R(x_i) words.
 __global__ void __launch_bounds__(256) landmark_hist_kernel(EngineArgs a, LmkArgs l)
 {
     const int n = a.g.n, K = a.lmk_k, W = a.co.W;
@@ -1987,6 +2010,7 @@ __global__ void __launch_bounds__(256) landmark_hist_kernel(EngineArgs a, LmkArg
             rx[i] = i < K ? rec[i] : 0ull;
             any |= rx[i];
         }
+        l.any[t] = any;
         if (!any) continue;
         const unsigned long long d = (unsigned long long)(__ldg(a.g.rp + y + 1) - __ldg(a.g.rp + y));
         while (any) {
@@ -2482,6 +2506,7 @@ EngineArgs engine_args(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
     for (int i = 0; i < MAX_LMK; ++i) a.lmk_x[i] = -1;
     a.lmk_rx = ws.lmk_rx.p;
     a.lmk_ux = ws.lmk_ux.p;
+    a.lmk_any = ws.lmk_any.p;
     a.lmk_U = ws.lmk_U.p;
     a.lmk_E = ws.lmk_E.p;
     a.ntasks = 0;
@@ -2605,6 +2630,7 @@ sg_status init_gains_t(sg_graph *g, sg_workspace &ws, const Coins &co, int heavy
         LmkArgs l;
         l.rx = ws.lmk_rx.p;
         l.ux = ws.lmk_ux.p;
+        l.any = ws.lmk_any.p;
         l.pendf = ws.pendf.p;
         l.fq_a = ws.fq_a.p;
         l.fq_b = ws.fq_b.p;

@@ -558,6 +558,38 @@ def test_rmat20_full_initial_gains_equal_oracle(sg, rmat20, rmat20_oracle):
     assert e_gpu == int(rmat20_oracle["counters"][0])
 
 
+def test_rmat20_served_requests_equal_oracle(sg, rmat20):
+    """Full size through the server: two requests of the served trace's
+    shape (R in {100, 200}, hash seeds 100000 + j) on the R-MAT scale-20
+    graph, submitted together so that they overlap on the device; each
+    one's seeds and gains equal the oracle's selection for the same query."""
+    import time
+
+    wl, g, o, res = rmat20
+    reqs = [(100, 12, 100000), (200, 20, 100001)]
+    srv = sg.sg_server_create(max_running=2, k_cap=32)
+    try:
+        ids = [(sg.sg_server_submit(srv, g.handle, R, k, wl.model, wl.p, seed), R, k, seed) for R, k, seed in reqs]
+        got = {}
+        deadline = time.time() + 300
+        while len(got) < len(ids) and time.time() < deadline:
+            for rid, R, k, seed in ids:
+                if rid in got:
+                    continue
+                done, seeds, gains, _ = sg.sg_server_poll(srv, rid, k)
+                if done:
+                    got[rid] = (seeds, gains)
+            time.sleep(0.01)
+        assert len(got) == len(ids)
+    finally:
+        sg.sg_server_destroy(srv)
+    for rid, R, k, seed in ids:
+        ref = o.select(R, k, seed, mode=oracle.CELF)
+        seeds, gains = got[rid]
+        assert np.array_equal(seeds, ref["seeds"]), (R, k)
+        assert np.array_equal(gains, ref["gains"]), (R, k)
+
+
 def test_rmat20_gains_are_exact_marginals(sg, rmat20):
     wl, g, o, res = rmat20
     gains = res.gains
