@@ -234,20 +234,16 @@ void free_graph_buffers(sg_graph *g, cudaStream_t st)
     dbuf_free(g->hid_out, st);
     dbuf_free(g->hrow_out, st);
     dbuf_free(g->hpref_out, st);
-    dbuf_free(g->hcpref_out, st);
-    dbuf_free(g->hbrow_out, st);
-    dbuf_free(g->hbrow_in, st);
     dbuf_free(g->hid_in, st);
     dbuf_free(g->hrow_in, st);
     dbuf_free(g->hpref_in, st);
-    dbuf_free(g->hcpref_in, st);
     dbuf_free(g->cc_esrc, st);
     dbuf_free(g->cc_pmin, st);
 }
 
 // Heavy rows of one direction (row offsets rp): degree >= min_deg.
 struct HeavyHost {
-    std::vector<int32_t> hid, hrow, hcpref, hbrow;  // hbrow: the heavy row of each index-build block
+    std::vector<int32_t> hid, hrow;
     std::vector<long long> hpref;
 };
 
@@ -256,7 +252,6 @@ HeavyHost heavy_rows(int64_t n, const std::vector<int32_t> &rp, int min_deg)
     HeavyHost h;
     h.hid.assign((size_t)n, -1);
     h.hpref.push_back(0);
-    h.hcpref.push_back(0);
     if (min_deg <= 0) return h;
     for (int64_t v = 0; v < n; ++v) {
         const int d = rp[(size_t)v + 1] - rp[(size_t)v];
@@ -264,8 +259,6 @@ HeavyHost heavy_rows(int64_t n, const std::vector<int32_t> &rp, int min_deg)
             h.hid[(size_t)v] = (int32_t)h.hrow.size();
             h.hrow.push_back((int32_t)v);
             h.hpref.push_back(h.hpref.back() + d);
-            h.hcpref.push_back(h.hcpref.back() + (d + 1023) / 1024);
-            for (int b = 0; b < (d + 1023) / 1024; ++b) h.hbrow.push_back((int32_t)h.hrow.size() - 1);
         }
     }
     return h;
@@ -352,13 +345,9 @@ sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> 
         (rc = upload(g->hid_out, ho.hid.data(), ho.hid.size(), st)) != SG_OK ||
         (rc = upload(g->hrow_out, ho.hrow.data(), ho.hrow.size(), st)) != SG_OK ||
         (rc = upload(g->hpref_out, ho.hpref.data(), ho.hpref.size(), st)) != SG_OK ||
-        (rc = upload(g->hcpref_out, ho.hcpref.data(), ho.hcpref.size(), st)) != SG_OK ||
         (rc = upload(g->hid_in, hi.hid.data(), hi.hid.size(), st)) != SG_OK ||
         (rc = upload(g->hrow_in, hi.hrow.data(), hi.hrow.size(), st)) != SG_OK ||
-        (rc = upload(g->hpref_in, hi.hpref.data(), hi.hpref.size(), st)) != SG_OK ||
-        (rc = upload(g->hcpref_in, hi.hcpref.data(), hi.hcpref.size(), st)) != SG_OK ||
-        (rc = upload(g->hbrow_out, ho.hbrow.data(), ho.hbrow.size(), st)) != SG_OK ||
-        (rc = upload(g->hbrow_in, hi.hbrow.data(), hi.hbrow.size(), st)) != SG_OK) {
+        (rc = upload(g->hpref_in, hi.hpref.data(), hi.hpref.size(), st)) != SG_OK) {
         free_graph_buffers(g, st);
         delete g;
         return rc;

@@ -307,8 +307,6 @@ struct sg_graph {
     sgi::DBuf<int32_t> cc_esrc, cc_pmin;
     sgi::DBuf<int32_t> hid_out, hrow_out, hid_in, hrow_in;
     sgi::DBuf<long long> hpref_out, hpref_in;
-    sgi::DBuf<int32_t> hcpref_out, hcpref_in;  // prefix of ceil(deg / index-build block) per heavy row
-    sgi::DBuf<int32_t> hbrow_out, hbrow_in;    // heavy row of each index-build block
     sg_workspace ws;
 };
 
