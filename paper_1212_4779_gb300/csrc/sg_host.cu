@@ -13,6 +13,7 @@
 #include <thread>
 #include <vector>
 
+#include "sg_graph_build.h"
 #include "sg_internal.cuh"
 
 namespace sgi {
@@ -144,67 +145,6 @@ sg_status ensure_wic(sg_graph *g, cudaStream_t st);
 namespace {
 
 // Workers for host-side passes over rows.
-int host_threads()
-{
-    unsigned h = std::thread::hardware_concurrency();
-    if (h == 0) h = 4;
-    return (int)std::min(h, 64u);
-}
-
-template <class F>
-void parallel_rows(int64_t n, F &&f)
-{
-    const int T = host_threads();
-    if (n < 4096 || T <= 1) {
-        f(0, n);
-        return;
-    }
-    std::vector<std::thread> th;
-    const int64_t chunk = (n + T - 1) / T;
-    for (int t = 0; t < T; ++t) {
-        const int64_t a = t * chunk, b = std::min(n, a + chunk);
-        if (a >= b) break;
-        th.emplace_back([&f, a, b] { f(a, b); });
-    }
-    for (auto &x : th) x.join();
-}
-
-// Canonical CSR: per row, destinations sorted ascending, repeats merged,
-// self-loops dropped (the paper treats parallel edges as one edge).  The
-// input rows are permuted in place in `col` (a private copy).
-sg_status canonicalise(int64_t n, std::vector<int64_t> &rp_in, std::vector<int32_t> &col,
-                       std::vector<int32_t> &rp_out, std::vector<int32_t> &col_out)
-{
-    std::vector<int32_t> len((size_t)n);
-    parallel_rows(n, [&](int64_t a, int64_t b) {
-        for (int64_t u = a; u < b; ++u) {
-            int32_t *r = col.data() + rp_in[u];
-            const int64_t d = rp_in[u + 1] - rp_in[u];
-            bool canon = true;
-            for (int64_t i = 0; i < d && canon; ++i)
-                if (r[i] == u || (i > 0 && r[i] <= r[i - 1])) canon = false;
-            if (!canon) std::sort(r, r + d);
-            int64_t c = 0;
-            for (int64_t i = 0; i < d; ++i)
-                if (r[i] != u && (i == 0 || r[i] != r[i - 1])) ++c;
-            len[(size_t)u] = (int32_t)c;
-        }
-    });
-    rp_out.assign((size_t)n + 1, 0);
-    for (int64_t u = 0; u < n; ++u) rp_out[(size_t)u + 1] = rp_out[(size_t)u] + len[(size_t)u];
-    col_out.resize((size_t)std::max<int64_t>(1, rp_out[(size_t)n]));
-    parallel_rows(n, [&](int64_t a, int64_t b) {
-        for (int64_t u = a; u < b; ++u) {
-            const int32_t *r = col.data() + rp_in[u];
-            const int64_t d = rp_in[u + 1] - rp_in[u];
-            int32_t *o = col_out.data() + rp_out[(size_t)u];
-            for (int64_t i = 0; i < d; ++i)
-                if (r[i] != u && (i == 0 || r[i] != r[i - 1])) *o++ = r[i];
-        }
-    });
-    return SG_OK;
-}
-
 __global__ void build_fw_kernel(long long m, const int32_t *col, const uint32_t *tmi, uint2 *fw)
 {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m;
@@ -247,7 +187,7 @@ struct HeavyHost {
     std::vector<long long> hpref;
 };
 
-HeavyHost heavy_rows(int64_t n, const std::vector<int32_t> &rp, int min_deg)
+HeavyHost heavy_rows(int64_t n, const sgh::hvec<int32_t> &rp, int min_deg)
 {
     HeavyHost h;
     h.hid.assign((size_t)n, -1);
@@ -265,27 +205,23 @@ HeavyHost heavy_rows(int64_t n, const std::vector<int32_t> &rp, int min_deg)
 }
 
 // Build a graph handle from a canonical CSR held on the host.
-sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> &col, cudaStream_t st,
+sg_status finish_load(int64_t n, sgh::hvec<int32_t> &rp, sgh::hvec<int32_t> &col, cudaStream_t st,
                       sg_graph **out)
 {
     const int64_t m = rp[(size_t)n];
     // CSC by a stable counting sort on destination: in-arcs of each node in
-    // increasing (source, arc id) order.
-    std::vector<int32_t> crp((size_t)n + 1, 0);
-    for (int64_t e = 0; e < m; ++e) crp[(size_t)col[(size_t)e] + 1]++;
-    for (int64_t v = 0; v < n; ++v) crp[(size_t)v + 1] += crp[(size_t)v];
-    std::vector<int2> cin((size_t)std::max<int64_t>(1, m));
-    {
-        std::vector<int32_t> fill(crp.begin(), crp.end() - 1);
-        for (int64_t u = 0; u < n; ++u)
-            for (int32_t e = rp[(size_t)u]; e < rp[(size_t)u + 1]; ++e)
-                cin[(size_t)fill[(size_t)col[(size_t)e]]++] = make_int2((int)u, e);
-    }
+    // increasing (source, arc id) order
+    sgh::hvec<int32_t> crp;
+    sgh::hvec<sgh::Arc2> cin;
+    sgh::build_csc(n, rp, col, crp, cin);
+    static_assert(sizeof(sgh::Arc2) == sizeof(int2), "CSC entries upload as int2");
     std::vector<uint32_t> tmi((size_t)n);
-    for (int64_t v = 0; v < n; ++v) {
-        const int64_t d = crp[(size_t)v + 1] - crp[(size_t)v];
-        tmi[(size_t)v] = d > 0 ? (uint32_t)((1ull << 32) / (uint64_t)d - 1ull) : 0xffffffffu;
-    }
+    sgh::parallel_rows(n, [&](int64_t a, int64_t b) {
+        for (int64_t v = a; v < b; ++v) {
+            const int64_t d = crp[(size_t)v + 1] - crp[(size_t)v];
+            tmi[(size_t)v] = d > 0 ? (uint32_t)((1ull << 32) / (uint64_t)d - 1ull) : 0xffffffffu;
+        }
+    });
     sg_graph *g = new (std::nothrow) sg_graph();
     if (!g) {
         set_error("host allocation failed");
@@ -326,13 +262,28 @@ sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> 
     g->nh_in = (int32_t)hi.hrow.size();
     {
         // expected live out-arcs per snapshot over the indexed rows under
-        // the weighted cascade (sizes the forward per-snapshot lists)
-        double acc = 0.0;
-        for (int32_t x : ho.hrow)
-            for (int32_t e = rp[(size_t)x]; e < rp[(size_t)x + 1]; ++e) {
-                const int32_t y = col[(size_t)e];
-                acc += 1.0 / (double)(crp[(size_t)y + 1] - crp[(size_t)y]);
+        // the weighted cascade (sizes the forward per-snapshot lists); 64
+        // fixed parts summed in order, so the value does not depend on the
+        // host's thread count
+        constexpr int P = 64;
+        std::vector<double> part(P, 0.0);
+        const size_t nr = ho.hrow.size(), pc = (nr + P - 1) / P;
+        const int PT = std::min(P, sgh::host_threads());
+        sgh::parallel_parts(PT, [&](int t) {
+            for (int q = t; q < P; q += PT) {
+                double acc = 0.0;
+                for (size_t i = q * pc; i < std::min(nr, (q + 1) * pc); ++i) {
+                    const int32_t x = ho.hrow[i];
+                    for (int32_t e = rp[(size_t)x]; e < rp[(size_t)x + 1]; ++e) {
+                        const int32_t y = col[(size_t)e];
+                        acc += 1.0 / (double)(crp[(size_t)y + 1] - crp[(size_t)y]);
+                    }
+                }
+                part[(size_t)q] = acc;
             }
+        });
+        double acc = 0.0;
+        for (double v : part) acc += v;
         g->hlive_out_wic = acc;
     }
     g->hsum_out = ho.hpref.back();
@@ -340,7 +291,7 @@ sg_status finish_load(int64_t n, std::vector<int32_t> &rp, std::vector<int32_t> 
     if ((rc = upload(g->rp, rp.data(), (size_t)n + 1, st)) != SG_OK ||
         (rc = upload(g->col, col.data(), (size_t)m, st)) != SG_OK ||
         (rc = upload(g->crp, crp.data(), (size_t)n + 1, st)) != SG_OK ||
-        (rc = upload(g->cin, cin.data(), (size_t)m, st)) != SG_OK ||
+        (rc = upload(g->cin, reinterpret_cast<const int2 *>(cin.data()), (size_t)m, st)) != SG_OK ||
         (rc = upload(g->tmi, tmi.data(), (size_t)n, st)) != SG_OK ||
         (rc = upload(g->hid_out, ho.hid.data(), ho.hid.size(), st)) != SG_OK ||
         (rc = upload(g->hrow_out, ho.hrow.data(), ho.hrow.size(), st)) != SG_OK ||
@@ -951,32 +902,37 @@ sg_status sg_load_graph(int64_t n, int64_t m, const int64_t *row_ptr, const int3
         set_error("sg_load_graph: need 1 <= n < 2^31, 0 <= m < 2^31 and non-NULL arrays");
         return SG_EINVAL;
     }
-    std::vector<int64_t> rp((size_t)n + 1);
-    std::vector<int32_t> c((size_t)std::max<int64_t>(1, m));
+    // host arrays are read in place; device arrays are copied to the host
+    std::vector<int64_t> rp_copy;
+    std::vector<int32_t> c_copy;
+    const int64_t *rp = row_ptr;
+    const int32_t *c = col;
     if (is_device_ptr) {
-        SG_CUDA_TRY(cudaMemcpyAsync(rp.data(), row_ptr, rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        if (m) SG_CUDA_TRY(cudaMemcpyAsync(c.data(), col, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        rp_copy.resize((size_t)n + 1);
+        c_copy.resize((size_t)std::max<int64_t>(1, m));
+        SG_CUDA_TRY(cudaMemcpyAsync(rp_copy.data(), row_ptr, rp_copy.size() * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    st));
+        if (m) SG_CUDA_TRY(cudaMemcpyAsync(c_copy.data(), col, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         SG_CUDA_TRY(cudaStreamSynchronize(st));
-    } else {
-        memcpy(rp.data(), row_ptr, rp.size() * sizeof(int64_t));
-        if (m) memcpy(c.data(), col, (size_t)m * sizeof(int32_t));
+        rp = rp_copy.data();
+        c = c_copy.data();
     }
     if (rp[0] != 0 || rp[(size_t)n] != m) {
         set_error("sg_load_graph: row_ptr[0] must be 0 and row_ptr[n] must be m");
         return SG_EINVAL;
     }
-    for (int64_t u = 0; u < n; ++u)
-        if (rp[(size_t)u + 1] < rp[(size_t)u]) {
-            set_error("sg_load_graph: row_ptr decreases at row %lld", (long long)u);
-            return SG_EINVAL;
-        }
-    for (int64_t e = 0; e < m; ++e)
-        if (c[(size_t)e] < 0 || c[(size_t)e] >= n) {
-            set_error("sg_load_graph: col[%lld] = %d out of range", (long long)e, c[(size_t)e]);
-            return SG_EINVAL;
-        }
-    std::vector<int32_t> rpc, colc;
-    SG_TRY(canonicalise(n, rp, c, rpc, colc));
+    const int64_t bu = sgh::parallel_first(n, [&](int64_t u) { return rp[(size_t)u + 1] < rp[(size_t)u]; });
+    if (bu < n) {
+        set_error("sg_load_graph: row_ptr decreases at row %lld", (long long)bu);
+        return SG_EINVAL;
+    }
+    const int64_t be = sgh::parallel_first(m, [&](int64_t e) { return c[(size_t)e] < 0 || c[(size_t)e] >= n; });
+    if (be < m) {
+        set_error("sg_load_graph: col[%lld] = %d out of range", (long long)be, c[(size_t)be]);
+        return SG_EINVAL;
+    }
+    sgh::hvec<int32_t> rpc, colc;
+    sgh::canonicalise(n, rp, c, rpc, colc);
     return finish_load(n, rpc, colc, st, out);
 }
 
@@ -1015,8 +971,8 @@ sg_status sg_load_graph_coo(int64_t n, int64_t m, const int32_t *src, const int3
         std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
         for (int64_t i = 0; i < m; ++i) c[(size_t)fill[(size_t)s[(size_t)i]]++] = d[(size_t)i];
     }
-    std::vector<int32_t> rpc, colc;
-    SG_TRY(canonicalise(n, rp, c, rpc, colc));
+    sgh::hvec<int32_t> rpc, colc;
+    sgh::canonicalise(n, rp.data(), c.data(), rpc, colc);
     return finish_load(n, rpc, colc, st, out);
 }
 
