@@ -520,13 +520,14 @@ sg_status ensure_wic(sg_graph *g, cudaStream_t st)
     return SG_OK;
 }
 
-// Tier-3 slot memory: 4 KB per node per resident dense block per SM (12 KB
-// at three), between 64 MB and 16 GiB.
+// Tier-3 slot memory: 4 KB per node per resident dense block per SM (48 KB
+// at twelve), between 64 MB and 16 GiB per three blocks (64 GiB at twelve).
 size_t tier3_budget(int64_t n)
 {
-    // about 24 bytes per node per slot: 12 KB per node gives every graph up
-    // to 1.1 M nodes its three slots per SM (tier-3 tasks are latency-bound,
-    // so the number of resident blocks sets their throughput)
+    // about 24 bytes per node per slot, 4 KB per node for each block per
+    // SM: every graph up to about 1.3 M nodes gets its full count of slots
+    // (tier-3 tasks are latency-bound, so the number of resident blocks
+    // sets their throughput)
     const size_t b = (size_t)n * 4096 * SG_DENSE_BLOCKS;
     const size_t cap = ((size_t)16 << 30) * (size_t)std::max(1, SG_DENSE_BLOCKS / 3);
     return std::min<size_t>(cap, std::max<size_t>((size_t)64 << 20, b));

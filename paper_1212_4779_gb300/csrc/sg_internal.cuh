@@ -46,10 +46,10 @@
 #define SG_DENSE_INIT_BLOCKS 4
 #endif
 #ifndef SG_DENSE_REV_THREADS
-#define SG_DENSE_REV_THREADS 256
+#define SG_DENSE_REV_THREADS 128
 #endif
 #ifndef SG_DENSE_REV_BLOCKS
-#define SG_DENSE_REV_BLOCKS 6
+#define SG_DENSE_REV_BLOCKS 12
 #endif
 #define SG_DENSE_BLOCKS (SG_DENSE_INIT_BLOCKS > SG_DENSE_REV_BLOCKS ? SG_DENSE_INIT_BLOCKS : SG_DENSE_REV_BLOCKS)
 // log2 of the shared-memory table slots of the reverse tasks' block-shared

@@ -1182,8 +1182,11 @@ struct SlotArgs {
 // 512-thread blocks.  Tasks are deep and narrow walks, so tasks in flight
 // per SM set the throughput more than threads per task.  The dense tier
 // (LOGC selects its shape: 0 initial gains, 1 reverse tasks) runs four
-// 384-thread blocks per SM for initial gains and six 256-thread blocks for
-// the smaller reverse tasks (40 registers either way).
+// 384-thread blocks per SM for initial gains and twelve 128-thread blocks
+// for the smaller reverse tasks (40 registers either way): a reverse
+// task's frontier rarely keeps more than four warps busy, so more tasks in
+// flight pay (six 256-thread blocks: 26 ms more per R-MAT 20 select),
+// while initial-gain tasks lose with fewer warps each.
 constexpr int CO_LOGC = 12;  // the largest shared-memory table
 constexpr unsigned short QE16 = 0xFFFF;
 enum { TAB_HASH = 0, TAB_DENSE = 1 };
