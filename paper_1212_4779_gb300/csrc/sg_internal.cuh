@@ -52,6 +52,18 @@
 #define SG_DENSE_REV_BLOCKS 12
 #endif
 #define SG_DENSE_BLOCKS (SG_DENSE_INIT_BLOCKS > SG_DENSE_REV_BLOCKS ? SG_DENSE_INIT_BLOCKS : SG_DENSE_REV_BLOCKS)
+// Dense-engine queue entries held in shared memory per block (the first
+// positions of each task's queue; the rest go to the global ring).  Initial
+// gains: 4096 (16 KB; the R-MAT 20 dense launch 267.0 -> 260.7 ms, 8192:
+// 261.2 ms); reverse tasks none (2048 made the selection rounds 5 ms
+// slower: twelve blocks' carve-out leaves less L1 to a kernel whose
+// scattered accesses keep the L1 data pipe the busiest unit).
+#ifndef SG_DENSE_INIT_SQ
+#define SG_DENSE_INIT_SQ 4096
+#endif
+#ifndef SG_DENSE_REV_SQ
+#define SG_DENSE_REV_SQ 0
+#endif
 // log2 of the shared-memory table slots of the reverse tasks' block-shared
 // tier (11: 2048-slot tables, four 256-thread blocks per SM, tasks past 1024
 // keys go on to the dense tier; 12: 4096-slot tables, two 512-thread blocks)

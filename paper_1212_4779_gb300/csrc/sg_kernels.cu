@@ -1199,6 +1199,7 @@ template <int LOGC>
 struct CoopShape<TAB_DENSE, LOGC> {
     static constexpr int T = LOGC == 0 ? SG_DENSE_INIT_THREADS : SG_DENSE_REV_THREADS;
     static constexpr int MINB = LOGC == 0 ? SG_DENSE_INIT_BLOCKS : SG_DENSE_REV_BLOCKS;
+    static constexpr int SQ = LOGC == 0 ? SG_DENSE_INIT_SQ : SG_DENSE_REV_SQ;  // shared-memory queue entries
 };
 
 struct CoopCtl {
@@ -1288,16 +1289,25 @@ struct CoopTab<TAB_DENSE, LOGC> {
     unsigned long long *st;
     int *queue, *touched;
     int qmask;
+    // queue positions below scap live in shared memory (sq), the rest in
+    // the global ring: most tasks push fewer entries than scap, so their
+    // producer-to-consumer hand-off stays on the SM
+    int *sq;
+    int scap;
+    __device__ __forceinline__ volatile int *qref(int pos)
+    {
+        return pos < scap ? (volatile int *)&sq[pos] : (volatile int *)&queue[pos & qmask];
+    }
 
     __device__ __forceinline__ unsigned long long &visr(int idx) { return st[2 * (size_t)idx]; }
     __device__ __forceinline__ unsigned long long &pendr(int idx) { return st[2 * (size_t)idx + 1]; }
     __device__ __forceinline__ int slot(int y, int, CoopCtl &) { return y; }
     __device__ __forceinline__ void note_new(int y, CoopCtl &c) { touched[atomicAdd(&c.nkeys, 1)] = y; }
     __device__ __forceinline__ int node(int idx) const { return idx; }
-    __device__ __forceinline__ void put(int pos, int idx) { *(volatile int *)&queue[pos & qmask] = idx; }
+    __device__ __forceinline__ void put(int pos, int idx) { *qref(pos) = idx; }
     __device__ __forceinline__ int take(int pos, CoopCtl &c, long long spin)
     {
-        volatile int *q = &queue[pos & qmask];
+        volatile int *q = qref(pos);
         for (long long i = 0; i < spin; ++i) {
             const int v = *q;
             if (v != EMPTY_KEY) {
@@ -1317,7 +1327,7 @@ struct CoopTab<TAB_DENSE, LOGC> {
     __device__ __forceinline__ int touched_at(int i) const { return touched[i]; }
     __device__ __forceinline__ void clear_queue(int head, int tail)
     {
-        for (int i = head + (int)threadIdx.x; i < tail; i += blockDim.x) queue[i & qmask] = EMPTY_KEY;
+        for (int i = head + (int)threadIdx.x; i < tail; i += blockDim.x) *qref(i) = EMPTY_KEY;
     }
 };
 
@@ -1542,6 +1552,9 @@ __global__ void __launch_bounds__(CoopShape<TAB, LOGC>::T, CoopShape<TAB, LOGC>:
         T.touched = sl.touched + so;
         T.queue = sl.qa + (size_t)blockIdx.x * (size_t)(sl.qmask + 1);
         T.qmask = sl.qmask;
+        T.sq = reinterpret_cast<int *>(smem_raw);
+        T.scap = CoopShape<TAB, LOGC>::SQ;
+        for (int i = tid; i < T.scap; i += CO_T) T.sq[i] = EMPTY_KEY;
     }
     const long long count = (long long)*(volatile unsigned long long *)io.in_count;
     unsigned long long *next = io.next;
@@ -2590,7 +2603,11 @@ sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cuda
     {
         constexpr int DV = TASK == TASK_INIT ? 0 : 1;  // dense shape by task kind
         const int blocks = std::min(ws.nslots, g->num_sms * CoopShape<TAB_DENSE, DV>::MINB);
-        coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK, DV><<<blocks, CoopShape<TAB_DENSE, DV>::T, 0, st>>>(
+        constexpr size_t sqb = (size_t)CoopShape<TAB_DENSE, DV>::SQ * sizeof(int);
+        if (sqb)
+            SG_CUDA_TRY(cudaFuncSetAttribute(coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK, DV>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sqb));
+        coop_engine_kernel<TAB_DENSE, DIR, MODEL, TASK, DV><<<blocks, CoopShape<TAB_DENSE, DV>::T, sqb, st>>>(
             a, slot_args(ws), StageIO{ws.list2.p, &ws.ctl.p->l2_count, &ws.ctl.p->l2_next, nullptr, nullptr, 2});
     }
     SG_CUDA_TRY(cudaGetLastError());
