@@ -228,7 +228,8 @@ sg_status sg_set_direction(int32_t mode, int32_t divisor);
 /* Blocks per 64-snapshot word of the level-synchronous walks (the forward
  * dynamic update's walk from each new seed and the landmark walks of the
  * initial gains): each block owns 64/groups of the word's snapshot bits.
- * 8, 16, 32 or 64 (default 32); more blocks spread one walk over more SMs.
+ * 8, 16, 32 or 64 (default 64: one snapshot bit per block); more blocks
+ * spread one walk over more SMs.
  * Workspaces size their level queues for max(8, groups) at creation (4
  * bytes per node, word and block, twice); a query on an older workspace
  * uses at most what it was sized for.  Results do not depend on it.

@@ -88,7 +88,7 @@ sg_status run_poison(const sg_graph *g, sg_workspace &ws, int32_t *seeds, long l
 int g_snapshot_lists = 1;
 int g_mask_cache = 0;
 int g_fwd_lists = 1;
-int g_walk_groups = 32;
+int g_walk_groups = 64;
 int g_word_major = 1;
 int g_t1_direct = 16;
 

@@ -85,7 +85,7 @@ def test_lt_every_walk_setting_and_tier_agrees(sg):
             assert got == [int(x) for x in ref["counters"]]
     finally:
         sg.sg_set_engine_limits(64, 2048)
-        sg.sg_set_walk_groups(32)
+        sg.sg_set_walk_groups(64)
         sg.sg_set_direction(1, 4)
     g.close()
 

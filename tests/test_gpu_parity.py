@@ -128,7 +128,7 @@ def limits(sg):
     sg.sg_set_snapshot_lists(1)
     sg.sg_set_mask_cache(0)
     sg.sg_set_forward_lists(1)
-    sg.sg_set_walk_groups(32)
+    sg.sg_set_walk_groups(64)
     sg.sg_set_direction(1, 4)
     sg.sg_set_scc_condensation(1)
     _set_tier1_direct(sg, 16)

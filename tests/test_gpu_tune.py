@@ -81,7 +81,7 @@ def test_batch_with_per_query_tunings_equals_oracle(sg):
             tun = sg.sg_tuning(**variants[i % len(variants)])
             items.append((g.handle, wss[-1], q["R"], q["k"], q["model"], q["p"], q["seed"], so, go, tun))
     finally:
-        sg.sg_set_walk_groups(32)
+        sg.sg_set_walk_groups(64)
     try:
         st = sg.sg_select_batch(items, concurrency=4)
         torch.cuda.synchronize()
