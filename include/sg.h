@@ -316,6 +316,20 @@ sg_status sg_graph_info(const sg_graph *g, int64_t *n, int64_t *m_canonical);
 sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
                     int32_t *out_seeds, int64_t *out_gains, sg_stats *stats);
 
+/* sg_select, then the state Algorithm 2 maintains after its k rounds, for
+ * checking its invariant (Section 4):
+ *   out_s   int64[n]: for every non-seed u the marginal gain
+ *           f(S ∪ {u}) − f(S) of the k seeds S (the s_u of Algorithm 2 after
+ *           the last round's update); seeds hold a negative marker
+ *   out_cov uint64[ceil(R/64) * n]: bit b of out_cov[w*n + u] is set iff u
+ *           is reached from S in snapshot 64w + b (the coverage of S)
+ * Outputs are host or device memory; the call synchronises `stream`.
+ * Cascades SG_UIC, SG_WIC and SG_LT (the undirected variant keeps its
+ * state as per-snapshot components).  Errors: as sg_select, and SG_EINVAL
+ * for NULL outputs or the undirected variant. */
+sg_status sg_select_state(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                          int32_t *out_seeds, int64_t *out_gains, int64_t *out_s, uint64_t *out_cov);
+
 /* Per-query device state (gains, coverage bitsets, task lists, caches).
  * sg_select uses one owned by the graph; several queries can run on one
  * graph at the same time only with workspaces of their own.

@@ -1254,6 +1254,31 @@ sg_status sg_select(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t se
     return select_impl(g, g->ws, R, k, c, seed, stream, out_seeds, out_gains, stats, false);
 }
 
+sg_status sg_select_state(sg_graph *g, int32_t R, int32_t k, sg_cascade c, uint64_t seed, void *stream,
+                          int32_t *out_seeds, int64_t *out_gains, int64_t *out_s, uint64_t *out_cov)
+{
+    clear_error();
+    if (!g || !out_s || !out_cov) {
+        set_error("sg_select_state: NULL argument");
+        return SG_EINVAL;
+    }
+    if (c.model == SG_UIC_UNDIRECTED) {
+        set_error("sg_select_state: the undirected variant keeps no coverage bitsets");
+        return SG_EINVAL;
+    }
+    sg_stats stats;
+    SG_TRY(select_impl(g, g->ws, R, k, c, seed, stream, out_seeds, out_gains, &stats, false));
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t W = (size_t)(R + 63) / 64;
+    // the round loop leaves s and the coverage in the workspace (both are
+    // cleared when the next query starts)
+    SG_CUDA_TRY(cudaMemcpyAsync(out_s, g->ws.s.p, (size_t)g->n * sizeof(long long), cudaMemcpyDefault, st));
+    SG_CUDA_TRY(cudaMemcpyAsync(out_cov, g->ws.cov.p, (size_t)g->n * W * 8, cudaMemcpyDefault, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    return SG_OK;
+}
+
 sg_status sg_workspace_create(const sg_graph *g, int32_t R_max, int32_t k_max, void *stream, sg_workspace **out)
 {
     clear_error();

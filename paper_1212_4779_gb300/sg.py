@@ -32,7 +32,7 @@ EXPORTS = ("sg_workspace_create", "sg_workspace_bytes", "sg_workspace_free", "sg
            "sg_server_poll", "sg_server_counts", "sg_server_destroy",
            "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
            "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_set_walk_groups", "sg_set_direction", "sg_set_scc_condensation", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_graph_trim", "sg_select",
-           "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version",
+           "sg_select_state", "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr", "sg_free_graph", "sg_last_error", "sg_version",
            "sg_debug_inject_flags", "sg_debug_set_wait_limit", "sg_get_tuning", "sg_set_tuning", "sg_autotune")
 
 
@@ -136,6 +136,7 @@ def lib() -> ctypes.CDLL:
         L.sg_load_graph_coo.argtypes = [i64, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
         L.sg_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.sg_select.argtypes = [P, i32, i32, sg_cascade, u64, P, P, P, ctypes.POINTER(sg_stats)]
+        L.sg_select_state.argtypes = [P, i32, i32, sg_cascade, u64, P, P, P, P, P]
         L.sg_init_gains.argtypes = [P, i32, sg_cascade, u64, P, P, ctypes.POINTER(u64)]
         L.sg_live_masks.argtypes = [P, i32, sg_cascade, u64, P, P]
         L.sg_graph_csr.argtypes = [P, P, P, P]
@@ -163,7 +164,7 @@ def lib() -> ctypes.CDLL:
                      "sg_batch_capture", "sg_batch_launch", "sg_server_create", "sg_server_submit",
                      "sg_server_poll", "sg_server_counts", "sg_set_allocator", "sg_set_heavy_threshold", "sg_set_engine_limits", "sg_set_landmarks",
                      "sg_set_snapshot_lists", "sg_set_forward_lists", "sg_set_mask_cache", "sg_set_walk_groups", "sg_set_direction", "sg_set_scc_condensation", "sg_argmax_noalloc", "sg_load_graph", "sg_load_graph_coo", "sg_graph_info", "sg_select",
-                     "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr",
+                     "sg_select_state", "sg_init_gains", "sg_spread", "sg_select_celf", "sg_live_masks", "sg_graph_csr",
                      "sg_debug_inject_flags", "sg_debug_set_wait_limit", "sg_get_tuning", "sg_set_tuning",
                      "sg_autotune"):
             getattr(L, name).restype = ctypes.c_int
@@ -403,6 +404,16 @@ def sg_select(h, R, k, model, p, seed, out_seeds, out_gains, stream=None, stats=
     return st.as_dict() if stats else None
 
 
+def sg_select_state(h, R, k, model, p, seed, out_seeds, out_gains, out_s, out_cov, stream=None):
+    """sg_select, then Algorithm 2's state after the k rounds: ``out_s``
+    (int64[n]: marginal gains of non-seeds, seeds negative) and ``out_cov``
+    (uint64[ceil(R/64) * n]: coverage bits of the seeds)."""
+    _check(lib().sg_select_state(h, int(R), int(k), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
+                                 _stream_ptr(stream), ctypes.c_void_p(_addr(out_seeds)[0]),
+                                 ctypes.c_void_p(_addr(out_gains)[0]), ctypes.c_void_p(_addr(out_s)[0]),
+                                 ctypes.c_void_p(_addr(out_cov)[0])))
+
+
 def sg_init_gains(h, R, model, p, seed, out_s, stream=None, want_edges=False):
     ed = ctypes.c_uint64(0)
     _check(lib().sg_init_gains(h, int(R), _cascade(model, p), ctypes.c_uint64(seed & (2**64 - 1)),
@@ -594,6 +605,16 @@ class Graph:
         gains = np.zeros(k, dtype=np.int64)
         st = sg_select(self._h, R, k, model, p, seed, seeds, gains, stream, stats)
         return Selection(seeds, gains, st)
+
+    def select_state(self, R, k, model="uic", p=0.0, seed=0, stream=None):
+        """(Selection, s int64[n], cov uint64[W, n]) after the k rounds."""
+        W = (R + 63) // 64
+        seeds = np.zeros(k, dtype=np.int32)
+        gains = np.zeros(k, dtype=np.int64)
+        s = np.zeros(self.n, dtype=np.int64)
+        cov = np.zeros((W, self.n), dtype=np.uint64)
+        sg_select_state(self._h, R, k, model, p, seed, seeds, gains, s, cov, stream)
+        return Selection(seeds, gains, None), s, cov
 
     def init_gains(self, R, model="uic", p=0.0, seed=0, stream=None):
         s = np.zeros(self.n, dtype=np.int64)

@@ -73,6 +73,7 @@ def test_invalid_arguments_are_rejected_without_gpu(libpath):
     assert b"n" in L.sg_last_error()
     assert L.sg_graph_info(None, None, None) == sg.SG_EINVAL
     assert L.sg_select(None, 10, 1, sg.sg_cascade(0, 0.1), 1, None, None, None, None) == sg.SG_EINVAL
+    assert L.sg_select_state(None, 10, 1, sg.sg_cascade(0, 0.1), 1, None, None, None, None, None) == sg.SG_EINVAL
     L.sg_free_graph(None)
 
 

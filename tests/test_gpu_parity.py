@@ -451,6 +451,61 @@ EDGE_CASES = [
 ]
 
 
+def _coverage_reference(o, n, R, seed, S):
+    """Coverage of S in every snapshot from the oracle's live masks (bits
+    pinned to the coin definition) and a library breadth-first search:
+    cov[w, u] bit b = u reached from S in snapshot 64w + b."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import breadth_first_order
+
+    W = (R + 63) // 64
+    masks = o.live_masks(R, seed)
+    src = np.repeat(np.arange(n), np.diff(o.rp)).astype(np.int64)
+    dst = o.col[: o.m].astype(np.int64)
+    cov = np.zeros((W, n), dtype=np.uint64)
+    for r in range(R):
+        live = ((masks[:, r // 64] >> np.uint64(r % 64)) & np.uint64(1)).astype(bool)
+        # a virtual root n with an arc to every seed: one search from S
+        rows = np.concatenate([src[live], np.full(len(S), n)])
+        cols = np.concatenate([dst[live], np.asarray(S, dtype=np.int64)])
+        A = sp.csr_matrix((np.ones(rows.size, dtype=np.int8), (rows, cols)), shape=(n + 1, n + 1))
+        reached = breadth_first_order(A, n, directed=True, return_predecessors=False)
+        reached = reached[reached < n]
+        cov[r // 64, reached] |= np.uint64(1) << np.uint64(r % 64)
+    return cov
+
+
+@pytest.mark.parametrize("name,model,p,R,k", [("er2k", "uic", 0.1, 100, 10), ("cl15k", "wic", 0.0, 100, 20),
+                                              ("cl15k", "lt", 0.0, 130, 12)])
+def test_state_after_k_rounds_matches_oracle(sg, name, model, p, R, k):
+    """The state Algorithm 2 maintains (Section 4) after its k rounds: the
+    whole gain vector equals the oracle's DU vector (every non-seed's
+    marginal gain f(S + u) - f(S), checked on a sample against the oracle's
+    spread too; seeds negative), and the coverage bitsets equal the reach
+    of S in every snapshot, from the oracle's live masks and a library
+    breadth-first search (the last word masked to R mod 64)."""
+    gens = {"er2k": lambda: inputs.er_directed(2000, 10000, 101),
+            "cl15k": lambda: inputs.chung_lu_undirected(15000, 58000, 2.5, 7.7, 102)}
+    n, s, d = gens[name]()
+    g, o = _both(sg, n, s, d, model, p)
+    seed = 77
+    sel, s_gpu, cov = g.select_state(R, k, model, p, seed)
+    ref = o.select(R, k, seed, mode=oracle.DU, want_hist=True)
+    assert np.array_equal(sel.seeds, ref["seeds"]) and np.array_equal(sel.gains, ref["gains"])
+    S = sel.seeds
+    nonseed = np.ones(n, dtype=bool)
+    nonseed[S] = False
+    assert np.array_equal(s_gpu[nonseed], ref["s_hist"][k - 1][nonseed])
+    assert np.all(s_gpu[S] < 0)
+    fS = o.spread(R, seed, S)
+    assert fS == int(sel.gains.sum())
+    rng = np.random.default_rng(5)
+    for u in rng.choice(np.flatnonzero(nonseed), 8, replace=False):
+        assert s_gpu[u] == o.spread(R, seed, np.append(S, u)) - fS
+    assert np.array_equal(cov, _coverage_reference(o, n, R, seed, S))
+    assert sum(bin(int(x)).count("1") for x in cov.ravel()) == fS
+
+
 @pytest.mark.parametrize("label,gen,model,p,R,k", EDGE_CASES, ids=[c[0] for c in EDGE_CASES])
 def test_select_edge_cases(sg, label, gen, model, p, R, k):
     n, s, d = gen()
