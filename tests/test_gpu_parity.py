@@ -100,6 +100,22 @@ def test_init_gains_match_oracle(sg, name, R):
     assert ed == ed_want
 
 
+@pytest.mark.parametrize("name", ["cl15k_wic", "er2k_uic0.1"])
+def test_init_gains_per_word_partial_sums(sg, name):
+    """Per-word partial sums of the initial gains: the gains over R = 192
+    snapshots minus those over R = 128 (a snapshot's coins do not depend
+    on R) are word 2's sums, equal to the oracle's over snapshots 128..191;
+    likewise word 0 against R = 64."""
+    wl = inputs.workload(name)
+    n, s, d = wl.graph()
+    g, o = _both(sg, n, s, d, wl.model, wl.p)
+    s64, _ = g.init_gains(64, wl.model, wl.p, wl.seed)
+    s128, _ = g.init_gains(128, wl.model, wl.p, wl.seed)
+    s192, _ = g.init_gains(192, wl.model, wl.p, wl.seed)
+    assert np.array_equal(s64, o.init_gains(192, wl.seed, 0, 64)[0])
+    assert np.array_equal(s192 - s128, o.init_gains(192, wl.seed, 128, 192)[0])
+
+
 @pytest.mark.parametrize("lmk", [0, 8])
 def test_big_tasks_take_the_upper_tiers_and_agree(sg, limits, lmk):
     """High-probability cascade: most sources reach hundreds of nodes per
