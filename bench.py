@@ -778,7 +778,7 @@ def phase_rates(st):
     """Snapshot-edges per second of each phase, and elements actually
     expanded per second.  The reverse counter is the implementation-
     independent sum over every (w, r) the dynamic update removes and every u
-    reaching w of indeg(u) (the paper's per-node reverse BFS); this build
+    reaching w of indeg(u) (the paper's per-node reverse BFS); the library
     settles most of it without walking (the ancestor pass credits |N_r| to
     every ancestor of v* at once, target-sliced tasks share walks), so the
     reverse and total rates are nominal, while `elements_per_s` counts the
