@@ -23,13 +23,15 @@
 //   tier 1  one warp per task, visited/pending words in a 512-slot
 //           shared-memory hash table; frontier expanded 32 elements at a
 //           time with a load-balanced (prefix sum + shuffle search) split.
-//   tier 2  one 16-warp block per task sharing an 8192-slot shared-memory
+//   tier 2  one 8-warp block per task sharing a 2048-slot shared-memory
 //           table and an asynchronous ring queue, for tasks that filled the
-//           tier-1 table past its limit.
+//           tier-1 table past its limit with a small frontier left.
 //   tier 3  the same cooperative engine over dense per-block arrays in
-//           global memory (no limit).
-//   The forward dynamic update and the ancestor walk run a level-
-//   synchronous block traversal over the coverage bitsets.
+//           global memory (no limit): initial gains in 12-warp blocks
+//           (the first queue positions in shared memory), reverse tasks in
+//           4-warp blocks.
+//   The forward dynamic update, the landmark walks and the ancestor walk
+//   run level-synchronous block traversals over the coverage bitsets.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -1164,15 +1166,15 @@ struct SlotArgs {
 
 // ===================================================== cooperative engine
 //
-// One 512-thread block per task: its 16 warps share one visited/pending
-// table and one ring queue of frontier entries.  A warp claims up to 32
+// One block per task: its warps share one visited/pending table and one
+// ring queue of frontier entries (block shapes below).  A warp claims up to 32
 // queued entries at a time (CAS on the queue head), expands them with the
 // same load-balanced arc split as the warp engine and pushes the nodes that
 // gain new bits; there are no level barriers.  The traversal ends when the
 // queue is empty and no warp holds claimed entries.  Every spin (waiting
 // for work, waiting for a pushed entry to land) is bounded; on expiry the
 // block records an error flag instead of waiting on.
-//   TAB_HASH   8192-slot table in shared memory (tier 2; a task that grows
+//   TAB_HASH   hash table in shared memory (tier 2; a task that grows
 //              past the key limit moves on to tier 3)
 //   TAB_DENSE  dense per-block arrays in global memory indexed by node
 //              (tier 3; never overflows)
@@ -2587,8 +2589,7 @@ sg_status launch_tiers(sg_graph *g, sg_workspace &ws, const EngineArgs &a0, cuda
         // 2048-slot tables, four per SM (a 4096-slot second stage for their
         // 1-2 K-node tasks was slower than sending those to tier 3); so do
         // reverse tasks by default (4096-slot tables, two per SM, measured
-        // 34 ms slower per select once the dense tier ran six reverse blocks
-        // per SM).
+        // 34 ms slower per select with the dense tier's reverse blocks).
         const int lim1 = std::max(1, std::min(knobs().t1_keys, (1 << T1_LOGC) / 2));
         const int t2 = std::max(1, std::min(knobs().t2_keys, (1 << CO_LOGC) / 2));
         Ctl *ctl = ws.ctl.p;
